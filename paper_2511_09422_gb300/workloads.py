@@ -1,0 +1,234 @@
+"""Seeded synthetic inputs: grids, model parameters and initial fields.
+
+This module only builds inputs.  It holds none of the LB method's arithmetic,
+so both the GPU path and the FP64 oracle can be fed from it.  Every workload
+is a dict ``{"grid": ..., "params": ..., "fields": ..., "steps": ..., "name": ...}``:
+
+* ``grid``   -- lattice size and wall conditions (x is always periodic; walls
+  sit half-way between rows, at y = -1/2 and y = ny - 1/2);
+* ``params`` -- per-phase properties (liquid ``_l``, solid ``_s``, the
+  surrounding phase phi = -1 ``_g``), enthalpy, solute, interface and
+  surface-tension constants;
+* ``fields`` -- initial phi, T, C, ux, uy as float64 arrays of shape (ny, nx).
+
+The order parameter starts from the equilibrium profile phi = tanh(2 d / W)
+with d the signed distance to the interface (positive inside the
+phase-change material) and W = 4 cells, i.e. epsilon = W / (2 sqrt 2)
+(Eq. 3 with phi_1 = 1, phi_2 = -1).
+
+Lattice-unit values that the paper does not fix are chosen here and stated
+beside each workload.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WALL_DIRICHLET_T = 0
+WALL_ADIABATIC = 1
+
+INTERFACE_WIDTH = 4.0
+EPS = INTERFACE_WIDTH / (2.0 * math.sqrt(2.0))
+
+
+def base_params(**kw) -> dict:
+    """Liquid-like defaults in lattice units: rho_l = Cp = 1, nu = 0.1 in every
+    phase, lambda = 0.3, mobility 0.1, eps = sqrt(2) (W = 4)."""
+    p = dict(rho_l=1.0, rho_s=1.0, rho_g=1.0, mu_l=0.1, mu_s=0.1, mu_g=0.1,
+             lam_l=0.3, lam_s=0.3, lam_g=0.3, cp_l=1.0, cp_s=1.0, cp_g=1.0,
+             latent=10.0, T_sol=0.0, T_liq=0.0, k_p=1.0, D_l=0.1, D_s=0.1,
+             eps=EPS, mobility=0.1, sigma0=1e-3, sigma_T=0.0, sigma_c=0.0, T_ref=0.0,
+             c_ref=0.0, gx=0.0, gy=0.0, fs_modulated_st=1, phase_change_on=1, divu_mode=0)
+    p.update(kw)
+    return p
+
+
+def gas_properties(p: dict, rho_g: float, nu: float = 0.1, lam_ratio: float = 0.1) -> dict:
+    """Surrounding phase with density rho_g, the liquid's volumetric heat
+    capacity (rho Cp)_g = (rho Cp)_l, conductivity lam_ratio * lam_l and the
+    common kinematic viscosity nu."""
+    p = dict(p)
+    p["rho_g"] = rho_g
+    p["cp_g"] = p["rho_l"] * p["cp_l"] / rho_g
+    p["lam_g"] = lam_ratio * p["lam_l"]
+    p["mu_l"] = nu * p["rho_l"]
+    p["mu_s"] = nu * p["rho_s"]
+    p["mu_g"] = nu * rho_g
+    return p
+
+
+def grid(nx, ny, bc_bottom=WALL_DIRICHLET_T, bc_top=WALL_ADIABATIC, T_bottom=0.0, T_top=0.0,
+         T_bottom_amp=0.0, T_bottom_modes=1) -> dict:
+    return dict(nx=int(nx), ny=int(ny), bc_bottom=int(bc_bottom), bc_top=int(bc_top),
+                T_bottom=float(T_bottom), T_top=float(T_top), T_bottom_amp=float(T_bottom_amp),
+                T_bottom_modes=int(T_bottom_modes))
+
+
+def tanh_profile(d: np.ndarray, width: float = INTERFACE_WIDTH) -> np.ndarray:
+    return np.tanh(2.0 * d / width)
+
+
+def _coords(nx, ny):
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y
+
+
+def _fields(phi, T, C, ux=None, uy=None) -> dict:
+    z = np.zeros_like(phi)
+    return dict(phi=phi, T=T, C=C, ux=z.copy() if ux is None else ux, uy=z.copy() if uy is None else uy)
+
+
+# --------------------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------------------
+
+def stefan_layer(nx=64, ny=256, h0=128, ste=0.1, rho_ratio=0.9, rho_g=0.1, T_wall=-1.0,
+                 T_melt=0.0, lam=0.3, steps=2000) -> dict:
+    """Film freezing on a cold wall with a gas layer on top (three-phase Stefan
+    problem, Sec. 4.2): liquid for y < h0, gas above; bottom wall Dirichlet
+    T_wall, top adiabatic; T_0 = T_m everywhere; L = Cp_s (T_m - T_w) / Ste;
+    rho_s / rho_l = rho_ratio; no solute, no Marangoni stress."""
+    x, y = _coords(nx, ny)
+    d = (h0 - 0.5) - y
+    phi = tanh_profile(d)
+    T = np.full_like(phi, T_melt)
+    C = np.zeros_like(phi)
+    p = base_params(rho_s=rho_ratio, lam_l=lam, lam_s=lam, T_sol=T_melt, T_liq=T_melt,
+                    latent=1.0 * (T_melt - T_wall) / ste)
+    p = gas_properties(p, rho_g)
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_ADIABATIC, T_bottom=T_wall)
+    return dict(name="stefan_layer_%dx%d" % (nx, ny), grid=g, params=p,
+                fields=_fields(phi, T, C), steps=steps,
+                meta=dict(h0=h0, ste=ste, rho_ratio=rho_ratio, T_wall=T_wall, T_melt=T_melt))
+
+
+def thermocapillary_channel(nx=512, ny=256, h=None, T_h=20.0, T_c=10.0, T_0=4.0, T_ref=10.0,
+                            sigma_ref=2.5e-2, mu=0.2, lam=0.2, ma=0.1, steps=20000,
+                            width=INTERFACE_WIDTH) -> dict:
+    """Marangoni convection of two superposed fluids (Sec. 4.1, second test and
+    Appendix A): lower fluid (phi = 1) for y < h, upper fluid above, equal
+    rho = Cp = 1, mu and lambda; bottom wall T_h + T_0 cos(2 pi x / L), top T_c;
+    sigma(T) = sigma_ref + sigma_T (T - T_ref) with sigma_T < 0 fixed by
+    Ma = rho Cp |sigma_T| T_0 h / (mu lambda); no phase change, no solute.
+    The temperature starts from the conduction profile between the walls."""
+    if h is None:
+        h = ny // 2
+    x, y = _coords(nx, ny)
+    d = (h - 0.5) - y
+    phi = tanh_profile(d, width)
+    Htot = float(ny)
+    T = T_h + (T_c - T_h) * (y + 0.5) / Htot
+    C = np.zeros_like(phi)
+    sigma_T = -ma * mu * lam / (1.0 * 1.0 * T_0 * h)
+    p = base_params(rho_l=1.0, rho_s=1.0, rho_g=1.0, mu_l=mu, mu_s=mu, mu_g=mu, lam_l=lam,
+                    lam_s=lam, lam_g=lam, cp_l=1.0, cp_s=1.0, cp_g=1.0, latent=0.0,
+                    sigma0=sigma_ref, sigma_T=sigma_T, T_ref=T_ref, phase_change_on=0,
+                    fs_modulated_st=1, eps=width / (2.0 * math.sqrt(2.0)))
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_DIRICHLET_T, T_bottom=T_h, T_top=T_c,
+             T_bottom_amp=T_0, T_bottom_modes=1)
+    return dict(name="thermocapillary_channel_%dx%d" % (nx, ny), grid=g, params=p,
+                fields=_fields(phi, T, C), steps=steps,
+                meta=dict(h=h, H=ny - h, T_h=T_h, T_c=T_c, T_0=T_0, sigma_T=sigma_T, mu=mu, lam=lam))
+
+
+def sessile_droplet(nx=512, ny=512, radius=100.0, rho_ratio=0.9, rho_g=0.001, ste=0.1, c0=0.05,
+                    ma_T=10.0, ma_C=10.0, k_p=0.5, D_l=0.05, D_s=0.005, sigma0=0.01,
+                    T_wall=-1.0, lam=0.3, nu=0.1, steps=None, perturb=0.0, seed=0) -> dict:
+    """Binary droplet freezing on a cold substrate (Sec. 4.4): a half-disc of
+    radius R centred on the bottom wall (90-degree contact angle), solute C0 in
+    the droplet, T_0 = T_m = 0, bottom wall Dirichlet T_wall, top adiabatic.
+    Thermal Marangoni: |sigma_T| from Ma_T = |sigma_T| (T_m - T_w) R / (mu_l alpha_l);
+    solutal: |sigma_c| from Ma_C = |sigma_c| C0 R / (mu_l D_l); sigma falls with T
+    and with C (Sec. 4.4).  ``perturb`` adds seeded uniform noise of that
+    amplitude to T everywhere (upwards, so that no cell starts below T_m) and
+    to C inside the droplet."""
+    x, y = _coords(nx, ny)
+    xc, yc = nx / 2.0, -0.5
+    d = radius - np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
+    phi = tanh_profile(d)
+    T = np.zeros_like(phi)
+    chi = np.clip(0.5 * (1.0 + phi), 0.0, 1.0)
+    C = c0 * chi
+    if perturb:
+        rng = np.random.default_rng(seed)
+        T = T + perturb * rng.uniform(0.0, 1.0, size=T.shape)
+        C = C + perturb * chi * rng.uniform(-1.0, 1.0, size=C.shape)
+    p = base_params(rho_s=rho_ratio, lam_l=lam, lam_s=lam, k_p=k_p, D_l=D_l, D_s=D_s,
+                    sigma0=sigma0, latent=1.0 * (0.0 - T_wall) / ste, T_ref=0.0, c_ref=c0)
+    p = gas_properties(p, rho_g, nu=nu)
+    alpha_l = p["lam_l"] / (p["rho_l"] * p["cp_l"])
+    p["sigma_T"] = -ma_T * p["mu_l"] * alpha_l / ((0.0 - T_wall) * radius) if ma_T else 0.0
+    p["sigma_c"] = -ma_C * p["mu_l"] * D_l / (c0 * radius) if (ma_C and c0) else 0.0
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_ADIABATIC, T_bottom=T_wall)
+    return dict(name="sessile_droplet_%dx%d" % (nx, ny), grid=g, params=p,
+                fields=_fields(phi, T, C), steps=steps,
+                meta=dict(radius=radius, ste=ste, c0=c0, ma_T=ma_T, ma_C=ma_C))
+
+
+def parity_droplet(nx=128, ny=128, rho_g=0.1, seed=0, steps=100) -> dict:
+    """Parity case: a 128x128 version of the sessile droplet with R = 0.3 nx,
+    Marangoni stresses on, solute on, seeded +-1e-3 noise on T and on C in the
+    droplet so that every term of the step is exercised within 100 steps."""
+    w = sessile_droplet(nx=nx, ny=ny, radius=0.3 * nx, rho_g=rho_g, perturb=1e-3, seed=seed)
+    w["name"] = "parity_droplet_%dx%d" % (nx, ny)
+    w["steps"] = steps
+    return w
+
+
+def impurity_front(nx=4096, ny=4096, radius=200.0, rho_ratio_impurity=2.0, c0=0.05, ma=10.0,
+                   ste=0.1, rho_ratio=0.9, T_wall=-1.0, lam=0.3, k_p=0.5, D_l=0.05, D_s=0.005,
+                   sigma0=0.01, center=None, steps=1000) -> dict:
+    """Planar freezing front from the cold bottom wall into a binary liquid
+    (C0) that holds an insoluble circular impurity (the phi = -1 phase) of
+    radius ``radius`` with rho_i / rho_l = 2 and lambda_i = lambda_l, centred
+    at (nx/2, ny/4); Marangoni stresses at the impurity interface with
+    Ma_T = Ma_C = ``ma`` as in ``sessile_droplet``; top wall adiabatic."""
+    x, y = _coords(nx, ny)
+    if center is None:
+        center = (nx / 2.0, ny / 4.0)
+    d = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2) - radius
+    phi = tanh_profile(d)
+    T = np.zeros_like(phi)
+    chi = np.clip(0.5 * (1.0 + phi), 0.0, 1.0)
+    C = c0 * chi
+    p = base_params(rho_s=rho_ratio, lam_l=lam, lam_s=lam, k_p=k_p, D_l=D_l, D_s=D_s,
+                    sigma0=sigma0, latent=1.0 * (0.0 - T_wall) / ste, T_ref=0.0, c_ref=c0)
+    rho_i = rho_ratio_impurity * p["rho_l"]
+    p = gas_properties(p, rho_i, lam_ratio=1.0)
+    alpha_l = p["lam_l"] / (p["rho_l"] * p["cp_l"])
+    p["sigma_T"] = -ma * p["mu_l"] * alpha_l / ((0.0 - T_wall) * radius)
+    p["sigma_c"] = -ma * p["mu_l"] * D_l / (c0 * radius)
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_ADIABATIC, T_bottom=T_wall)
+    return dict(name="impurity_front_%dx%d" % (nx, ny), grid=g, params=p,
+                fields=_fields(phi, T, C), steps=steps,
+                meta=dict(radius=radius, c0=c0, ma=ma, center=center))
+
+
+def static_droplet(nx=96, ny=96, radius=20.0, sigma=0.01, rho_g=1.0, steps=4000) -> dict:
+    """Static droplet in the middle of the box, no phase change, no solute,
+    uniform temperature, constant surface tension (Laplace test)."""
+    x, y = _coords(nx, ny)
+    d = radius - np.sqrt((x - (nx - 1) / 2.0) ** 2 + (y - (ny - 1) / 2.0) ** 2)
+    phi = tanh_profile(d)
+    T = np.zeros_like(phi)
+    C = np.zeros_like(phi)
+    p = base_params(sigma0=sigma, phase_change_on=0, latent=0.0)
+    p = gas_properties(p, rho_g, lam_ratio=1.0)
+    g = grid(nx, ny, WALL_ADIABATIC, WALL_ADIABATIC)
+    return dict(name="static_droplet_%dx%d" % (nx, ny), grid=g, params=p,
+                fields=_fields(phi, T, C), steps=steps, meta=dict(radius=radius, sigma=sigma))
+
+
+WORKLOADS = {
+    "stefan_layer": stefan_layer,
+    "thermocapillary_channel": thermocapillary_channel,
+    "sessile_droplet": sessile_droplet,
+    "parity_droplet": parity_droplet,
+    "impurity_front": impurity_front,
+    "static_droplet": static_droplet,
+}
+
+
+def make(name: str, **kw) -> dict:
+    return WORKLOADS[name](**kw)

@@ -1,0 +1,406 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself: each check is a closed form
+printed in the paper, a moment identity the LB equilibria and sources must
+satisfy to recover the paper's macroscopic equations, an exact property of
+the difference schemes, a conservation law of the model, or a value printed
+in the paper (tests/golden).  A plausible mistake in any part of the oracle
+(dropped term, wrong sign or index, transposed operand) fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import analytic as A
+from paper_2511_09422_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=np.float64)
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=np.float64)
+CS2 = 1.0 / 3.0
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                rows.append(line)
+    return rows
+
+
+# ------------------------------------------------------------------------------------------
+# Difference schemes (end of Sec. 3.4)
+# ------------------------------------------------------------------------------------------
+
+def test_stencil_exact_on_quadratics(oracle_mod):
+    nx, ny = 12, 10
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    a, b, c, d, e, f = 0.3, -1.2, 0.7, 0.11, -0.05, 0.09
+    v = a + b * x + c * y + d * x * x + e * x * y + f * y * y
+    g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    gx, gy, lap = oracle_mod.stencil_field(g, v, 0)
+    inner = (slice(1, ny - 1), slice(1, nx - 1))
+    np.testing.assert_allclose(gx[inner], (b + 2 * d * x + e * y)[inner], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(gy[inner], (c + e * x + 2 * f * y)[inner], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lap[inner], 2 * d + 2 * f, rtol=0, atol=1e-12)
+
+
+def test_stencil_wall_ghosts(oracle_mod):
+    nx, ny = 8, 6
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    # a field even about the wall y = -1/2: the mirror ghost is its exact extension
+    v = (y + 0.5) ** 2
+    g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    _, gy, lap = oracle_mod.stencil_field(g, v, 0)
+    np.testing.assert_allclose(gy[0], 2 * 0.5, atol=1e-12)
+    np.testing.assert_allclose(lap[0], 2.0, atol=1e-12)
+    # a temperature linear in y with T = T_w(x) on the bottom wall: the Dirichlet
+    # ghost 2 T_w - T is exact; the x-derivative of the cosine is the central difference
+    Tb, amp, k = 2.0, 0.5, 2
+    g = W.grid(nx, ny, W.WALL_DIRICHLET_T, W.WALL_DIRICHLET_T, T_bottom=Tb, T_top=Tb + 0.3 * ny,
+               T_bottom_amp=amp, T_bottom_modes=k)
+    wall = Tb + amp * np.cos(2 * np.pi * k * x / nx)
+    T = wall + 0.3 * (y + 0.5)
+    gx, gy, _ = oracle_mod.stencil_field(g, T, 1)  # bottom row only: the top wall is not consistent
+    np.testing.assert_allclose(gy[0], 0.3, atol=1e-12)
+    kk = 2 * np.pi * k / nx
+    np.testing.assert_allclose(gx[0], -amp * np.sin(kk * x[0]) * np.sin(kk), atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------
+# Equilibria and sources: the moments that recover the model equations
+# ------------------------------------------------------------------------------------------
+
+def _moments(v):
+    return v.sum(), (CX * v).sum(), (CY * v).sum(), (CX * CX * v).sum(), (CX * CY * v).sum(), (CY * CY * v).sum()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibrium_moments(oracle_mod, seed):
+    rng = np.random.default_rng(seed)
+    p = W.base_params(rho_s=0.9, cp_s=0.8, cp_l=1.3)
+    phi, C, rhoH, T, pr = rng.uniform(-1, 1), rng.uniform(0, 0.2), rng.uniform(-2, 12), rng.uniform(-1, 1), rng.uniform(-1e-2, 1e-2)
+    ux, uy, rho, rhocp = rng.uniform(-0.05, 0.05), rng.uniform(-0.05, 0.05), rng.uniform(0.1, 1), rng.uniform(0.5, 2)
+    f, g, h, l = oracle_mod.equilibria(p, phi, C, rhoH, T, pr, ux, uy, rho, rhocp)
+    rr = p["rho_l"] * 2 * p["cp_s"] * p["cp_l"] / (p["cp_s"] + p["cp_l"])
+    # phase field: zeroth phi, first phi u (advective flux of Eq. ACE)
+    m = _moments(f)
+    np.testing.assert_allclose(m[:3], [phi, phi * ux, phi * uy], atol=1e-14)
+    np.testing.assert_allclose(m[3:], [CS2 * phi, 0, CS2 * phi], atol=1e-14)
+    # flow: zeroth 0 (pressure-based), first rho u, second p I + rho u u (Eq. NS2)
+    m = _moments(g)
+    np.testing.assert_allclose(m, [0, rho * ux, rho * uy, pr + rho * ux * ux, rho * ux * uy, pr + rho * uy * uy], atol=1e-14)
+    # enthalpy: zeroth rho H, first rho Cp T u (Eq. Tem), second rho_ref Cp_ref T cs2 I + rho Cp T u u
+    m = _moments(h)
+    np.testing.assert_allclose(m, [rhoH, rhocp * T * ux, rhocp * T * uy, rr * T * CS2 + rhocp * T * ux * ux,
+                                   rhocp * T * ux * uy, rr * T * CS2 + rhocp * T * uy * uy], atol=1e-13)
+    # solute: zeroth C, first C u (Eq. c)
+    m = _moments(l)
+    np.testing.assert_allclose(m[:3], [C, C * ux, C * uy], atol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_source_moments(oracle_mod, seed):
+    rng = np.random.default_rng(10 + seed)
+    kw = {k: rng.uniform(-0.1, 0.1) for k in ("dphiux", "dphiuy", "mdot", "S", "Fx", "Fy", "rfx", "rfy", "Ftx",
+                                             "Fty", "ux", "uy", "Q", "dCux", "dCuy", "Rx", "Ry")}
+    th = rng.uniform(0, 2 * np.pi)
+    kw.update(nx=math.cos(th), ny=math.sin(th), phi=rng.uniform(-1, 1), eps=math.sqrt(2.0))
+    F, G, H, L = oracle_mod.sources(**kw)
+    divu = kw["mdot"]
+    kf = (1 - kw["phi"] ** 2) / (math.sqrt(2) * kw["eps"])
+    m = _moments(F)
+    np.testing.assert_allclose(m[:3], [kw["phi"] * divu, kw["dphiux"] + CS2 * kf * kw["nx"],
+                                       kw["dphiuy"] + CS2 * kf * kw["ny"]], atol=1e-14)
+    m = _moments(G)
+    uFx, uFy = kw["ux"] * kw["Ftx"], kw["uy"] * kw["Fty"]
+    np.testing.assert_allclose(m, [kw["S"], kw["Fx"] + kw["rfx"], kw["Fy"] + kw["rfy"],
+                                   kw["S"] * CS2 + 2 * uFx, kw["ux"] * kw["Fty"] + kw["uy"] * kw["Ftx"],
+                                   kw["S"] * CS2 + 2 * uFy], atol=1e-14)
+    m = _moments(H)
+    np.testing.assert_allclose(m[:3], [kw["Q"], 0, 0], atol=1e-15)
+    m = _moments(L)
+    np.testing.assert_allclose(m[:3], [0, kw["dCux"] + CS2 * kw["Rx"], kw["dCuy"] + CS2 * kw["Ry"]], atol=1e-14)
+
+
+# ------------------------------------------------------------------------------------------
+# Enthalpy relation (Eq. Hfl)
+# ------------------------------------------------------------------------------------------
+
+def test_enthalpy_relation(oracle_mod):
+    # a binary alloy with a mushy range, solid and liquid properties different
+    p = W.base_params(rho_s=0.9, cp_s=0.7, cp_l=1.2, latent=4.0, T_sol=-0.3, T_liq=0.2)
+    p = W.gas_properties(p, 0.1)
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        T, chi = rng.uniform(-2, 2), rng.uniform(0, 1)
+        e = oracle_mod.enthalpy_forward(p, T, chi)
+        T2, fs = oracle_mod.enthalpy_invert(p, e, chi)
+        assert abs(T2 - T) < 1e-12 and -1e-15 <= fs <= chi + 1e-15
+    # Eq. Hfl at chi = 1, written out for the pure phase-change material
+    rsHs = p["rho_s"] * p["cp_s"] * p["T_sol"]
+    rlHl = p["rho_l"] * (p["cp_l"] * p["T_liq"] + p["latent"])
+    for rH in np.linspace(rsHs - 1.5, rlHl + 1.5, 41):
+        if rH < rsHs:
+            fl, T = 0.0, rH / (p["rho_s"] * p["cp_s"])
+        elif rH <= rlHl:
+            fl = (rH - rsHs) / (rlHl - rsHs)
+            T = p["T_sol"] + fl * (p["T_liq"] - p["T_sol"])
+        else:
+            fl, T = 1.0, p["T_liq"] + (rH - rlHl) / (p["rho_l"] * p["cp_l"])
+        T2, fs = oracle_mod.enthalpy_invert(p, rH, 1.0)
+        assert abs(T2 - T) < 1e-12 and abs(fs - (1 - fl)) < 1e-12
+    # continuity at the solidus and liquidus enthalpies, for any chi
+    for chi in (0.0, 0.3, 1.0):
+        for T in (p["T_sol"], p["T_liq"]):
+            e = oracle_mod.enthalpy_forward(p, T, chi)
+            lo, hi = oracle_mod.enthalpy_invert(p, e - 1e-9, chi), oracle_mod.enthalpy_invert(p, e + 1e-9, chi)
+            assert abs(lo[0] - hi[0]) < 1e-7 and abs(lo[1] - hi[1]) < 1e-7
+    # the gas never holds solid
+    assert oracle_mod.enthalpy_invert(p, -5.0, 0.0)[1] == 0.0
+
+
+def test_property_rule(oracle_mod):
+    # zeta(phi, f_s): liquid (1, 0), solid (1, 1), gas (-1, 0) -- end of Sec. 2
+    for (phi, fs, want) in ((1, 0, 2.0), (1, 1, 5.0), (-1, 0, 7.0), (0, 0, 4.5)):
+        assert abs(oracle_mod.zeta(phi, fs, 2.0, 5.0, 7.0) - want) < 1e-15
+
+
+# ------------------------------------------------------------------------------------------
+# Conservation laws
+# ------------------------------------------------------------------------------------------
+
+def test_phase_field_conservation(oracle_mod):
+    """Without phase change sum(phi) is conserved to round-off (Sec. 2, 'strictly
+    preserve mass conservation'), in a flow driven by surface tension."""
+    w = W.static_droplet(nx=40, ny=36, radius=10, rho_g=0.1)
+    # off-centre, so that the walls and the periodic seam see the flow
+    w["fields"]["phi"] = W.tanh_profile(10 - np.hypot(np.arange(40)[None, :] - 7.3, np.arange(36)[:, None] - 12.1))
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    s0 = o.reduce()[0]
+    o.step(300)
+    s1 = o.reduce()[0]
+    f = o.fields()
+    assert np.abs(f["ux"]).max() > 1e-6  # a real flow
+    assert abs(s1 - s0) <= 1e-12 * np.abs(f["phi"]).sum()
+
+
+def test_solute_conservation(oracle_mod):
+    """Eq. c is conservative and every wall is no-flux: sum(C) is constant, here
+    through freezing, Marangoni flow and volume change."""
+    w = W.parity_droplet(nx=48, ny=40)
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    c0 = o.reduce()[2]
+    o.step(200)
+    r = o.reduce()
+    assert r[3] > 1.0  # something froze
+    assert abs(r[2] - c0) <= 1e-11 * abs(c0)
+
+
+# ------------------------------------------------------------------------------------------
+# Analytic solutions printed in the paper
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ste", [0.1, 0.2])
+def test_neumann_front(oracle_mod, ste):
+    """Sec. 4.2: s(t) = 2 kappa sqrt(alpha_s t), here without volume change
+    (rho_s = rho_l) and T_0 = T_m, kappa from the transcendental equation."""
+    w = W.stefan_layer(nx=2, ny=160, h0=128, ste=ste, rho_ratio=1.0, rho_g=0.1)
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    kappa = A.neumann_kappa(ste)
+    alpha_s = w["params"]["lam_s"] / (w["params"]["rho_s"] * w["params"]["cp_s"])
+    for t in (1000, 2500):
+        o.step(t - o.steps)
+        s = o.reduce()[5]
+        assert abs(s / A.neumann_front(t, kappa, alpha_s) - 1) < 4e-3, (t, s)
+
+
+def test_neumann_superheated(oracle_mod):
+    """Same problem with a superheated liquid (T_0 > T_m): the second term of the
+    transcendental equation is active (alpha_r = 1, rho_r = 1)."""
+    ny = 400
+    w = W.stefan_layer(nx=2, ny=ny, h0=380, ste=0.2, rho_ratio=1.0, rho_g=0.1)
+    w["fields"]["T"][:] = 0.3
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    p = w["params"]
+    kappa = A.neumann_kappa(0.2, T0=0.3, Tm=0.0, Tw=-1.0, lam_s=p["lam_s"], lam_l=p["lam_l"])
+    assert kappa < A.neumann_kappa(0.2)
+    o.step(4000)
+    s = o.reduce()[5]
+    assert abs(s / A.neumann_front(4000, kappa, p["lam_s"]) - 1) < 1e-2, s
+
+
+def test_binary_solidification(oracle_mod):
+    """Sec. 4.3 without gas (phi = 1 everywhere; the model reduces to the classical
+    enthalpy method for a binary material): front, temperature and the solute
+    rejected at the front against the closed forms."""
+    ny, kp, C0, Dl, al = 300, 0.5, 0.1, 0.05, 0.3
+    p = W.base_params(rho_s=1.0, lam_l=al, lam_s=al, k_p=kp, D_l=Dl, D_s=0.0, latent=10.0,
+                      T_sol=0.0, T_liq=0.0, sigma0=0.0)
+    g = W.grid(2, ny, W.WALL_DIRICHLET_T, W.WALL_ADIABATIC, T_bottom=-1.0)
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, 2)), T=np.zeros((ny, 2)), C=np.full((ny, 2), C0)))
+    k = A.binary_stefan_k(1.0, 1.0, 10.0, 0.0, -1.0, 0.0, al, al)
+    t = 4000
+    o.step(t)
+    f, r = o.fields(), o.reduce()
+    y = np.arange(ny) + 0.5
+    Ta, Ca, s = A.binary_stefan_fields(y, t, k, -1.0, 0.0, 0.0, C0, kp, al, al, Dl)
+    assert abs(r[5] / s - 1) < 3e-3
+    assert np.abs(f["T"][:, 0] - Ta).max() < 0.03
+    assert abs(r[2] / 2 - C0 * ny) < 1e-10 * C0 * ny
+    # solute is rejected: depleted solid, enriched liquid ahead of the front,
+    # far field at C0.  The enthalpy method resolves the front by one cell,
+    # which smears the partition: the solid and the liquid peak are compared
+    # with a tolerance of 30% of the closed-form depletion and enrichment.
+    mid = int(s / 2)
+    assert abs(f["C"][mid, 0] - Ca[mid]) < 0.3 * (C0 - Ca[mid])
+    liq = y > s + 3
+    assert np.abs(f["C"][liq, 0] - Ca[liq]).max() < 0.3 * (Ca.max() - C0)
+    assert abs(f["C"][-1, 0] - C0) < 1e-6
+
+
+def test_laplace_jump(oracle_mod):
+    """Static droplet: the capillary force of Eq. Fs with delta = alpha |grad phi|^2,
+    alpha = 3 sqrt(2) eps / 4, gives the 2-D Laplace jump sigma / R.  The
+    isotropic gradient integrates |grad phi|^2 of the W = 4 profile to 0.939 of
+    its exact value, so that is the jump to expect on this lattice."""
+    N, R, sig = 48, 12.0, 0.01
+    w = W.static_droplet(nx=N, ny=N, radius=R, rho_g=1.0, sigma=sig)
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    o.step(6000)
+    f = o.fields()
+    c = N // 2
+    dp = f["p"][c - 2:c + 2, c - 2:c + 2].mean() - f["p"][:4, :4].mean()
+    j = np.arange(-40, 40) + 0.5
+    ph = np.tanh(j / 2.0)
+    d = (np.roll(ph, -1) - np.roll(ph, 1)) / 2.0
+    discrete = (3 * math.sqrt(2) * W.EPS / 4 * d[2:-2] ** 2).sum()
+    assert 0.93 < discrete < 0.945
+    assert abs(dp / (sig / R) / discrete - 1) < 0.03, dp / (sig / R)
+
+
+def test_stratified_marangoni(oracle_mod):
+    """Appendix A: layered thermocapillary flow, converged at L = 80, h = H = 20.
+    The temperature matches the closed form closely; the velocity within the
+    smearing of a 4-cell diffuse interface over a 20-cell layer."""
+    L, h = 80, 20
+    w = W.thermocapillary_channel(nx=L, ny=2 * h, h=h)
+    m = w["meta"]
+    o = oracle_mod.Oracle(w["grid"], w["params"], w["fields"])
+    o.step(4000)
+    f = o.fields()
+    y = np.arange(2 * h) + 0.5 - h
+    xq = L // 4
+    T, ux, _, Um = A.stratified_marangoni(xq, y, L, h, h, m["T_h"], m["T_c"], m["T_0"], m["sigma_T"], m["mu"])
+    assert np.abs(f["T"][:, xq] - T).max() < 1e-3
+    err = f["ux"][:, xq] - ux
+    assert np.sqrt((err ** 2).mean()) < 0.1 * Um
+    lobe = h // 3
+    assert 0.8 < f["ux"][lobe, xq] / ux[lobe] < 1.02
+    T, _, uy, _ = A.stratified_marangoni(0, y, L, h, h, m["T_h"], m["T_c"], m["T_0"], m["sigma_T"], m["mu"])
+    assert np.abs(f["uy"][:, 0] - uy).max() < 0.1 * Um
+    # flow goes from the hot to the cold part of the interface
+    assert f["ux"][h, L // 4] > 0 and f["ux"][h, 3 * L // 4] < 0
+
+
+def test_heat_conduction_decay(oracle_mod):
+    """Enthalpy set alone (no phase change, no flow): T(y, 0) = sin(pi (y+1/2)/ny)
+    between two Dirichlet walls at T = 0 decays as exp(-alpha (pi/ny)^2 t); the
+    two-relaxation-time collision with 1/tau_bar + 1/tau_tilde = 2 keeps the
+    anti-bounce-back walls exactly half-way."""
+    ny, lam = 40, 0.25
+    p = W.base_params(lam_l=lam, lam_s=lam, lam_g=lam, phase_change_on=0, latent=0.0, sigma0=0.0)
+    g = W.grid(2, ny, W.WALL_DIRICHLET_T, W.WALL_DIRICHLET_T)
+    y = np.arange(ny) + 0.5
+    T0 = np.repeat(np.sin(np.pi * y / ny)[:, None], 2, axis=1)
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, 2)), T=T0, C=np.zeros((ny, 2))))
+    t = 1500
+    o.step(t)
+    T = o.fields()["T"][:, 0]
+    want = np.exp(-lam * (np.pi / ny) ** 2 * t) * np.sin(np.pi * y / ny)
+    assert np.abs(T - want).max() < 2e-3 * want.max()
+
+
+def test_poiseuille(oracle_mod):
+    """Flow set alone: body force rho g between half-way bounce-back walls gives
+    the parabola g (y+1/2)(ny-y-1/2) / (2 nu)."""
+    ny, nu, gx = 24, 0.1, 1e-6
+    p = W.base_params(phase_change_on=0, latent=0.0, sigma0=0.0, gx=gx)
+    g = W.grid(2, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, 2)), T=np.zeros((ny, 2)), C=np.zeros((ny, 2))))
+    o.step(6000)
+    u = o.fields()["ux"][:, 0]
+    want = A.poiseuille(np.arange(ny), ny, gx, nu)
+    assert np.abs(u - want).max() < 5e-3 * want.max()
+
+
+def test_solid_drag(oracle_mod):
+    """The solid-liquid interaction force f = f_s (0 - u*) keeps a frozen region at
+    rest under the same body force that drives a Poiseuille flow."""
+    ny, gx = 24, 1e-6
+    p = W.base_params(sigma0=0.0, gx=gx)
+    g = W.grid(2, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, 2)), T=np.full((ny, 2), -0.5), C=np.zeros((ny, 2))))
+    o.step(3000)
+    f = o.fields()
+    assert f["fs"].min() > 1 - 1e-9
+    assert np.abs(f["ux"]).max() < 2 * gx
+
+
+def test_no_solid_reduction(oracle_mod):
+    """With every cell far above the melting point the phase-change model must
+    reduce to the plain two-phase model (Sec. 2, reduction consistency): no
+    solid, mdot = 0, and the same phase field, velocity and pressure.  (The
+    temperature is not compared: the latent enthalpy that the liquid holds is
+    not advected by Eq. Tem, whose flux is rho Cp T u, so where the interface
+    moves T differs from a run without latent heat.)"""
+    w = W.static_droplet(nx=32, ny=32, radius=9, rho_g=0.1)
+    w["fields"]["T"][:] = 5.0
+    w["grid"]["bc_bottom"] = W.WALL_ADIABATIC
+    a = dict(w["params"], phase_change_on=1, latent=3.0, T_sol=-1.0, T_liq=-1.0)
+    b = dict(w["params"], phase_change_on=0)
+    oa = oracle_mod.Oracle(w["grid"], a, w["fields"])
+    ob = oracle_mod.Oracle(w["grid"], b, w["fields"])
+    oa.step(200)
+    ob.step(200)
+    fa, fb = oa.fields(), ob.fields()
+    assert fa["fs"].max() == 0.0
+    for k in ("phi", "ux", "uy", "p"):
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_table1_final_height(oracle_mod):
+    """Table 1 (tests/golden): a film freezes completely in a closed box and its
+    final height is h_0 rho_l / rho_s by mass conservation.  In a closed box the
+    expansion can only compress the gas; the phase field follows that only
+    when its div u source is the velocity divergence (divu_mode = 1).  The
+    paper's own errors reach 7e-3; this lattice (a 16-cell film, 4-cell
+    interface, gas density 0.1) lands within 2.5%, with the right sign."""
+    rows = [list(map(float, r.split())) for r in _golden("table1_final_height.txt")]
+    for rr, analytic, *_ in rows:
+        assert abs(analytic - 1.0 / rr) < 1e-3
+    h0 = 16
+    for rr in (0.8, 0.9, 1.2):
+        w = W.stefan_layer(nx=2, ny=3 * h0, h0=h0, rho_ratio=rr, rho_g=0.1, ste=0.2)
+        o = oracle_mod.Oracle(w["grid"], dict(w["params"], divu_mode=1), w["fields"])
+        for _ in range(20):
+            o.step(500)
+            r = o.reduce()
+            if r[3] >= 0.999 * r[4]:
+                break
+        hf = r[5] / h0
+        analytic = [a for (x, a, *_) in rows if abs(x - rr) < 1e-9][0]
+        assert abs(hf / analytic - 1) < 0.025, (rr, hf)
+        assert (hf - 1) * (1 - rr) > 0
+
+
+def test_printed_ygb_velocity():
+    """The migration speed printed in Sec. 4.1 follows from the YGB formula."""
+    kv = dict(r.split("=") for r in _golden("printed_numbers.txt"))
+    kv = {k.strip(): float(v) for k, v in kv.items()}
+    u = A.ygb_velocity(-1e-4, 0.1, 20.0, 0.2, 0.2, 0.2, 0.2)
+    assert abs(u / kv["ygb_velocity"] - 1) < 1e-3
