@@ -1,0 +1,283 @@
+#!/usr/bin/env python
+"""Throughput of the fused diffuse-interface LB freezing step on GB300.
+
+Workload: the 4096 x 4096 planar freezing front advancing into a binary
+liquid (C0 = 0.05) toward an insoluble circular impurity of radius 200 cells
+(density ratio 2), Marangoni stresses on (Ma = 10), all four coupled D2Q9 sets
+active.  One step = one fused kernel launch over the whole lattice.
+
+Metric: MLUPS = lattice cells x steps / time / 1e6 (one update = one cell
+advancing all four sets by one step), with the HBM-roofline fraction of the
+step kernel against the measured copy bandwidth.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs its own lattice (replicas; the step
+has no data-path exchange in this form) and the whole-job MLUPS is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_UPDATE = 360  # 36 populations read + written, 9 lagged fields read + written, FP32
+WORKLOAD = dict(name="impurity_front", nx=4096, ny=4096)
+PROFILE = os.path.join(ROOT, "profiles", "lb_step_kernel_impurity_front.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2511_09422_gb300", "csrc", "lb_kernels.cuh")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_per_launch(cells: int):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, scaled
+    to this lattice; None if there is none or the kernel changed since."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    kv = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("kernel_source_sha256_16") != _kernel_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_cell"]) * cells
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 3 + i and r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+SAMPLE = "the same workload on a 1024x1024 lattice (impurity r=200 at (nx/2, ny/4), same parameters)"
+
+
+def _oracle_sample(steps_min: int, seconds: float):
+    """The FP64 oracle on a 1024 x 1024 lattice of the same workload, timed on
+    the host cores after one untimed step: returns (MLUPS, steps, cores, s)."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_09422_gb300 import workloads as W
+    w = W.impurity_front(nx=1024, ny=1024)
+    f = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in w["fields"].items()}
+    o = oracle.Oracle(w["grid"], w["params"], f)
+    o.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps_min or time.perf_counter() - t0 < seconds:
+        o.step(1)
+        n += 1
+        if n >= 10 * max(steps_min, 1):
+            break
+    dt = time.perf_counter() - t0
+    return 1024 * 1024 * n / dt / 1e6, n, oracle.oracle.num_threads(), dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    mlups, n, cores, dt = _oracle_sample(max(args.steps, 1), 0.0)
+    line = {
+        "impl": "reference", "metric": "MLUPS (all coupled fields)", "value": round(mlups, 3),
+        "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "impurity_front, FP64 CPU oracle on " + SAMPLE, "steps_timed": n},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d oracle steps on %s" % (n, SAMPLE)},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2511_09422_gb300 import lbfreeze
+    from paper_2511_09422_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    nx, ny = args.size, args.size
+    w = W.impurity_front(nx=nx, ny=ny, radius=200.0 * nx / 4096.0)
+    f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
+    cells = nx * ny
+    stream = torch.cuda.Stream()
+
+    # ---- device-resident throughput -------------------------------------------------------
+    solver = lbfreeze.Solver(w["grid"], w["params"], f32, stream=stream)
+    solver.step(args.warmup)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        solver.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    ms_total = e0.elapsed_time(e1)
+    red = solver.reduce()
+    solver.close()
+    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.barrier()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+    kernel_ms = ms_total / args.steps
+
+    # ---- end to end through the public API with host buffers -----------------------------
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s2 = lbfreeze.Solver(w["grid"], w["params"], f32, stream=stream)
+    for _ in range(args.steps):
+        s2.step(1)
+        s2.reduce()
+    out = s2.fields()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    s2.close()
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = ws * cells * args.steps / float(te.item()) / 1e6
+    h2d = 5 * 4 * cells / args.steps
+    d2h = 8 * 8 + 7 * 4 * cells / args.steps
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, src = _peaks()
+    achieved = BYTES_PER_UPDATE * cells / (kernel_ms * 1e-3) / 1e9
+    traffic = _traffic_per_launch(cells)
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        mlups, n, cores, dt = _oracle_sample(3, 10.0)
+        cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "%d FP64 oracle steps on %s (%.1f s)" % (n, SAMPLE, dt)}
+    line = {
+        "metric": "MLUPS (all coupled fields)", "value": round(value, 2), "unit": "MLUPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "impurity_front %dx%d (planar front + insoluble impurity r=%g, C0=0.05, Ma=10)"
+                               % (nx, ny, 200.0 * nx / 4096.0),
+                   "cells": cells, "l2": "working set %.1f GB >> L2 (inputs larger than L2)" % (cells * BYTES_PER_UPDATE / 2 / 1e9),
+                   "parallelism": "replica per GPU" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"),
+                     "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs"), 4),
+                     "peak_source": src, "bytes_per_update": BYTES_PER_UPDATE,
+                     "traffic": None if traffic is None else round(traffic)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d),
+                "d2h_bytes_per_step": round(d2h)},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "check": {"sum_phi": red[0], "sum_C": red[2], "front": red[5]},
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lbfreeze", choices=["lbfreeze", "reference"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

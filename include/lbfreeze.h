@@ -1,0 +1,164 @@
+/*
+ * lbfreeze.h -- C ABI of the GB300 (sm_103a) fused diffuse-interface lattice
+ * Boltzmann step for gas-liquid-solid freezing of a binary fluid with
+ * thermal and solutal Marangoni flow (Huang, Chai, Liu, Huang,
+ * arXiv 2511.09422).
+ *
+ * The library evolves, on one GPU, the four coupled D2Q9 distribution sets of
+ * Sec. 3 of the paper on a 2-D lattice:
+ *   f  conservative Allen-Cahn phase field (Sec. 3.1, Eq. ACE),
+ *   g  pressure-based flow with the solid-liquid interaction force and the
+ *      volume-change source (Sec. 3.2, Eqs. NS1-NS2),
+ *   h  total enthalpy, two-relaxation-time (Sec. 3.3, Eqs. Tem and Hfl),
+ *   l  solute with the pseudo-potential concentration (Sec. 3.4, Eq. c),
+ * coupled through the continuum surface force with Marangoni and capillary
+ * parts (Eq. Fs), the linear surface-tension equation of state, and the
+ * property rule zeta(phi, f_s) (end of Sec. 2).  Gradients use the isotropic
+ * schemes at the end of Sec. 3.4.  x is periodic; the walls at y = -1/2 and
+ * y = ny - 1/2 are half-way bounce-back (no slip, no flux) with
+ * anti-bounce-back for a Dirichlet temperature (Sec. 4.5).
+ *
+ * Conventions
+ *   - Fields are nx*ny arrays, row-major with x fastest: v[y*nx + x].
+ *   - All calls return an lb_status code; nothing throws across the ABI.
+ *   - A handle owns all of its device memory.  Pointers passed in are
+ *     borrowed for the duration of the call only.
+ *   - Work is enqueued on the handle's stream (the legacy default stream
+ *     until lb_set_stream).  lb_step is asynchronous; lb_get_fields with host
+ *     outputs, lb_reduce, lb_save and lb_load synchronise that stream.
+ *   - The first error is sticky: once a call has failed with LB_ERR_CUDA or
+ *     LB_ERR_UNSTABLE, later calls on the handle return the same code.
+ *   - Arithmetic is FP32 with FP64 global sums.
+ */
+#ifndef LBFREEZE_H
+#define LBFREEZE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_INVALID_ARG = 1, /* null pointer, empty or oversized lattice, tau <= 1/2, eps <= 0 ... */
+    LB_ERR_CUDA = 2,        /* a CUDA runtime call failed (message via lb_last_error) */
+    LB_ERR_OOM = 3,         /* device allocation failed */
+    LB_ERR_UNSTABLE = 4     /* a non-finite value was produced by the step */
+} lb_status;
+
+#define LB_WALL_DIRICHLET_T 0 /* anti-bounce-back to the wall temperature */
+#define LB_WALL_ADIABATIC 1   /* bounce-back for the enthalpy as well */
+
+/* Lattice and walls (problem statement, Sec. 2, Fig. 1; boundary
+ * treatment of Sec. 4.5).  The bottom-wall temperature may vary along x as
+ * T_bottom + T_bottom_amp * cos(2 pi T_bottom_modes x / nx) (the heated
+ * channel of Sec. 4.1), with cell centres at integer x. */
+typedef struct {
+    int nx, ny;             /* 1 <= nx, ny; nx*ny <= LB_MAX_CELLS */
+    int bc_bottom, bc_top;  /* LB_WALL_DIRICHLET_T or LB_WALL_ADIABATIC */
+    double T_bottom, T_top;
+    double T_bottom_amp;
+    int T_bottom_modes;
+} lb_grid;
+
+#define LB_MAX_CELLS (1L << 28)
+
+/* Model constants (Sec. 2 and 3).  Suffix _l liquid, _s solid, _g the
+ * surrounding phase (phi = -1).  mu is the dynamic viscosity, lam the
+ * conductivity, cp the specific heat; the property rule interpolates rho,
+ * mu, lam and the volumetric heat capacity rho*cp.  latent is L of
+ * H = Cp T + L f_l; T_sol, T_liq the solidus and liquidus; k_p the partition
+ * coefficient and D_l, D_s the solute diffusivities of Eq. c; eps the
+ * interface parameter of Eq. 3 and mobility M of Eq. ACE
+ * (tau_f = 1/2 + M/cs^2); sigma0, sigma_T, sigma_c, T_ref, c_ref the linear
+ * equation of state sigma = sigma0 + sigma_T (T - T_ref) + sigma_c (C - c_ref);
+ * (gx, gy) the body-force acceleration (F_b = rho g).
+ * fs_modulated_st: 1 multiplies the surface force by (1 - f_s) (Sec. 4.5).
+ * phase_change_on: 0 drops the latent heat and keeps f_s = 0.
+ * divu_mode: 0 takes div u = mdot (the model value of Eq. NS1) in the
+ * phase-field and enthalpy sources; other values are rejected. */
+typedef struct {
+    double rho_l, rho_s, rho_g;
+    double mu_l, mu_s, mu_g;
+    double lam_l, lam_s, lam_g;
+    double cp_l, cp_s, cp_g;
+    double latent, T_sol, T_liq;
+    double k_p, D_l, D_s;
+    double eps, mobility;
+    double sigma0, sigma_T, sigma_c, T_ref, c_ref;
+    double gx, gy;
+    int fs_modulated_st, phase_change_on;
+    int divu_mode;
+} lb_params;
+
+/* Initial fields, nx*ny floats each, host or device memory (on_device = 0/1).
+ * ux, uy may be NULL (fluid at rest). */
+typedef struct {
+    const float *phi, *T, *C, *ux, *uy;
+    int on_device;
+} lb_fields;
+
+typedef struct lb_handle lb_handle;
+
+/* Allocate the state and initialise it at rest in time: post-streaming
+ * populations equal to the equilibria of the initial fields with p = 0,
+ * the enthalpy from (T, chi) by the inverse of Eq. Hfl.
+ * Returns LB_ERR_INVALID_ARG for null pointers, nx or ny < 1, nx*ny above
+ * LB_MAX_CELLS, eps <= 0, non-positive densities, a relaxation time <= 1/2
+ * anywhere in the property range, or divu_mode != 0.  *out is set only on
+ * success.  Synchronises the device. */
+lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init,
+                    lb_handle **out);
+
+/* Use a CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work of the handle; NULL selects the legacy default stream. */
+lb_status lb_set_stream(lb_handle *h, void *cuda_stream);
+
+/* Enqueue n >= 0 time steps (one fused kernel launch each).  Asynchronous. */
+lb_status lb_step(lb_handle *h, int n);
+
+/* Macroscopic fields of the current state -- the values the next step
+ * computes before it collides: order parameter phi, temperature T, solid
+ * fraction f_s, concentration C, velocity (ux, uy), pressure p.  Each output
+ * is nx*ny floats, host or device memory as on_device says; any may be NULL.
+ * With host outputs the call synchronises the stream. */
+lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C, float *ux,
+                        float *uy, float *p, int on_device);
+
+/* Global diagnostics of the current state in FP64, summed in a fixed order:
+ *   out[0] sum phi     out[1] sum rho H    out[2] sum C     out[3] sum f_s
+ *   out[4] sum chi, chi = clamp((1 + phi)/2, 0, 1)
+ *   out[5] front height: sum over y of f_s on the column x = nx/2
+ *   out[6] V*_s  = sum f_s / V_0     out[7] V*_sl = sum chi / V_0
+ * with V_0 = sum chi of the initial state.  Synchronises the stream; returns
+ * LB_ERR_UNSTABLE if the step has produced a non-finite value. */
+lb_status lb_reduce(lb_handle *h, double out[8]);
+
+/* Number of steps taken since lb_create (or restored by lb_load). */
+lb_status lb_steps_taken(lb_handle *h, long *out);
+
+/* Checkpoint: write / read the complete state (populations, lagged fields,
+ * step count, V_0) of the handle to / from a file.  lb_load requires a file
+ * written for the same nx, ny; the result continues bit-for-bit as the saved
+ * run would have.  Both synchronise the stream. */
+lb_status lb_save(lb_handle *h, const char *path);
+lb_status lb_load(lb_handle *h, const char *path);
+
+/* Free the handle and its device memory; NULL is a no-op. */
+void lb_destroy(lb_handle *h);
+
+/* Static description of a status code. */
+const char *lb_error_string(int status);
+
+/* Message of the last failure on this handle (or of the last failed
+ * lb_create when h is NULL); never NULL. */
+const char *lb_last_error(const lb_handle *h);
+
+/* Device bytes held by the handle. */
+size_t lb_device_bytes(const lb_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -453,9 +453,16 @@ static void cell_dynamics(const orc_state *st, int x, int y, cell_out *o)
      * same chi-weighted mixture that the enthalpy relation uses. */
     double rhocp = orc_zeta(phi, fs, p->rho_l * p->cp_l, p->rho_s * p->cp_s, p->rho_g * p->cp_g);
 
-    /* unit normal n = grad phi / |grad phi|, regularised where grad phi = 0 */
+    /* unit normal n = grad phi / |grad phi| (Eq. 1), undefined where
+     * grad phi = 0.  Regularised as grad phi / sqrt(|grad phi|^2 + 1e-6): the
+     * normal only matters in the interface, where the counter term's factor
+     * (1 - phi^2)/(sqrt2 eps) equals |grad phi| on the equilibrium profile, so
+     * for |phi| < 0.99 the normal is unbiased to better than 1%; away from the
+     * interface the product (1 - phi^2) n fades smoothly instead of taking a
+     * random direction from round-off gradients, which would make the scheme
+     * amplify 1e-7 perturbations to 1e-3 within 100 steps. */
     double g2 = gpx * gpx + gpy * gpy;
-    double inv = 1.0 / sqrt(g2 + 1e-12);
+    double inv = 1.0 / sqrt(g2 + 1e-6);
     double nx_ = gpx * inv, ny_ = gpy * inv;
 
     /* chemical potential with phi1 = 1, phi2 = -1, k = 1, beta = 1/(4 eps^2):

@@ -1,0 +1,419 @@
+// lb_api.cu -- host side of the C ABI declared in include/lbfreeze.h.
+//
+// Owns the device state of one lattice (double-buffered populations and
+// lagged fields, a field buffer for read-back, FP64 reduction partials) and
+// launches the kernels of lb_kernels.cuh on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "lb_kernels.cuh"
+#include "lbfreeze.h"
+
+using lbk::Consts;
+
+struct lb_handle {
+    lb_grid grid;
+    lb_params params;
+    Consts K;
+    float *pops[2] = {nullptr, nullptr};
+    float *aux[2] = {nullptr, nullptr};
+    float *fields = nullptr;     // 7 planes
+    double *partials = nullptr;  // reduction partials, red_blocks * NRED
+    double *red_out = nullptr;   // NRED doubles on the device
+    unsigned *status = nullptr;
+    int red_blocks = 0;
+    int cur = 0;
+    cudaStream_t stream = nullptr;
+    double V0 = 0.0;
+    long steps = 0;
+    lb_status sticky = LB_OK;
+    std::string err;
+    size_t bytes = 0;
+};
+
+static std::string g_create_error = "";
+
+static const char *k_status_text[] = {"ok", "invalid argument", "CUDA error", "out of device memory",
+                                      "unstable: a non-finite value was produced"};
+
+extern "C" const char *lb_error_string(int status)
+{
+    if (status < 0 || status > 4) return "unknown status";
+    return k_status_text[status];
+}
+
+extern "C" const char *lb_last_error(const lb_handle *h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" size_t lb_device_bytes(const lb_handle *h) { return h ? h->bytes : 0; }
+
+static lb_status fail(lb_handle *h, lb_status s, const std::string &msg)
+{
+    if (h) {
+        if (h->sticky == LB_OK && (s == LB_ERR_CUDA || s == LB_ERR_UNSTABLE)) h->sticky = s;
+        h->err = msg;
+    } else {
+        g_create_error = msg;
+    }
+    return s;
+}
+
+static lb_status cuda_fail(lb_handle *h, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, m);
+}
+
+#define CK(h, call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------
+// Parameter checks: every relaxation time must stay above 1/2 over the whole
+// property range (phi in [-1, 1], f_s in [0, 1]).
+// ---------------------------------------------------------------------------------------
+static bool finite_all(const lb_params *p)
+{
+    const double v[] = {p->rho_l, p->rho_s, p->rho_g, p->mu_l, p->mu_s, p->mu_g, p->lam_l, p->lam_s, p->lam_g,
+                        p->cp_l, p->cp_s, p->cp_g, p->latent, p->T_sol, p->T_liq, p->k_p, p->D_l, p->D_s,
+                        p->eps, p->mobility, p->sigma0, p->sigma_T, p->sigma_c, p->T_ref, p->c_ref, p->gx, p->gy};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+static std::string check_params(const lb_grid *g, const lb_params *p)
+{
+    if (g->nx < 1 || g->ny < 1) return "nx and ny must be >= 1";
+    if ((long)g->nx * (long)g->ny > LB_MAX_CELLS) return "lattice larger than LB_MAX_CELLS";
+    if (g->bc_bottom < 0 || g->bc_bottom > 1 || g->bc_top < 0 || g->bc_top > 1) return "unknown wall type";
+    if (!finite_all(p)) return "non-finite parameter";
+    if (!(p->eps > 0)) return "eps must be > 0";
+    if (!(p->rho_l > 0 && p->rho_s > 0 && p->rho_g > 0)) return "densities must be > 0";
+    if (!(p->cp_l > 0 && p->cp_s > 0 && p->cp_g > 0)) return "heat capacities must be > 0";
+    if (!(p->mobility > 0)) return "mobility must be > 0 (tau_f > 1/2)";
+    if (!(p->mu_l > 0 && p->mu_s > 0 && p->mu_g > 0)) return "viscosities must be > 0 (tau_g > 1/2)";
+    if (!(p->lam_l > 0 && p->lam_s > 0 && p->lam_g > 0)) return "conductivities must be > 0 (tau_h > 1/2)";
+    if (!(p->D_l > 0) || p->D_s < 0) return "D_l must be > 0 and D_s >= 0 (tau_l > 1/2 in the liquid)";
+    if (!(p->k_p > 0)) return "k_p must be > 0";
+    if (p->divu_mode != 0) return "divu_mode must be 0";
+    if (p->phase_change_on && p->T_liq < p->T_sol) return "T_liq < T_sol";
+    return "";
+}
+
+static Consts make_consts(const lb_grid *g, const lb_params *p)
+{
+    Consts K;
+    memset(&K, 0, sizeof(K));
+    K.nx = g->nx;
+    K.ny = g->ny;
+    K.pitch = (g->nx + 31) / 32 * 32;
+    K.plane = (long long)K.pitch * g->ny;
+    K.bc_bottom = g->bc_bottom;
+    K.bc_top = g->bc_top;
+    K.T_bottom = (real)g->T_bottom;
+    K.T_top = (real)g->T_top;
+    K.T_bottom_amp = (real)g->T_bottom_amp;
+    K.wall_k = (real)(2.0 * g->T_bottom_modes / g->nx);
+    K.rho_l = (real)p->rho_l; K.rho_s = (real)p->rho_s; K.rho_g = (real)p->rho_g;
+    K.mu_l = (real)p->mu_l; K.mu_s = (real)p->mu_s; K.mu_g = (real)p->mu_g;
+    K.lam_l = (real)p->lam_l; K.lam_s = (real)p->lam_s; K.lam_g = (real)p->lam_g;
+    K.rcp_l = (real)(p->rho_l * p->cp_l);
+    K.rcp_s = (real)(p->rho_s * p->cp_s);
+    K.rcp_g = (real)(p->rho_g * p->cp_g);
+    K.latent_l = (real)(p->rho_l * p->latent);
+    K.lat_l = p->phase_change_on ? K.latent_l : 0.0f;
+    K.T_sol = (real)p->T_sol; K.T_liq = (real)p->T_liq;
+    K.k_p = (real)p->k_p; K.D_l = (real)p->D_l; K.D_s = (real)p->D_s;
+    K.rr = (real)(p->rho_l * 2.0 * p->cp_s * p->cp_l / (p->cp_s + p->cp_l));
+    K.inv_eps2 = (real)(1.0 / (p->eps * p->eps));
+    K.inv_s2eps = (real)(1.0 / (std::sqrt(2.0) * p->eps));
+    K.alpha = (real)(3.0 * std::sqrt(2.0) * p->eps / 4.0);
+    K.tau_f = (real)(0.5 + 3.0 * p->mobility);
+    K.sigma0 = (real)p->sigma0; K.sigma_T = (real)p->sigma_T; K.sigma_c = (real)p->sigma_c;
+    K.T_ref = (real)p->T_ref; K.c_ref = (real)p->c_ref;
+    K.gx = (real)p->gx; K.gy = (real)p->gy;
+    K.expand = (real)(1.0 - p->rho_s / p->rho_l);
+    K.fs_mod = p->fs_modulated_st ? 1 : 0;
+    K.phase_change = p->phase_change_on ? 1 : 0;
+    return K;
+}
+
+static dim3 step_grid(const Consts &K)
+{
+    return dim3((K.nx + LB_TX - 1) / LB_TX, (K.ny + LB_TY - 1) / LB_TY, 1);
+}
+
+static int flat_blocks(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    long long cap = 152LL * 8;
+    return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
+{
+    const Consts &K = h->K;
+    lbk::lb_reduce_partial_kernel<<<h->red_blocks, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
+                                                                                    h->partials);
+    CK(h, cudaGetLastError());
+    lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_blocks, h->red_out);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * lbk::NRED, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+static void free_all(lb_handle *h)
+{
+    void *ptrs[] = {h->pops[0], h->pops[1], h->aux[0], h->aux[1], h->fields, h->partials, h->red_out, h->status};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init, lb_handle **out)
+{
+    if (!grid || !params || !init || !out) return fail(nullptr, LB_ERR_INVALID_ARG, "null argument");
+    std::string why = check_params(grid, params);
+    if (!why.empty()) return fail(nullptr, LB_ERR_INVALID_ARG, why);
+    if (!init->phi || !init->T || !init->C) return fail(nullptr, LB_ERR_INVALID_ARG, "initial phi, T and C are required");
+
+    lb_handle *h = new lb_handle();
+    h->grid = *grid;
+    h->params = *params;
+    h->K = make_consts(grid, params);
+    const Consts &K = h->K;
+    const long long n = (long long)grid->nx * grid->ny;
+    const size_t plane_b = sizeof(float) * (size_t)K.plane;
+    h->red_blocks = flat_blocks(n, lbk::RED_THREADS);
+
+    auto alloc = [&](void **p, size_t b) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, b);
+        if (e == cudaSuccess) h->bytes += b;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->pops[k], 36 * plane_b);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->aux[k], lbk::NAUX * plane_b);
+    if (e == cudaSuccess) e = alloc((void **)&h->fields, 7 * plane_b);
+    if (e == cudaSuccess) e = alloc((void **)&h->partials, sizeof(double) * lbk::NRED * h->red_blocks);
+    if (e == cudaSuccess) e = alloc((void **)&h->red_out, sizeof(double) * lbk::NRED);
+    if (e == cudaSuccess) e = alloc((void **)&h->status, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        lb_status s = cuda_fail(nullptr, e, "cudaMalloc");
+        cudaGetLastError();
+        free_all(h);
+        delete h;
+        return s;
+    }
+
+    // initial fields on the device (the field buffer serves as staging)
+    const float *src[5] = {init->phi, init->T, init->C, init->ux, init->uy};
+    const float *dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    lb_status st = LB_OK;
+    do {
+        cudaError_t me = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
+        if (me != cudaSuccess) { st = cuda_fail(h, me, "cudaMemsetAsync"); break; }
+        for (int k = 0; k < 5; k++) {
+            if (!src[k]) continue;
+            float *d = h->fields + (size_t)k * K.plane;
+            cudaError_t ce = cudaMemcpyAsync(d, src[k], sizeof(float) * n,
+                                             init->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+            if (ce != cudaSuccess) { st = cuda_fail(h, ce, "copy of the initial fields"); break; }
+            dev[k] = d;
+        }
+        if (st != LB_OK) break;
+        float *eq = h->pops[1];
+        lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4], eq,
+                                                                           h->aux[0]);
+        lbk::lb_init_unstream_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0], h->pops[0]);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) { st = cuda_fail(h, ce, "init kernels"); break; }
+        h->cur = 0;
+        double r[lbk::NRED];
+        st = launch_reduce(h, r);
+        if (st != LB_OK) break;
+        h->V0 = r[4];
+    } while (0);
+    if (st != LB_OK) {
+        g_create_error = h->err;
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_set_stream(lb_handle *h, void *cuda_stream)
+{
+    if (!h) return LB_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)cuda_stream;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_step(lb_handle *h, int n)
+{
+    if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
+    if (h->sticky != LB_OK) return h->sticky;
+    const dim3 grid = step_grid(h->K), block(32, LB_WARPS, 1);
+    for (int s = 0; s < n; s++) {
+        lbk::Buffers B;
+        B.pin = h->pops[h->cur];
+        B.pout = h->pops[1 - h->cur];
+        B.ain = h->aux[h->cur];
+        B.aout = h->aux[1 - h->cur];
+        B.fields = nullptr;
+        B.status = h->status;
+        lbk::lb_step_kernel<lbk::MODE_STEP><<<grid, block, lbk::STEP_SMEM, h->stream>>>(h->K, B);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
+        h->cur = 1 - h->cur;
+        h->steps++;
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_steps_taken(lb_handle *h, long *out)
+{
+    if (!h || !out) return LB_ERR_INVALID_ARG;
+    *out = h->steps;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C, float *ux, float *uy,
+                                   float *p, int on_device)
+{
+    if (!h) return LB_ERR_INVALID_ARG;
+    if (h->sticky != LB_OK) return h->sticky;
+    const Consts &K = h->K;
+    lbk::Buffers B;
+    B.pin = h->pops[h->cur];
+    B.pout = nullptr;
+    B.ain = h->aux[h->cur];
+    B.aout = nullptr;
+    B.fields = h->fields;
+    B.status = h->status;
+    lbk::lb_step_kernel<lbk::MODE_FIELDS><<<step_grid(K), dim3(32, LB_WARPS, 1), lbk::STEP_SMEM, h->stream>>>(K, B);
+    CK(h, cudaGetLastError());
+    float *dst[7] = {phi, T, fs, C, ux, uy, p};
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < 7; k++) {
+        if (!dst[k]) continue;
+        CK(h, cudaMemcpy2DAsync(dst[k], sizeof(float) * K.nx, h->fields + (size_t)k * K.plane, sizeof(float) * K.pitch,
+                                sizeof(float) * K.nx, K.ny, kind, h->stream));
+    }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_reduce(lb_handle *h, double out[8])
+{
+    if (!h || !out) return fail(h, LB_ERR_INVALID_ARG, "null argument");
+    if (h->sticky != LB_OK) return h->sticky;
+    double r[lbk::NRED];
+    lb_status s = launch_reduce(h, r);
+    if (s != LB_OK) return s;
+    unsigned status = 0;
+    CK(h, cudaMemcpyAsync(&status, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 6; k++) out[k] = r[k];
+    out[6] = h->V0 > 0 ? r[3] / h->V0 : 0.0;
+    out[7] = h->V0 > 0 ? r[4] / h->V0 : 0.0;
+    bool finite = true;
+    for (int k = 0; k < 6; k++) finite = finite && std::isfinite(r[k]);
+    if (status || !finite) return fail(h, LB_ERR_UNSTABLE, "non-finite value in the lattice state");
+    return LB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Checkpoint: header + raw planes (populations, lagged fields) of the current buffer.
+// ---------------------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, pitch;
+    long steps;
+    double V0;
+};
+
+extern "C" lb_status lb_save(lb_handle *h, const char *path)
+{
+    if (!h || !path) return fail(h, LB_ERR_INVALID_ARG, "null argument");
+    if (h->sticky != LB_OK) return h->sticky;
+    const Consts &K = h->K;
+    const size_t np = 36 * (size_t)K.plane, na = lbk::NAUX * (size_t)K.plane;
+    float *buf = (float *)malloc(sizeof(float) * (np + na));
+    if (!buf) return fail(h, LB_ERR_INVALID_ARG, "host allocation for the checkpoint failed");
+    cudaError_t e = cudaMemcpyAsync(buf, h->pops[h->cur], sizeof(float) * np, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + np, h->aux[h->cur], sizeof(float) * na, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        free(buf);
+        return cuda_fail(h, e, "checkpoint read-back");
+    }
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        free(buf);
+        return fail(h, LB_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    }
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBFRZ01", 8);
+    hd.version = 1; hd.nx = K.nx; hd.ny = K.ny; hd.pitch = K.pitch; hd.steps = h->steps; hd.V0 = h->V0;
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf, sizeof(float), np + na, f) == np + na;
+    ok = (fclose(f) == 0) && ok;
+    free(buf);
+    return ok ? LB_OK : fail(h, LB_ERR_INVALID_ARG, std::string("write failed: ") + path);
+}
+
+extern "C" lb_status lb_load(lb_handle *h, const char *path)
+{
+    if (!h || !path) return fail(h, LB_ERR_INVALID_ARG, "null argument");
+    if (h->sticky != LB_OK) return h->sticky;
+    const Consts &K = h->K;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(h, LB_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    CkptHeader hd;
+    if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBFRZ01", 8) != 0 || hd.nx != K.nx || hd.ny != K.ny ||
+        hd.pitch != K.pitch) {
+        fclose(f);
+        return fail(h, LB_ERR_INVALID_ARG, "checkpoint does not match this lattice");
+    }
+    const size_t np = 36 * (size_t)K.plane, na = lbk::NAUX * (size_t)K.plane;
+    float *buf = (float *)malloc(sizeof(float) * (np + na));
+    if (!buf) {
+        fclose(f);
+        return fail(h, LB_ERR_INVALID_ARG, "host allocation for the checkpoint failed");
+    }
+    bool ok = fread(buf, sizeof(float), np + na, f) == np + na;
+    fclose(f);
+    if (!ok) {
+        free(buf);
+        return fail(h, LB_ERR_INVALID_ARG, "truncated checkpoint");
+    }
+    cudaError_t e = cudaMemcpyAsync(h->pops[h->cur], buf, sizeof(float) * np, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->aux[h->cur], buf + np, sizeof(float) * na, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    free(buf);
+    if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint upload");
+    h->steps = hd.steps;
+    h->V0 = hd.V0;
+    return LB_OK;
+}
+
+extern "C" void lb_destroy(lb_handle *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}

@@ -1,0 +1,779 @@
+// lb_kernels.cuh -- sm_103a kernels of the fused diffuse-interface LB freezing step.
+//
+// One launch of lb_step_kernel advances the whole lattice by one time step of
+// the four coupled D2Q9 sets of arXiv 2511.09422, Sec. 3: phase field f
+// (BGK, Sec. 3.1), pressure-based flow g (BGK, Sec. 3.2), total enthalpy h
+// (two-relaxation-time, Sec. 3.3) and solute l (BGK, Sec. 3.4).
+//
+// Memory layout (HBM): structure of arrays.  Every population direction and
+// every lagged field is a plane of pitch*ny floats (row pitch a multiple of
+// 32 floats, so each warp row access is one aligned 128-byte line).  The
+// state is double-buffered: the kernel pulls post-collision populations of
+// the previous step from buffer A (stream-then-collide, "pull" form) and
+// writes this step's post-collision populations to buffer B at the own cell.
+// Lagged fields (plane index):
+//   0 f_s  1 Q = rho Cp T div u  2 u_x  3 u_y  4 phi  5 C  6 p  7 S  8 T
+// are read from A and written to B the same way.
+//
+// Storage form.  The phase-field, flow and enthalpy populations are stored
+// as deviations from a reference rebuilt exactly on reading, so that FP32
+// rounding at storage applies to the small non-equilibrium part instead of
+// the whole value:
+//   f_i   stored as f_i* - w_i phi^n(s)
+//   g_i   stored as g_i* - 3 p^n(s) (w_i - [i = 0])
+//   h_i   stored as h_i* - w_i rr T^n(s)                     (i > 0)
+//   h_0   stored as h_0* - w_0 rr T^n(s) - rho_l L (chi(phi^n(s)) - f_s^n(s))
+// with s the cell that wrote the value, rr = rho_ref Cp_ref, and phi^n, p^n,
+// T^n, f_s^n the lagged fields written by the same step.  The step's
+// arithmetic carries phi, p and T as (lagged value, small change) pairs, so
+// that the large parts -- phi ~ 1, the pressure, T, and the latent enthalpy
+// ~ rho_l L -- cancel analytically instead of in FP32.
+//
+// Tiling: a CTA of 32 x LB_WARPS threads owns an interior tile of 30 x LB_TY
+// cells.  Phase A computes, for the tile plus a one-cell halo (32 x (LB_TY+2)
+// cells, one warp row of 32 lanes per lattice row), the local fields of the
+// step -- T, f_s, mdot, phi, C -- from the pulled populations and stores them
+// with the lagged p and S in shared memory.  Phase B then forms, for the
+// interior cells, the isotropic gradients from shared memory, the forces,
+// velocity and pressure, and collides the four sets.  The halo is recomputed
+// by both neighbouring tiles instead of being exchanged; its population reads
+// are L2 hits, so DRAM sees each byte about once.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// Compute type of the step's arithmetic (storage is FP32 regardless).
+#ifndef LB_REAL
+#define LB_REAL float
+#endif
+typedef LB_REAL real;
+#define R(x) ((real)(x))
+
+#ifndef LB_WARPS
+#define LB_WARPS 8
+#endif
+#ifndef LB_TY
+#define LB_TY 30
+#endif
+#define LB_TX 30
+#define LB_EXT_W 32
+#define LB_EXT_H (LB_TY + 2)
+
+namespace lbk {
+
+// ---------------------------------------------------------------------------------------
+// D2Q9: 0 rest; 1 (+1,0) 2 (0,+1) 3 (-1,0) 4 (0,-1); 5 (+1,+1) 6 (-1,+1) 7 (-1,-1) 8 (+1,-1)
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int cy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
+__host__ __device__ constexpr real wgt(int i) { return i == 0 ? (R(4.0) / R(9.0)) : (i <= 4 ? (R(1.0) / R(9.0)) : (R(1.0) / R(36.0))); }
+
+constexpr int SET_F = 0, SET_G = 1, SET_H = 2, SET_L = 3;
+constexpr int AUX_FS = 0, AUX_Q = 1, AUX_UX = 2, AUX_UY = 3, AUX_PHI = 4, AUX_C = 5, AUX_P = 6, AUX_S = 7, AUX_T = 8;
+constexpr int NAUX = 9;
+constexpr int WALL_DIRICHLET = 0;
+
+// Constants of one run, precomputed on the host from lb_params.
+struct Consts {
+    int nx, ny, pitch;
+    long long plane;          // floats per plane (pitch * ny)
+    int bc_bottom, bc_top;
+    real T_bottom, T_top, T_bottom_amp, wall_k;  // wall_k = 2 * modes / nx (argument of cospi)
+    real rho_l, rho_s, rho_g, mu_l, mu_s, mu_g, lam_l, lam_s, lam_g;
+    real rcp_l, rcp_s, rcp_g;   // volumetric heat capacities rho*Cp
+    real latent_l;              // rho_l * L
+    real lat_l;                 // rho_l * L if phase change is on, else 0 (latent reference of h_0)
+    real T_sol, T_liq, k_p, D_l, D_s;
+    real rr;                    // rho_ref Cp_ref
+    real inv_eps2, inv_s2eps, alpha;
+    real tau_f;
+    real sigma0, sigma_T, sigma_c, T_ref, c_ref, gx, gy;
+    real expand;                // 1 - rho_s / rho_l
+    int fs_mod, phase_change;
+};
+
+struct Buffers {
+    const float *__restrict__ pin;
+    float *__restrict__ pout;
+    const float *__restrict__ ain;
+    float *__restrict__ aout;
+    float *__restrict__ fields;  // 7 planes, fields mode only
+    unsigned *status;
+};
+
+__device__ __forceinline__ real zeta(real phi, real fs, real zl, real zs, real zg)
+{
+    return R(0.5) * phi * (zl - zg) + fs * (zs - zl) + R(0.5) * (zl + zg);
+}
+
+__device__ __forceinline__ int wrapx(int x, int nx)
+{
+    return x < 0 ? x + nx : (x >= nx ? x - nx : x);
+}
+
+__device__ __forceinline__ real clamp01(real v) { return fmin(fmax(v, R(0.0)), R(1.0)); }
+
+// Bottom-wall temperature at continuous abscissa x.
+__device__ __forceinline__ real wall_T_bottom(const Consts &K, real x)
+{
+    return K.T_bottom_amp == R(0.0) ? K.T_bottom : K.T_bottom + K.T_bottom_amp * cospi(K.wall_k * x);
+}
+
+// Enthalpy -> (T, f_s) of Eq. Hfl with chi-weighted solidus / liquidus
+// enthalpies (Eq. Hfl at chi = 1), f_s in [0, chi].  The enthalpy is passed
+// as rho H = ed + rr T_p + rho_l L (chi_p - fs_p) with ed small, and chi with
+// its change dchi = chi - chi_p formed from small terms, so that e - E_l,
+// e - E_s and T - T_p are free of the large magnitudes.  Returns dT = T - T_p.
+__device__ __forceinline__ void invert_enthalpy(const Consts &K, real ed, real T_p, real chi_p, real fs_p, real chi,
+                                                real dchi, real &dT, real &fs)
+{
+    const real Al = chi * K.rcp_l + (R(1.0) - chi) * K.rcp_g;
+    if (!K.phase_change) {
+        dT = (ed + (K.rr - Al) * T_p) / Al;
+        fs = R(0.0);
+        return;
+    }
+    const real As = chi * K.rcp_s + (R(1.0) - chi) * K.rcp_g;
+    const real lat_p = K.lat_l * (chi_p - fs_p);
+    const real em_s = ed + K.rr * T_p + lat_p - As * K.T_sol;                   // e - E_s
+    const real em_l = ed + K.rr * T_p - K.lat_l * (dchi + fs_p) - Al * K.T_liq;  // e - E_l
+    if (em_s < R(0.0)) {
+        fs = chi;
+        dT = (ed + lat_p + (K.rr - As) * T_p) / As;
+    } else if (em_l > R(0.0)) {
+        fs = R(0.0);
+        dT = (ed - K.lat_l * (dchi + fs_p) + (K.rr - Al) * T_p) / Al;
+    } else {
+        const real d = Al * K.T_liq - As * K.T_sol + chi * K.latent_l;
+        const real r = (d < R(1e-14) * fmax(R(1.0), fabs(em_s))) ? R(1.0) : em_s / d;
+        fs = chi * (R(1.0) - r);
+        dT = (K.T_sol - T_p) + r * (K.T_liq - K.T_sol);
+    }
+}
+
+// Forward map (T, chi) -> sensible enthalpy e - rho_l L (chi - f_s) and f_s;
+// T exactly at T_s = T_l counts as liquid.
+__device__ __forceinline__ real forward_sensible(const Consts &K, real T, real chi, real &fs)
+{
+    const real Al = chi * K.rcp_l + (R(1.0) - chi) * K.rcp_g;
+    if (!K.phase_change) {
+        fs = R(0.0);
+        return Al * T;
+    }
+    const real As = chi * K.rcp_s + (R(1.0) - chi) * K.rcp_g;
+    if (T >= K.T_liq) {
+        fs = R(0.0);
+        return Al * T;
+    }
+    if (T < K.T_sol) {
+        fs = chi;
+        return As * T;
+    }
+    const real r = (T - K.T_sol) / (K.T_liq - K.T_sol);
+    fs = chi * (R(1.0) - r);
+    return As * K.T_sol + r * (Al * K.T_liq - As * K.T_sol);
+}
+
+// Pull one stored post-collision population of set S into direction I at cell
+// (x, y): from (x - c_I) in the bulk; from the own cell's opposite direction
+// at a wall (half-way bounce-back).  For the enthalpy at a Dirichlet wall the
+// anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (wall temperature at the
+// link midpoint) is applied in deviation form relative to w rr T_own.
+template <int S, int I>
+__device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
+                                     real T_own)
+{
+    constexpr int ys_off = -cy(I);
+    const int ys = y + ys_off;
+    if (ys_off != 0 && (ys < 0 || ys >= K.ny)) {
+        real v = __ldg(pin + (long long)(S * 9 + opp(I)) * K.plane + cell);
+        if (S == SET_H) {
+            const bool bottom = ys < 0;
+            if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
+                real Tw = bottom ? wall_T_bottom(K, (real)x - R(0.5) * (real)cx(I)) : K.T_top;
+                v = -v + R(2.0) * wgt(I) * K.rr * (Tw - T_own);
+            }
+        }
+        return v;
+    }
+    const int xs = wrapx(x - cx(I), K.nx);
+    return __ldg(pin + (long long)(S * 9 + I) * K.plane + (long long)ys * K.pitch + xs);
+}
+
+template <int S>
+__device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell, real v[9],
+                                      real T_own = R(0.0))
+{
+    v[0] = pull<S, 0>(K, pin, x, y, cell, T_own);
+    v[1] = pull<S, 1>(K, pin, x, y, cell, T_own);
+    v[2] = pull<S, 2>(K, pin, x, y, cell, T_own);
+    v[3] = pull<S, 3>(K, pin, x, y, cell, T_own);
+    v[4] = pull<S, 4>(K, pin, x, y, cell, T_own);
+    v[5] = pull<S, 5>(K, pin, x, y, cell, T_own);
+    v[6] = pull<S, 6>(K, pin, x, y, cell, T_own);
+    v[7] = pull<S, 7>(K, pin, x, y, cell, T_own);
+    v[8] = pull<S, 8>(K, pin, x, y, cell, T_own);
+}
+
+// Lagged field (plane A) of the cell that wrote the population pulled into
+// direction I at (x, y) (the own cell at a wall).
+template <int A, int I>
+__device__ __forceinline__ real aux_src(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell)
+{
+    constexpr int ys_off = -cy(I);
+    const int ys = y + ys_off;
+    const float *a = ain + (long long)A * K.plane;
+    if (ys_off != 0 && (ys < 0 || ys >= K.ny)) return __ldg(a + cell);
+    return __ldg(a + (long long)ys * K.pitch + wrapx(x - cx(I), K.nx));
+}
+
+// sum_{i>0} w_i (z^n(source_i) - z^n(x)) of a lagged field: the reference
+// offsets of the pulled deviations relative to the own lagged value.
+template <int A>
+__device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell,
+                                            real own)
+{
+    return (wgt(1) * (aux_src<A, 1>(K, ain, x, y, cell) - own) + wgt(2) * (aux_src<A, 2>(K, ain, x, y, cell) - own) +
+            wgt(3) * (aux_src<A, 3>(K, ain, x, y, cell) - own) + wgt(4) * (aux_src<A, 4>(K, ain, x, y, cell) - own)) +
+           (wgt(5) * (aux_src<A, 5>(K, ain, x, y, cell) - own) + wgt(6) * (aux_src<A, 6>(K, ain, x, y, cell) - own) +
+            wgt(7) * (aux_src<A, 7>(K, ain, x, y, cell) - own) + wgt(8) * (aux_src<A, 8>(K, ain, x, y, cell) - own));
+}
+
+__device__ __forceinline__ real sum9(const real v[9])
+{
+    return v[0] + ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
+}
+
+// Local fields of one cell (Sec. 3.1, 3.3, 3.4, Eq. Hfl, Eq. NS1):
+//   sum f = phi_p + delta, rho H = ed + rr T_p + rho_l L (chi_p - fs_p)
+//   (ed includes Q^{n-1}/2), chi = clamp((1 + sum f)/2), (T, f_s) from the
+//   enthalpy, mdot = (1 - rho_s/rho_l)(f_s - f_s^{n-1}),
+//   phi = sum f / (1 - mdot/2) = phi_p + dphi, C = sum l.
+struct Local {
+    real dT, fs, mdot, dphi, C;
+};
+
+__device__ __forceinline__ Local local_fields(const Consts &K, real phi_p, real delta, real ed, real T_p, real chi_p,
+                                              real fs_p, real sl)
+{
+    Local o;
+    const real sf = phi_p + delta;
+    const real hs = R(0.5) * (R(1.0) + sf), hp = R(0.5) * (R(1.0) + phi_p);
+    const real chi = clamp01(hs);
+    const bool inside = hs >= R(0.0) && hs <= R(1.0) && hp >= R(0.0) && hp <= R(1.0);
+    const real dchi = inside ? R(0.5) * delta : chi - chi_p;
+    invert_enthalpy(K, ed, T_p, chi_p, fs_p, chi, dchi, o.dT, o.fs);
+    o.mdot = K.phase_change ? K.expand * (o.fs - fs_p) : R(0.0);
+    o.dphi = (delta + R(0.5) * o.mdot * phi_p) / (R(1.0) - R(0.5) * o.mdot);
+    o.C = sl;
+    return o;
+}
+
+// Phase-A work for one cell: pull f, h, l and the lagged values it needs.
+struct CellA {
+    Local L;
+    real ed, chi_p, fs_p, phi_p, T_p;
+};
+
+__device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict__ pin, const float *__restrict__ ain,
+                                        int x, int y, long long cell)
+{
+    CellA c;
+    real v[9];
+    c.phi_p = __ldg(ain + AUX_PHI * K.plane + cell);
+    c.T_p = __ldg(ain + AUX_T * K.plane + cell);
+    c.fs_p = __ldg(ain + AUX_FS * K.plane + cell);
+    c.chi_p = clamp01(R(0.5) * (R(1.0) + c.phi_p));
+    pull9<SET_F>(K, pin, x, y, cell, v);
+    const real delta = sum9(v) + aux_dev_sum<AUX_PHI>(K, ain, x, y, cell, c.phi_p);
+    pull9<SET_H>(K, pin, x, y, cell, v, c.T_p);
+    const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
+    c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
+    pull9<SET_L>(K, pin, x, y, cell, v);
+    const real sl = sum9(v);
+    c.L = local_fields(K, c.phi_p, delta, c.ed, c.T_p, c.chi_p, c.fs_p, sl);
+    return c;
+}
+
+// Shared-memory tile: the step's local fields on the tile plus a one-cell halo.
+struct Tile {
+    real phip[LB_EXT_H][LB_EXT_W];  // lagged phi (reference of the stored f deviations)
+    real dphi[LB_EXT_H][LB_EXT_W];  // phi - phi_p
+    real Tp[LB_EXT_H][LB_EXT_W];    // lagged T (reference of the stored h deviations)
+    real dT[LB_EXT_H][LB_EXT_W];    // T - T_p
+    real C[LB_EXT_H][LB_EXT_W];
+    real fs[LB_EXT_H][LB_EXT_W];
+    real p[LB_EXT_H][LB_EXT_W];
+    real S[LB_EXT_H][LB_EXT_W];
+    real mdot[LB_EXT_H][LB_EXT_W];
+};
+
+enum { MODE_STEP = 0, MODE_FIELDS = 1 };
+
+// ---------------------------------------------------------------------------------------
+// The fused step.  MODE_FIELDS runs the same arithmetic up to velocity and
+// pressure and stores the macroscopic fields instead of colliding.
+// ---------------------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, const Buffers B)
+{
+    extern __shared__ __align__(16) unsigned char lb_smem[];
+    Tile &t = *reinterpret_cast<Tile *>(lb_smem);
+    const int lane = threadIdx.x;
+    const int warp = threadIdx.y;
+    const int x0 = blockIdx.x * LB_TX;
+    const int y0 = blockIdx.y * LB_TY;
+    const int ex = x0 - 1 + lane;        // unwrapped abscissa of this lane
+    const int xg = ((ex % K.nx) + K.nx) % K.nx;
+    const float *__restrict__ pin = B.pin;
+    const float *__restrict__ ain = B.ain;
+
+    // ---- phase A: local fields on the extended tile ------------------------------------
+    for (int r = warp; r < LB_EXT_H; r += LB_WARPS) {
+        const int y = y0 - 1 + r;
+        if (y < 0 || y >= K.ny) continue;
+        const long long cell = (long long)y * K.pitch + xg;
+        const CellA c = cell_a(K, pin, ain, xg, y, cell);
+        t.phip[r][lane] = c.phi_p;
+        t.dphi[r][lane] = c.L.dphi;
+        t.Tp[r][lane] = c.T_p;
+        t.dT[r][lane] = c.L.dT;
+        t.C[r][lane] = c.L.C;
+        t.fs[r][lane] = c.L.fs;
+        t.mdot[r][lane] = c.L.mdot;
+        t.p[r][lane] = __ldg(ain + AUX_P * K.plane + cell);
+        t.S[r][lane] = __ldg(ain + AUX_S * K.plane + cell);
+    }
+    __syncthreads();
+
+    // ---- phase B: gradients, forces, velocity, pressure, collision ----------------------
+    if (lane == 0 || lane == LB_EXT_W - 1 || ex >= K.nx) return;
+    const int x = ex;
+    const real rr = K.rr;
+    for (int r = 1 + warp; r <= LB_TY; r += LB_WARPS) {
+        const int y = y0 - 1 + r;
+        if (y >= K.ny) break;
+        const long long cell = (long long)y * K.pitch + x;
+        const bool at_bottom = (y == 0), at_top = (y == K.ny - 1);
+        const int rs = at_bottom ? r : r - 1;  // south row (mirror ghost at the bottom wall)
+        const int rn = at_top ? r : r + 1;     // north row
+        const bool dir_b = at_bottom && K.bc_bottom == WALL_DIRICHLET;
+        const bool dir_t = at_top && K.bc_top == WALL_DIRICHLET;
+
+        // own fields: phi = phi_p + dphi, T = T_p + dT; phi_st, T_st are the values
+        // written to the lagged fields, which are also the references of the stored
+        // deviations (the parts below the FP32 spacing stay in those deviations)
+        const real phi_p = t.phip[r][lane], dphi = t.dphi[r][lane];
+        const real phi_st = (real)(float)(phi_p + dphi);
+        const real phi_lo = (phi_p - phi_st) + dphi;  // phi - phi_st
+        const real phi = phi_st + phi_lo;
+        const real T_p = t.Tp[r][lane], dT = t.dT[r][lane];
+        const real T_st = (real)(float)(T_p + dT);
+        const real T_lo = (T_p - T_st) + dT;          // T - T_st
+        const real T = T_st + T_lo;
+        const real C = t.C[r][lane], fs = (real)(float)t.fs[r][lane];
+        const real mdot = t.mdot[r][lane];
+
+        // isotropic gradient and Laplacian over the 8 neighbours (order 1..8), from
+        // differences z_i - z_0: grad z = 3 sum w_i c_i (z_i - z_0), lap z = 6 sum w_i (z_i - z_0).
+        // phi and T differences are split into lagged-value and change parts.  Wall rows
+        // are ghosts: mirror, or 2 T_w - T_adjacent for the temperature at a Dirichlet wall.
+        real gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, gPx, gPy, gSx, gSy;
+        {
+            const int lc[9] = {lane, lane + 1, lane, lane - 1, lane, lane + 1, lane - 1, lane - 1, lane + 1};
+            const int rw[9] = {r, r, rn, r, rs, rn, rn, rs, rs};
+            const real f0 = t.fs[r][lane], P0 = t.p[r][lane], S0 = t.S[r][lane];
+            real sx[6] = {0, 0, 0, 0, 0, 0}, sy[6] = {0, 0, 0, 0, 0, 0}, sl = R(0.0);
+#pragma unroll
+            for (int i = 1; i < 9; i++) {
+                const int a = rw[i], b = lc[i];
+                const real zph = (t.phip[a][b] - phi_p) + (t.dphi[a][b] - dphi);
+                real zT = (t.Tp[a][b] - T_p) + (t.dT[a][b] - dT);
+                if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
+                    const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
+                    // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
+                    zT = R(2.0) * (Tw - t.Tp[a][b]) + (t.Tp[a][b] - T_p) - (t.dT[a][b] + dT);
+                }
+                const real zv[6] = {zph, zT, t.C[a][b] - C, t.fs[a][b] - f0, t.p[a][b] - P0, t.S[a][b] - S0};
+                const real wcx = wgt(i) * (real)cx(i), wcy = wgt(i) * (real)cy(i);
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    sx[k] += wcx * zv[k];
+                    sy[k] += wcy * zv[k];
+                }
+                sl += R(2.0) * wgt(i) * zph;
+            }
+            gpx = R(3.0) * sx[0]; gpy = R(3.0) * sy[0]; lphi = R(3.0) * sl;
+            gTx = R(3.0) * sx[1]; gTy = R(3.0) * sy[1];
+            gCx = R(3.0) * sx[2]; gCy = R(3.0) * sy[2];
+            gfx = R(3.0) * sx[3]; gfy = R(3.0) * sy[3];
+            gPx = R(3.0) * sx[4]; gPy = R(3.0) * sy[4];
+            gSx = R(3.0) * sx[5]; gSy = R(3.0) * sy[5];
+        }
+
+        // properties by the linear rule; the density gradient follows from it exactly
+        const real rho = zeta(phi, fs, K.rho_l, K.rho_s, K.rho_g);
+        const real mu = zeta(phi, fs, K.mu_l, K.mu_s, K.mu_g);
+        const real lam = zeta(phi, fs, K.lam_l, K.lam_s, K.lam_g);
+        const real rhocp = zeta(phi, fs, K.rcp_l, K.rcp_s, K.rcp_g);
+        const real dr_phi = R(0.5) * (K.rho_l - K.rho_g), dr_fs = K.rho_s - K.rho_l;
+        const real grx = dr_phi * gpx + dr_fs * gfx, gry = dr_phi * gpy + dr_fs * gfy;
+
+        // normal, chemical potential, surface tension and its gradient
+        const real g2 = gpx * gpx + gpy * gpy;
+        const real inv = rsqrt(g2 + R(1e-6));  // regularised normal: smooth away from the interface
+        const real nxv = gpx * inv, nyv = gpy * inv;
+        // chemical potential: the cubic term and the Laplacian nearly cancel across the
+        // interface, so this short expression is evaluated in FP64
+        const double phd = (double)phi_p + (double)dphi;
+        const real muphi = (real)((phd * phd * phd - phd) * (double)K.inv_eps2 - (double)lphi);
+        const real sigma = K.sigma0 + K.sigma_T * (T - K.T_ref) + K.sigma_c * (C - K.c_ref);
+        const real gsx = K.sigma_T * gTx + K.sigma_c * gCx;
+        const real gsy = K.sigma_T * gTy + K.sigma_c * gCy;
+
+        // Eq. Fs: Marangoni part alpha (|grad phi|^2 grad sigma - (grad sigma . grad phi) grad phi)
+        // plus capillary part alpha sigma mu_phi grad phi, times (1 - f_s) when modulated
+        const real gsgp = gsx * gpx + gsy * gpy;
+        real Fsx = K.alpha * (g2 * gsx - gsgp * gpx) + K.alpha * sigma * muphi * gpx;
+        real Fsy = K.alpha * (g2 * gsy - gsgp * gpy) + K.alpha * sigma * muphi * gpy;
+        if (K.fs_mod) {
+            Fsx *= (R(1.0) - fs);
+            Fsy *= (R(1.0) - fs);
+        }
+        const real Fx = Fsx + rho * K.gx, Fy = Fsy + rho * K.gy;
+
+        // flow set: velocity and pressure (Sec. 3.2).  g is stored as deviations from
+        // 3 p^n(s) (w_i - [i = 0]); dg_i = g_i - 3 p_p (w_i - [i = 0]) with p_p the own
+        // lagged pressure, so that the momentum and the pressure are sums of small terms
+        const real p_p = t.p[r][lane];
+        real g[9], dg[9];
+        pull9<SET_G>(K, pin, x, y, cell, g);
+        real jx = R(0.0), jy = R(0.0), sg = R(0.0);
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const int ys = y - cy(i);
+            const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+            const real pps = (i == 0 || wall) ? p_p : t.p[r - cy(i)][lane - cx(i)];
+            dg[i] = g[i] + R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0))) * (pps - p_p);
+            jx += (real)cx(i) * dg[i];
+            jy += (real)cy(i) * dg[i];
+            if (i) sg += dg[i];
+        }
+        const real inv_rho = R(1.0) / rho;
+        const real usx = (jx + R(0.5) * Fx) * inv_rho, usy = (jy + R(0.5) * Fy) * inv_rho;
+        const real ffx = -fs * usx, ffy = -fs * usy;       // f = f_s (0 - u*)
+        const real ux = usx + R(0.5) * ffx, uy = usy + R(0.5) * ffy;
+        const real rfx = rho * ffx, rfy = rho * ffy;
+        const real S = rho * mdot + ux * grx + uy * gry;
+        const real Ftx = Fx - gPx + (R(1.0) / R(3.0)) * grx + (R(1.0) / R(3.0)) * gSx;
+        const real Fty = Fy - gPy + (R(1.0) / R(3.0)) * gry + (R(1.0) / R(3.0)) * gSy;
+        const real tau_g = R(0.5) + R(3.0) * mu * inv_rho;
+        const real uu = ux * ux + uy * uy;
+        const real uF = ux * Ftx + uy * Fty;
+        const real G0 = wgt(0) * (S - R(3.0) * uF);
+        const real s0 = wgt(0) * (-R(1.5) * uu);
+        // p = c_s^2/(1 - w_0) [sum_{i>0} g_i + S/2 + tau G_0 + rho s_0(u)] = p_p + dp
+        const real dp = (R(1.0) / R(3.0)) / (R(1.0) - wgt(0)) * (sg + R(0.5) * S + tau_g * G0 + rho * s0);
+        const real p_st = (real)(float)(p_p + dp);
+        const real p_lo = (p_p - p_st) + dp;  // p - p_st
+        const real pr = p_st + p_lo;
+
+        if (MODE == MODE_FIELDS) {
+            float *o = B.fields;
+            const long long P = K.plane;
+            o[0 * P + cell] = phi;
+            o[1 * P + cell] = T;
+            o[2 * P + cell] = fs;
+            o[3 * P + cell] = C;
+            o[4 * P + cell] = ux;
+            o[5 * P + cell] = uy;
+            o[6 * P + cell] = pr;
+            continue;
+        }
+
+        const real om_g = R(1.0) / tau_g, src_g = R(1.0) - R(0.5) * om_g;
+        float *__restrict__ pout = B.pout;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            // deviations from 3 p_st (w_i - [i = 0]), the reference of the stored value
+            const real wp = R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0)));
+            const real d = dg[i] + wp * (p_p - p_st);
+            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+            const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
+            const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+            const real deq = wp * p_lo + rho * si;
+            const real Gi = wgt(i) * (S + R(3.0) * ((real)cx(i) * (Fx + rfx) + (real)cy(i) * (Fy + rfy)) +
+                                       R(9.0) * (cu * cF - (R(1.0) / R(3.0)) * uF));
+            pout[(long long)(SET_G * 9 + i) * K.plane + cell] = d - (d - deq) * om_g + src_g * Gi;
+        }
+
+        // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
+        {
+            const real ux_p = __ldg(ain + AUX_UX * K.plane + cell), uy_p = __ldg(ain + AUX_UY * K.plane + cell);
+            const real kf = (R(1.0) / R(3.0)) * (R(1.0) - phi * phi) * K.inv_s2eps;
+            const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
+            const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
+            const real om = R(1.0) / K.tau_f, src = R(1.0) - R(0.5) * om;
+            // d_i = f_i - w_i phi_st: the stored deviation plus w_i (phi^n(source) - phi_st);
+            // stored as f_i* - w_i phi_st
+            real f[9];
+            pull9<SET_F>(K, pin, x, y, cell, f);
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const int ys = y - cy(i);
+                const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+                const real php = wall ? phi_p : t.phip[r - cy(i)][lane - cx(i)];
+                const real d = f[i] + wgt(i) * (php - phi_st);
+                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+                const real deq = wgt(i) * (phi_lo + phi * R(3.0) * cu);  // f_eq - w_i phi_st
+                const real Fi = wgt(i) * R(3.0) * ((real)cx(i) * ax + (real)cy(i) * ay) + wgt(i) * phi * mdot;
+                pout[(long long)(SET_F * 9 + i) * K.plane + cell] = d - (d - deq) * om + src * Fi;
+            }
+
+            // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
+            const real C_p = __ldg(ain + AUX_C * K.plane + cell);
+            const real keff = R(1.0) - fs * (R(1.0) - K.k_p);
+            const real De = fs * K.k_p * K.D_s + (R(1.0) - fs) * K.D_l;
+            const real tau_l = R(0.5) + R(3.0) * De / keff;
+            const real om_l = R(1.0) / tau_l, src_l = R(1.0) - R(0.5) * om_l;
+            const real Rx = (R(1.0) - phi) * C * nxv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfx / keff;
+            const real Ry = (R(1.0) - phi) * C * nyv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfy / keff;
+            const real bx = (C * ux - C_p * ux_p) + (R(1.0) / R(3.0)) * Rx;
+            const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
+            real l[9];
+            pull9<SET_L>(K, pin, x, y, cell, l);
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+                const real leq = wgt(i) * C * (R(1.0) + R(3.0) * cu);
+                const real Li = wgt(i) * R(3.0) * ((real)cx(i) * bx + (real)cy(i) * by);
+                pout[(long long)(SET_L * 9 + i) * K.plane + cell] = l[i] - (l[i] - leq) * om_l + src_l * Li;
+            }
+        }
+
+        // enthalpy set (Sec. 3.3), two relaxation times: antisymmetric part with
+        // tau_bar = 1/2 + lam/(rho_ref Cp_ref cs2), symmetric part with 1/tau_tilde = 2 - 1/tau_bar;
+        // isotropic source w_i Q weighted with (1 - 1/(2 tau_tilde)).  Everything is formed as
+        // deviations from w_i rr T_st (and the latent reference for i = 0).
+        const real Q = rhocp * T * mdot;
+        {
+            const real tau_hb = R(0.5) + R(3.0) * lam / rr;
+            const real om_a = R(1.0) / tau_hb, om_s = R(2.0) - om_a;
+            const real src_h = R(1.0) - R(0.5) * om_s;
+            const real rcT = rhocp * T;
+            real h[9], dh[9], deq[9];
+            pull9<SET_H>(K, pin, x, y, cell, h, T_p);
+#pragma unroll
+            for (int i = 1; i < 9; i++) {
+                const int ys = y - cy(i);
+                const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+                const real Tps = wall ? T_p : t.Tp[r - cy(i)][lane - cx(i)];
+                dh[i] = h[i] + wgt(i) * rr * (Tps - T_st);  // h_i - w_i rr T_st
+                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+                deq[i] = wgt(i) * (rr * T_lo + rcT * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+            }
+#pragma unroll
+            for (int i = 1; i < 9; i++) {
+                const int j = opp(i);
+                const real hs = R(0.5) * (dh[i] + dh[j]), ha = R(0.5) * (dh[i] - dh[j]);
+                const real es = R(0.5) * (deq[i] + deq[j]), ea = R(0.5) * (deq[i] - deq[j]);
+                pout[(long long)(SET_H * 9 + i) * K.plane + cell] =
+                    dh[i] - (ha - ea) * om_a - (hs - es) * om_s + src_h * wgt(i) * Q;
+            }
+            // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
+            // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
+            // moves from w_0 rr T_p + rho_l L (chi_p - fs_p) to w_0 rr T_st + rho_l L (chi_st - f_s)
+            {
+                const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
+                const real fs_p = __ldg(ain + AUX_FS * K.plane + cell);
+                const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
+                const real chi_n = clamp01(R(0.5) * (R(1.0) + phi_st));
+                // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
+                real snz = R(0.0);
+#pragma unroll
+                for (int i = 1; i < 9; i++) snz += dh[i];
+                const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
+                const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
+                pout[(long long)(SET_H * 9 + 0) * K.plane + cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
+            }
+        }
+
+        // lagged fields for the next step
+        float *__restrict__ aout = B.aout;
+        aout[AUX_FS * K.plane + cell] = fs;
+        aout[AUX_Q * K.plane + cell] = Q;
+        aout[AUX_UX * K.plane + cell] = ux;
+        aout[AUX_UY * K.plane + cell] = uy;
+        aout[AUX_PHI * K.plane + cell] = (float)phi_st;
+        aout[AUX_C * K.plane + cell] = C;
+        aout[AUX_P * K.plane + cell] = (float)p_st;
+        aout[AUX_S * K.plane + cell] = S;
+        aout[AUX_T * K.plane + cell] = (float)T_st;
+
+        // a non-finite value anywhere in the cell's new state is reported once
+        if (!isfinite(T + phi + C + ux + uy + pr)) atomicOr(B.status, 1u);
+    }
+}
+
+constexpr size_t STEP_SMEM = sizeof(Tile);
+
+// ---------------------------------------------------------------------------------------
+// Initialisation: equilibria of the initial fields (p = 0), written in natural
+// (post-streaming) layout to `eq`, h as deviations from w_i rr T (with the
+// latent reference for i = 0), and the lagged fields of a state at rest in time.
+// ---------------------------------------------------------------------------------------
+__global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0, const float *__restrict__ T0,
+                                  const float *__restrict__ C0, const float *__restrict__ ux0,
+                                  const float *__restrict__ uy0, float *__restrict__ eq, float *__restrict__ aux)
+{
+    const long long n = (long long)K.nx * K.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / K.nx), x = (int)(k % K.nx);
+        const long long cell = (long long)y * K.pitch + x;
+        const real phi = phi0[k], T = T0[k], C = C0[k];
+        const real ux = ux0 ? ux0[k] : R(0.0), uy = uy0 ? uy0[k] : R(0.0);
+        const real chi = clamp01(R(0.5) * (R(1.0) + phi));
+        real fs;
+        const real e_sens = forward_sensible(K, T, chi, fs);
+        const real rho = zeta(phi, fs, K.rho_l, K.rho_s, K.rho_g);
+        const real rhocp = zeta(phi, fs, K.rcp_l, K.rcp_s, K.rcp_g);
+        const real uu = ux * ux + uy * uy;
+        const real rcT = rhocp * T;
+#pragma unroll
+        for (int i = 0; i < 9; i++) {
+            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+            const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+            eq[(long long)(SET_F * 9 + i) * K.plane + cell] = wgt(i) * phi * (R(1.0) + R(3.0) * cu);
+            eq[(long long)(SET_G * 9 + i) * K.plane + cell] = rho * si;
+            eq[(long long)(SET_L * 9 + i) * K.plane + cell] = wgt(i) * C * (R(1.0) + R(3.0) * cu);
+            // h_0 - w_0 rr T - latent = e_sens - rr T - w_0 rho Cp T 3u.u/2;  h_i - w_i rr T = w_i rho Cp T (...)
+            eq[(long long)(SET_H * 9 + i) * K.plane + cell] =
+                i == 0 ? e_sens - K.rr * T - wgt(0) * rcT * R(1.5) * uu
+                       : wgt(i) * rcT * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        }
+        aux[AUX_FS * K.plane + cell] = fs;
+        aux[AUX_Q * K.plane + cell] = 0.0f;
+        aux[AUX_UX * K.plane + cell] = ux;
+        aux[AUX_UY * K.plane + cell] = uy;
+        aux[AUX_PHI * K.plane + cell] = phi;
+        aux[AUX_C * K.plane + cell] = C;
+        aux[AUX_P * K.plane + cell] = 0.0f;
+        aux[AUX_S * K.plane + cell] = 0.0f;
+        aux[AUX_T * K.plane + cell] = T;
+    }
+}
+
+// Inverse streaming: the stored state is post-collision, so the initial
+// post-streaming populations `eq` are placed where the next pull finds them,
+// f and h as deviations from the references of the cell that holds them.
+__global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict__ eq, const float *__restrict__ aux,
+                                        float *__restrict__ pops)
+{
+    const long long n = (long long)K.nx * K.ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / K.nx), x = (int)(k % K.nx);
+        const long long cell = (long long)y * K.pitch + x;
+        const real phi_here = aux[AUX_PHI * K.plane + cell];
+        const real T_here = aux[AUX_T * K.plane + cell];
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+#pragma unroll
+            for (int i = 0; i < 9; i++) {
+                const int yt = y + cy(i);
+                real v;
+                if (yt < 0 || yt >= K.ny) {
+                    v = eq[(long long)(s * 9 + opp(i)) * K.plane + cell];
+                    if (s == SET_H) {
+                        const bool bottom = yt < 0;
+                        if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
+                            // stored h_i(x) = 2 w rr T_w - h_eq_opp(x), as a deviation from w rr T(x)
+                            real Tw = bottom ? wall_T_bottom(K, (real)x + R(0.5) * (real)cx(i)) : K.T_top;
+                            v = R(2.0) * wgt(i) * K.rr * (Tw - T_here) - v;
+                        }
+                    }
+                } else {
+                    const int xt = wrapx(x + cx(i), K.nx);
+                    const long long ct = (long long)yt * K.pitch + xt;
+                    v = eq[(long long)(s * 9 + i) * K.plane + ct];
+                    if (s == SET_H && i != 0) v += wgt(i) * K.rr * ((real)aux[AUX_T * K.plane + ct] - T_here);
+                }
+                if (s == SET_F) v -= wgt(i) * phi_here;
+                pops[(long long)(s * 9 + i) * K.plane + cell] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagnostics: FP64 sums of phi, rho H, C, f_s, chi and the front column.
+// Pass 1 writes one partial per block (fixed order); pass 2 adds them in order.
+// ---------------------------------------------------------------------------------------
+constexpr int NRED = 6;
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) lb_reduce_partial_kernel(const Consts K, const float *__restrict__ pin,
+                                                                         const float *__restrict__ ain,
+                                                                         double *__restrict__ partials)
+{
+    __shared__ double sh[RED_THREADS / 32][NRED];
+    const long long n = (long long)K.nx * K.ny;
+    const int xc = K.nx / 2;
+    double acc[NRED] = {0, 0, 0, 0, 0, 0};
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / K.nx), x = (int)(k % K.nx);
+        const long long cell = (long long)y * K.pitch + x;
+        const CellA c = cell_a(K, pin, ain, x, y, cell);
+        const Local &L = c.L;
+        const double phid = (double)c.phi_p + (double)L.dphi;
+        acc[0] += phid;
+        acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
+        acc[2] += (double)L.C;
+        acc[3] += (double)L.fs;
+        acc[4] += (double)clamp01(R(0.5) * (R(1.0) + (real)phid));
+        if (x == xc) acc[5] += (double)L.fs;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED; q++) {
+        double s = warp_sum(acc[q]);
+        if (lane == 0) sh[w][q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        double s = 0.0;
+        for (int j = 0; j < RED_THREADS / 32; j++) s += sh[j][threadIdx.x];
+        partials[(long long)blockIdx.x * NRED + threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) lb_reduce_final_kernel(const double *__restrict__ partials, int nblocks,
+                                                                       double *__restrict__ out)
+{
+    __shared__ double sh[RED_THREADS / 32][NRED];
+    double acc[NRED] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < NRED; q++) acc[q] += partials[(long long)b * NRED + q];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NRED; q++) {
+        double s = warp_sum(acc[q]);
+        if (lane == 0) sh[w][q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < NRED) {
+        double s = 0.0;
+        for (int j = 0; j < RED_THREADS / 32; j++) s += sh[j][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+}  // namespace lbk

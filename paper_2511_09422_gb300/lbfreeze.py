@@ -1,0 +1,240 @@
+"""Thin ctypes binding of the C ABI in ``include/lbfreeze.h`` (``liblbfreeze.so``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device memory for inputs and outputs can be torch CUDA tensors
+(their data pointers are passed through) and the stream a torch stream.
+There is no CPU fallback: ``load()`` raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+LB_OK, LB_ERR_INVALID_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_UNSTABLE = 0, 1, 2, 3, 4
+FIELD_NAMES = ("phi", "T", "fs", "C", "ux", "uy", "p")
+REDUCE_NAMES = ("sum_phi", "sum_rhoH", "sum_C", "sum_fs", "sum_chi", "front", "Vs", "Vsl")
+
+
+class LbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("lbfreeze status %d: %s" % (status, msg))
+        self.status = status
+
+
+class lb_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc_bottom", C.c_int), ("bc_top", C.c_int),
+                ("T_bottom", C.c_double), ("T_top", C.c_double), ("T_bottom_amp", C.c_double),
+                ("T_bottom_modes", C.c_int)]
+
+
+_PARAM_DOUBLES = ("rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lam_l", "lam_s", "lam_g",
+                  "cp_l", "cp_s", "cp_g", "latent", "T_sol", "T_liq", "k_p", "D_l", "D_s", "eps",
+                  "mobility", "sigma0", "sigma_T", "sigma_c", "T_ref", "c_ref", "gx", "gy")
+_PARAM_INTS = ("fs_modulated_st", "phase_change_on", "divu_mode")
+
+
+class lb_params(C.Structure):
+    _fields_ = [(k, C.c_double) for k in _PARAM_DOUBLES] + [(k, C.c_int) for k in _PARAM_INTS]
+
+
+_fp = C.POINTER(C.c_float)
+
+
+class lb_fields(C.Structure):
+    _fields_ = [("phi", _fp), ("T", _fp), ("C", _fp), ("ux", _fp), ("uy", _fp), ("on_device", C.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = ("lb_create", "lb_set_stream", "lb_step", "lb_get_fields", "lb_reduce", "lb_steps_taken",
+           "lb_save", "lb_load", "lb_destroy", "lb_error_string", "lb_last_error", "lb_device_bytes")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load liblbfreeze.so; raises if it has not been built (``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("liblbfreeze.so is not built (%s); run __graft_entry__.build()" % path)
+        L = C.CDLL(path)
+        L.lb_create.restype = C.c_int
+        L.lb_create.argtypes = [C.POINTER(lb_grid), C.POINTER(lb_params), C.POINTER(lb_fields), C.POINTER(C.c_void_p)]
+        L.lb_set_stream.restype = C.c_int
+        L.lb_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.lb_step.restype = C.c_int
+        L.lb_step.argtypes = [C.c_void_p, C.c_int]
+        L.lb_get_fields.restype = C.c_int
+        L.lb_get_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 7 + [C.c_int]
+        L.lb_reduce.restype = C.c_int
+        L.lb_reduce.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+        L.lb_steps_taken.restype = C.c_int
+        L.lb_steps_taken.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
+        L.lb_save.restype = C.c_int
+        L.lb_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.lb_load.restype = C.c_int
+        L.lb_load.argtypes = [C.c_void_p, C.c_char_p]
+        L.lb_destroy.restype = None
+        L.lb_destroy.argtypes = [C.c_void_p]
+        L.lb_error_string.restype = C.c_char_p
+        L.lb_error_string.argtypes = [C.c_int]
+        L.lb_last_error.restype = C.c_char_p
+        L.lb_last_error.argtypes = [C.c_void_p]
+        L.lb_device_bytes.restype = C.c_size_t
+        L.lb_device_bytes.argtypes = [C.c_void_p]
+        _lib = L
+        return _lib
+
+
+def make_grid(g: dict) -> lb_grid:
+    s = lb_grid()
+    for k, _ in lb_grid._fields_:
+        setattr(s, k, g.get(k, 0))
+    return s
+
+
+def make_params(p: dict) -> lb_params:
+    s = lb_params()
+    for k in _PARAM_DOUBLES:
+        setattr(s, k, float(p[k]))
+    for k in _PARAM_INTS:
+        setattr(s, k, int(p.get(k, 0)))
+    return s
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+class Solver:
+    """One lattice on the GPU.
+
+    ``fields`` maps phi, T, C (and optionally ux, uy) to ny x nx arrays: numpy
+    arrays (host) or float32 contiguous torch CUDA tensors (device).  ``stream``
+    is a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default
+    stream)."""
+
+    def __init__(self, grid: dict, params: dict, fields: dict, stream=None):
+        L = load()
+        self.nx, self.ny = int(grid["nx"]), int(grid["ny"])
+        n = self.nx * self.ny
+        self._grid, self._params = make_grid(grid), make_params(params)
+        keep = {}
+        on_device = any(_is_torch(fields.get(k)) for k in ("phi", "T", "C"))
+        for k in ("phi", "T", "C", "ux", "uy"):
+            v = fields.get(k)
+            if v is None:
+                continue
+            if on_device:
+                if not (_is_torch(v) and v.is_cuda and v.dtype.__str__() == "torch.float32" and v.is_contiguous()):
+                    raise ValueError("device fields must be contiguous float32 CUDA tensors (%s)" % k)
+                if v.numel() != n:
+                    raise ValueError("field %s has %d values, expected %d" % (k, v.numel(), n))
+            else:
+                v = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(-1))
+                if v.size != n:
+                    raise ValueError("field %s has %d values, expected %d" % (k, v.size, n))
+            keep[k] = v
+        f = lb_fields()
+        for k in ("phi", "T", "C", "ux", "uy"):
+            v = keep.get(k)
+            if v is None:
+                setattr(f, k, None)
+            elif on_device:
+                setattr(f, k, C.cast(C.c_void_p(v.data_ptr()), _fp))
+            else:
+                setattr(f, k, v.ctypes.data_as(_fp))
+        f.on_device = 1 if on_device else 0
+        h = C.c_void_p()
+        st = L.lb_create(C.byref(self._grid), C.byref(self._params), C.byref(f), C.byref(h))
+        if st != LB_OK:
+            raise LbError(st, L.lb_last_error(None).decode())
+        self._h = h
+        self._stream_obj = None
+        if stream is not None:
+            self.set_stream(stream)
+
+    # -- plumbing ---------------------------------------------------------------------------
+    def _check(self, st: int):
+        if st != LB_OK:
+            raise LbError(st, load().lb_last_error(self._h).decode())
+
+    def set_stream(self, stream):
+        ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+        self._stream_obj = stream
+        self._check(load().lb_set_stream(self._h, C.c_void_p(int(ptr) if ptr else 0)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lb_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return int(self._h.value or 0)
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().lb_device_bytes(self._h))
+
+    @property
+    def steps(self) -> int:
+        v = C.c_long()
+        self._check(load().lb_steps_taken(self._h, C.byref(v)))
+        return int(v.value)
+
+    # -- the method ---------------------------------------------------------------------------
+    def step(self, n: int = 1):
+        self._check(load().lb_step(self._h, int(n)))
+
+    def fields(self, device: bool = False, names=FIELD_NAMES):
+        """Macroscopic fields of the current state as (ny, nx) arrays: numpy on
+        the host, or torch CUDA tensors with ``device=True``."""
+        if device:
+            import torch
+            out = {k: torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda") for k in names}
+            ptrs = [C.c_void_p(out[k].data_ptr()) if k in out else None for k in FIELD_NAMES]
+        else:
+            out = {k: np.empty((self.ny, self.nx), dtype=np.float32) for k in names}
+            ptrs = [C.c_void_p(out[k].ctypes.data) if k in out else None for k in FIELD_NAMES]
+        self._check(load().lb_get_fields(self._h, *ptrs, 1 if device else 0))
+        return out
+
+    def reduce(self) -> np.ndarray:
+        out = (C.c_double * 8)()
+        self._check(load().lb_reduce(self._h, out))
+        return np.array(out[:], dtype=np.float64)
+
+    def save(self, path: str):
+        self._check(load().lb_save(self._h, path.encode()))
+
+    def load_state(self, path: str):
+        self._check(load().lb_load(self._h, path.encode()))
+
+
+def from_workload(w: dict, stream=None) -> Solver:
+    return Solver(w["grid"], w["params"], w["fields"], stream=stream)

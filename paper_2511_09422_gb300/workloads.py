@@ -105,12 +105,13 @@ def stefan_layer(nx=64, ny=256, h0=128, ste=0.1, rho_ratio=0.9, rho_g=0.1, T_wal
 
 def thermocapillary_channel(nx=512, ny=256, h=None, T_h=20.0, T_c=10.0, T_0=4.0, T_ref=10.0,
                             sigma_ref=2.5e-2, mu=0.2, lam=0.2, ma=0.1, steps=20000,
-                            width=INTERFACE_WIDTH) -> dict:
+                            width=INTERFACE_WIDTH, sigma_T=None) -> dict:
     """Marangoni convection of two superposed fluids (Sec. 4.1, second test and
     Appendix A): lower fluid (phi = 1) for y < h, upper fluid above, equal
     rho = Cp = 1, mu and lambda; bottom wall T_h + T_0 cos(2 pi x / L), top T_c;
     sigma(T) = sigma_ref + sigma_T (T - T_ref) with sigma_T < 0 fixed by
-    Ma = rho Cp |sigma_T| T_0 h / (mu lambda); no phase change, no solute.
+    Ma = rho Cp |sigma_T| T_0 h / (mu lambda) unless ``sigma_T`` is given (the
+    paper's own Appendix-A runs use sigma_T = -5e-4); no phase change, no solute.
     The temperature starts from the conduction profile between the walls."""
     if h is None:
         h = ny // 2
@@ -120,7 +121,8 @@ def thermocapillary_channel(nx=512, ny=256, h=None, T_h=20.0, T_c=10.0, T_0=4.0,
     Htot = float(ny)
     T = T_h + (T_c - T_h) * (y + 0.5) / Htot
     C = np.zeros_like(phi)
-    sigma_T = -ma * mu * lam / (1.0 * 1.0 * T_0 * h)
+    if sigma_T is None:
+        sigma_T = -ma * mu * lam / (1.0 * 1.0 * T_0 * h)
     p = base_params(rho_l=1.0, rho_s=1.0, rho_g=1.0, mu_l=mu, mu_s=mu, mu_g=mu, lam_l=lam,
                     lam_s=lam, lam_g=lam, cp_l=1.0, cp_s=1.0, cp_g=1.0, latent=0.0,
                     sigma0=sigma_ref, sigma_T=sigma_T, T_ref=T_ref, phase_change_on=0,
