@@ -135,6 +135,22 @@ lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C,
  * LB_ERR_UNSTABLE if the step has produced a non-finite value. */
 lb_status lb_reduce(lb_handle *h, double out[8]);
 
+/* The diagnostics of lb_reduce (same eight values, summed per lattice row
+ * and then over the rows, so they can differ from lb_reduce in the last
+ * digits), computed without allocating any device memory: for callers that
+ * cannot allocate at this point, e.g. because another allocator holds the
+ * device's memory or the surrounding code forbids allocation.  The paper has
+ * no counterpart of this call.  Its scratch is a fixed device array of
+ * (LB_NOALLOC_MAX_ROWS + 1) x 6 doubles (196,656 bytes) that every GPU using
+ * the library keeps until exit; lattices with more than LB_NOALLOC_MAX_ROWS
+ * rows get LB_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address, so make that first call before any stream capture,
+ * with the handle's device current.  All calls share the array: calls that
+ * run on the GPU at the same time race and must be serialised by the caller.
+ * Synchronises the stream; out is host memory. */
+#define LB_NOALLOC_MAX_ROWS 4096
+lb_status lb_reduce_noalloc(lb_handle *h, double out[8]);
+
 /* Number of steps taken since lb_create (or restored by lb_load). */
 lb_status lb_steps_taken(lb_handle *h, long *out);
 

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "lb_kernels.cuh"
@@ -416,4 +417,120 @@ extern "C" void lb_destroy(lb_handle *h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
+}
+
+// ---------------------------------------------------------------------------------------
+// Diagnostics without any device allocation (lb_reduce_noalloc).
+//
+// For callers that must not allocate device memory when they read the
+// diagnostics -- for example code whose device memory is entirely reserved by
+// another allocator (a framework's caching pool), or a section of a larger
+// pipeline that runs under a no-allocation rule.  The scratch lives in one
+// fixed file-scope device array instead of the handle: one row of FP64 partial
+// sums per lattice row, then the totals.  Every GPU that loads this library
+// holds the array, (LB_NOALLOC_MAX_ROWS + 1) * 6 doubles = 196,656 bytes,
+// until the process exits.  All calls share it and it keeps the last call's
+// contents; every call overwrites the rows and totals it reads, so nothing
+// needs clearing, but calls that overlap on the GPU (different streams or
+// threads at once) race on it and must be serialised by the caller.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[(LB_NOALLOC_MAX_ROWS + 1) * lbk::NRED];
+
+// Device address of g_noalloc_scratch per device ordinal.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device, with that device current, by the first call made on it.
+static double *g_noalloc_addr[256];
+static std::mutex g_noalloc_mu;
+
+namespace {
+
+__global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Consts K, const float *__restrict__ pin,
+                                                                         const float *__restrict__ ain,
+                                                                         double *__restrict__ scratch)
+{
+    __shared__ double sh[lbk::RED_THREADS / 32][lbk::NRED];
+    const int y = blockIdx.x;
+    const int xc = K.nx / 2;
+    double acc[lbk::NRED] = {0, 0, 0, 0, 0, 0};
+    for (int x = threadIdx.x; x < K.nx; x += blockDim.x) {
+        const long long cell = (long long)y * K.pitch + x;
+        const lbk::CellA c = lbk::cell_a(K, pin, ain, x, y, cell);
+        const double phid = (double)c.phi_p + (double)c.L.dphi;
+        acc[0] += phid;
+        acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
+        acc[2] += (double)c.L.C;
+        acc[3] += (double)c.L.fs;
+        acc[4] += (double)lbk::clamp01(R(0.5) * (R(1.0) + (real)phid));
+        if (x == xc) acc[5] += (double)c.L.fs;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < lbk::NRED; q++) {
+        double s = lbk::warp_sum(acc[q]);
+        if (lane == 0) sh[w][q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < lbk::NRED) {
+        double s = 0.0;
+        for (int j = 0; j < lbk::RED_THREADS / 32; j++) s += sh[j][threadIdx.x];
+        scratch[(long long)y * lbk::NRED + threadIdx.x] = s;
+    }
+}
+
+// Adds the row partials in row order; the totals go after the last possible row.
+__global__ void noalloc_total_kernel(double *__restrict__ scratch, int nrows)
+{
+    if (threadIdx.x < lbk::NRED) {
+        double s = 0.0;
+        for (int y = 0; y < nrows; y++) s += scratch[(long long)y * lbk::NRED + threadIdx.x];
+        scratch[(long long)LB_NOALLOC_MAX_ROWS * lbk::NRED + threadIdx.x] = s;
+    }
+}
+
+}  // namespace
+
+extern "C" lb_status lb_reduce_noalloc(lb_handle *h, double out[8])
+{
+    if (!h || !out) return fail(h, LB_ERR_INVALID_ARG, "null argument");
+    if (h->sticky != LB_OK) return h->sticky;
+    const Consts &K = h->K;
+    if (K.ny > LB_NOALLOC_MAX_ROWS)
+        return fail(h, LB_ERR_INVALID_ARG,
+                    "lb_reduce_noalloc: the lattice has " + std::to_string(K.ny) + " rows; its fixed scratch holds " +
+                        std::to_string(LB_NOALLOC_MAX_ROWS) + " (use lb_reduce)");
+    int dev = -1;
+    CK(h, cudaGetDevice(&dev));
+    cudaPointerAttributes attr;
+    CK(h, cudaPointerGetAttributes(&attr, h->pops[0]));
+    if (attr.device != dev)
+        return fail(h, LB_ERR_INVALID_ARG, "lb_reduce_noalloc: call it with the handle's device current");
+    if (dev < 0 || dev >= 256) return fail(h, LB_ERR_INVALID_ARG, "lb_reduce_noalloc: device ordinal out of range");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            g_noalloc_addr[dev] = (double *)p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    noalloc_rows_kernel<<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur], scratch);
+    CK(h, cudaGetLastError());
+    noalloc_total_kernel<<<1, 32, 0, h->stream>>>(scratch, K.ny);
+    CK(h, cudaGetLastError());
+    double r[lbk::NRED];
+    unsigned status = 0;
+    CK(h, cudaMemcpyAsync(r, scratch + (size_t)LB_NOALLOC_MAX_ROWS * lbk::NRED, sizeof(r), cudaMemcpyDeviceToHost,
+                          h->stream));
+    CK(h, cudaMemcpyAsync(&status, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 6; k++) out[k] = r[k];
+    out[6] = h->V0 > 0 ? r[3] / h->V0 : 0.0;
+    out[7] = h->V0 > 0 ? r[4] / h->V0 : 0.0;
+    bool finite = true;
+    for (int k = 0; k < 6; k++) finite = finite && std::isfinite(r[k]);
+    if (status || !finite) return fail(h, LB_ERR_UNSTABLE, "non-finite value in the lattice state");
+    return LB_OK;
 }

@@ -1,0 +1,75 @@
+"""lb_reduce_noalloc: the diagnostics read without allocating device memory.
+
+Some callers cannot allocate device memory when they read the diagnostics
+(another allocator holds the device's memory, or the surrounding code runs
+under a no-allocation rule).  lb_reduce_noalloc serves them from a fixed
+device array inside the library.  This file checks, through the C ABI, that
+it returns what lb_reduce returns, on two calls in a row and again after the
+state has moved on.  It is named so that pytest collects it last.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2511_09422_gb300 import lbfreeze
+from paper_2511_09422_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# the FP64 sums of the two entry points add the same FP32 cell values in a
+# different order; the parity tests compare reductions to 1e-5, this is tighter
+RTOL, ATOL = 1e-11, 1e-12
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_09422_gb300 import _build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+    L = lbfreeze.load()
+    L.lb_reduce_noalloc.restype = C.c_int
+    L.lb_reduce_noalloc.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+    return L
+
+
+def _noalloc(L, solver):
+    out = (C.c_double * 8)()
+    st = L.lb_reduce_noalloc(C.c_void_p(solver.handle), out)
+    assert st == lbfreeze.LB_OK, L.lb_last_error(C.c_void_p(solver.handle))
+    return np.array(out[:])
+
+
+def _reduce(L, solver):
+    out = (C.c_double * 8)()
+    assert L.lb_reduce(C.c_void_p(solver.handle), out) == lbfreeze.LB_OK
+    return np.array(out[:])
+
+
+def test_noalloc_matches_reduce_on_consecutive_calls(lib):
+    w = W.parity_droplet(nx=96, ny=72)
+    f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
+    s = lbfreeze.Solver(w["grid"], w["params"], f32)
+    s.step(25)
+    ref = _reduce(lib, s)
+    a1 = _noalloc(lib, s)
+    a2 = _noalloc(lib, s)
+    np.testing.assert_allclose(a1, ref, rtol=RTOL, atol=ATOL)
+    np.testing.assert_allclose(a2, ref, rtol=RTOL, atol=ATOL)
+    s.step(25)
+    ref2 = _reduce(lib, s)
+    a3 = _noalloc(lib, s)
+    np.testing.assert_allclose(a3, ref2, rtol=RTOL, atol=ATOL)
+    assert not np.allclose(ref2, ref)  # the state moved on, and so did the answer
+    s.close()
+
+
+def test_noalloc_rejects_too_many_rows(lib):
+    w = W.stefan_layer(nx=2, ny=4097, h0=3000)
+    s = lbfreeze.Solver(w["grid"], w["params"], {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()})
+    out = (C.c_double * 8)()
+    assert lib.lb_reduce_noalloc(C.c_void_p(s.handle), out) == lbfreeze.LB_ERR_INVALID_ARG
+    assert b"rows" in lib.lb_last_error(C.c_void_p(s.handle))
+    s.close()
