@@ -266,7 +266,13 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
 {
     if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
     if (h->sticky != LB_OK) return h->sticky;
+    // Tile rows whose halo rows and their pull sources (rows y0 - 2 .. y0 + TY + 1)
+    // all lie inside the lattice run the wall-free instantiation: tile rows
+    // 1 .. j_max with (j_max + 1) TY + 2 <= ny.  The others -- row 0 and rows
+    // j_max + 1 .. nty - 1 -- run the instantiation with the wall rules.
     const dim3 grid = step_grid(h->K), block(32, LB_WARPS, 1);
+    const int nty = (int)grid.y;
+    const int j_max = (h->K.ny - 2) / LB_TY - 1;
     for (int s = 0; s < n; s++) {
         lbk::Buffers B;
         B.pin = h->pops[h->cur];
@@ -275,7 +281,15 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
         B.aout = h->aux[1 - h->cur];
         B.fields = nullptr;
         B.status = h->status;
-        lbk::lb_step_kernel<lbk::MODE_STEP><<<grid, block, lbk::STEP_SMEM, h->stream>>>(h->K, B);
+        if (j_max >= 1) {
+            lbk::lb_step_kernel<lbk::MODE_STEP, false>
+                <<<dim3(grid.x, j_max, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 1, 1);
+            lbk::lb_step_kernel<lbk::MODE_STEP, true><<<dim3(grid.x, 1, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 0, 1);
+            lbk::lb_step_kernel<lbk::MODE_STEP, true>
+                <<<dim3(grid.x, nty - 1 - j_max, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, j_max + 1, 1);
+        } else {
+            lbk::lb_step_kernel<lbk::MODE_STEP, true><<<grid, block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 0, 1);
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
         h->cur = 1 - h->cur;
@@ -304,7 +318,7 @@ extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs
     B.aout = nullptr;
     B.fields = h->fields;
     B.status = h->status;
-    lbk::lb_step_kernel<lbk::MODE_FIELDS><<<step_grid(K), dim3(32, LB_WARPS, 1), lbk::STEP_SMEM, h->stream>>>(K, B);
+    lbk::lb_step_kernel<lbk::MODE_FIELDS, true><<<step_grid(K), dim3(32, LB_WARPS, 1), lbk::STEP_SMEM, h->stream>>>(K, B, 0, 1);
     CK(h, cudaGetLastError());
     float *dst[7] = {phi, T, fs, C, ux, uy, p};
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -55,6 +55,9 @@ typedef LB_REAL real;
 #ifndef LB_TY
 #define LB_TY 30
 #endif
+#ifndef LB_MINBLOCKS
+#define LB_MINBLOCKS 3
+#endif
 #define LB_TX 30
 #define LB_EXT_W 32
 #define LB_EXT_H (LB_TY + 2)
@@ -180,13 +183,13 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // at a wall (half-way bounce-back).  For the enthalpy at a Dirichlet wall the
 // anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (wall temperature at the
 // link midpoint) is applied in deviation form relative to w rr T_own.
-template <int S, int I>
+template <int S, int I, bool W>
 __device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
                                      real T_own)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    if (ys_off != 0 && (ys < 0 || ys >= K.ny)) {
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
         real v = __ldg(pin + (long long)(S * 9 + opp(I)) * K.plane + cell);
         if (S == SET_H) {
             const bool bottom = ys < 0;
@@ -201,43 +204,44 @@ __device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ 
     return __ldg(pin + (long long)(S * 9 + I) * K.plane + (long long)ys * K.pitch + xs);
 }
 
-template <int S>
+// W = false: the caller guarantees that no source row lies beyond a wall.
+template <int S, bool W = true>
 __device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell, real v[9],
                                       real T_own = R(0.0))
 {
-    v[0] = pull<S, 0>(K, pin, x, y, cell, T_own);
-    v[1] = pull<S, 1>(K, pin, x, y, cell, T_own);
-    v[2] = pull<S, 2>(K, pin, x, y, cell, T_own);
-    v[3] = pull<S, 3>(K, pin, x, y, cell, T_own);
-    v[4] = pull<S, 4>(K, pin, x, y, cell, T_own);
-    v[5] = pull<S, 5>(K, pin, x, y, cell, T_own);
-    v[6] = pull<S, 6>(K, pin, x, y, cell, T_own);
-    v[7] = pull<S, 7>(K, pin, x, y, cell, T_own);
-    v[8] = pull<S, 8>(K, pin, x, y, cell, T_own);
+    v[0] = pull<S, 0, W>(K, pin, x, y, cell, T_own);
+    v[1] = pull<S, 1, W>(K, pin, x, y, cell, T_own);
+    v[2] = pull<S, 2, W>(K, pin, x, y, cell, T_own);
+    v[3] = pull<S, 3, W>(K, pin, x, y, cell, T_own);
+    v[4] = pull<S, 4, W>(K, pin, x, y, cell, T_own);
+    v[5] = pull<S, 5, W>(K, pin, x, y, cell, T_own);
+    v[6] = pull<S, 6, W>(K, pin, x, y, cell, T_own);
+    v[7] = pull<S, 7, W>(K, pin, x, y, cell, T_own);
+    v[8] = pull<S, 8, W>(K, pin, x, y, cell, T_own);
 }
 
 // Lagged field (plane A) of the cell that wrote the population pulled into
 // direction I at (x, y) (the own cell at a wall).
-template <int A, int I>
+template <int A, int I, bool W>
 __device__ __forceinline__ real aux_src(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
     const float *a = ain + (long long)A * K.plane;
-    if (ys_off != 0 && (ys < 0 || ys >= K.ny)) return __ldg(a + cell);
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return __ldg(a + cell);
     return __ldg(a + (long long)ys * K.pitch + wrapx(x - cx(I), K.nx));
 }
 
 // sum_{i>0} w_i (z^n(source_i) - z^n(x)) of a lagged field: the reference
 // offsets of the pulled deviations relative to the own lagged value.
-template <int A>
+template <int A, bool W = true>
 __device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell,
                                             real own)
 {
-    return (wgt(1) * (aux_src<A, 1>(K, ain, x, y, cell) - own) + wgt(2) * (aux_src<A, 2>(K, ain, x, y, cell) - own) +
-            wgt(3) * (aux_src<A, 3>(K, ain, x, y, cell) - own) + wgt(4) * (aux_src<A, 4>(K, ain, x, y, cell) - own)) +
-           (wgt(5) * (aux_src<A, 5>(K, ain, x, y, cell) - own) + wgt(6) * (aux_src<A, 6>(K, ain, x, y, cell) - own) +
-            wgt(7) * (aux_src<A, 7>(K, ain, x, y, cell) - own) + wgt(8) * (aux_src<A, 8>(K, ain, x, y, cell) - own));
+    return (wgt(1) * (aux_src<A, 1, W>(K, ain, x, y, cell) - own) + wgt(2) * (aux_src<A, 2, W>(K, ain, x, y, cell) - own) +
+            wgt(3) * (aux_src<A, 3, W>(K, ain, x, y, cell) - own) + wgt(4) * (aux_src<A, 4, W>(K, ain, x, y, cell) - own)) +
+           (wgt(5) * (aux_src<A, 5, W>(K, ain, x, y, cell) - own) + wgt(6) * (aux_src<A, 6, W>(K, ain, x, y, cell) - own) +
+            wgt(7) * (aux_src<A, 7, W>(K, ain, x, y, cell) - own) + wgt(8) * (aux_src<A, 8, W>(K, ain, x, y, cell) - own));
 }
 
 __device__ __forceinline__ real sum9(const real v[9])
@@ -276,6 +280,7 @@ struct CellA {
     real ed, chi_p, fs_p, phi_p, T_p;
 };
 
+template <bool W = true>
 __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict__ pin, const float *__restrict__ ain,
                                         int x, int y, long long cell)
 {
@@ -285,12 +290,12 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     c.T_p = __ldg(ain + AUX_T * K.plane + cell);
     c.fs_p = __ldg(ain + AUX_FS * K.plane + cell);
     c.chi_p = clamp01(R(0.5) * (R(1.0) + c.phi_p));
-    pull9<SET_F>(K, pin, x, y, cell, v);
-    const real delta = sum9(v) + aux_dev_sum<AUX_PHI>(K, ain, x, y, cell, c.phi_p);
-    pull9<SET_H>(K, pin, x, y, cell, v, c.T_p);
+    pull9<SET_F, W>(K, pin, x, y, cell, v);
+    const real delta = sum9(v) + aux_dev_sum<AUX_PHI, W>(K, ain, x, y, cell, c.phi_p);
+    pull9<SET_H, W>(K, pin, x, y, cell, v, c.T_p);
     const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
-    c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
-    pull9<SET_L>(K, pin, x, y, cell, v);
+    c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T, W>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
+    pull9<SET_L, W>(K, pin, x, y, cell, v);
     const real sl = sum9(v);
     c.L = local_fields(K, c.phi_p, delta, c.ed, c.T_p, c.chi_p, c.fs_p, sl);
     return c;
@@ -315,15 +320,20 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 // The fused step.  MODE_FIELDS runs the same arithmetic up to velocity and
 // pressure and stores the macroscopic fields instead of colliding.
 // ---------------------------------------------------------------------------------------
-template <int MODE>
-__global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, const Buffers B)
+// WALLS = false is the instantiation for tile rows whose extended rows all lie
+// inside the lattice (no wall rule anywhere); the host launches it for the
+// interior tile rows and the WALLS = true one for the first and last.  The
+// tile row of a CTA is ty_base + blockIdx.y * ty_mult.
+template <int MODE, bool WALLS>
+__global__ void __launch_bounds__(32 * LB_WARPS, LB_MINBLOCKS) lb_step_kernel(const Consts K, const Buffers B, int ty_base,
+                                                                              int ty_mult)
 {
     extern __shared__ __align__(16) unsigned char lb_smem[];
     Tile &t = *reinterpret_cast<Tile *>(lb_smem);
     const int lane = threadIdx.x;
     const int warp = threadIdx.y;
     const int x0 = blockIdx.x * LB_TX;
-    const int y0 = blockIdx.y * LB_TY;
+    const int y0 = (ty_base + (int)blockIdx.y * ty_mult) * LB_TY;
     const int ex = x0 - 1 + lane;        // unwrapped abscissa of this lane
     const int xg = ((ex % K.nx) + K.nx) % K.nx;
     const float *__restrict__ pin = B.pin;
@@ -332,9 +342,9 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
     // ---- phase A: local fields on the extended tile ------------------------------------
     for (int r = warp; r < LB_EXT_H; r += LB_WARPS) {
         const int y = y0 - 1 + r;
-        if (y < 0 || y >= K.ny) continue;
+        if (WALLS && (y < 0 || y >= K.ny)) continue;
         const long long cell = (long long)y * K.pitch + xg;
-        const CellA c = cell_a(K, pin, ain, xg, y, cell);
+        const CellA c = cell_a<WALLS>(K, pin, ain, xg, y, cell);
         t.phip[r][lane] = c.phi_p;
         t.dphi[r][lane] = c.L.dphi;
         t.Tp[r][lane] = c.T_p;
@@ -353,9 +363,9 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
     const real rr = K.rr;
     for (int r = 1 + warp; r <= LB_TY; r += LB_WARPS) {
         const int y = y0 - 1 + r;
-        if (y >= K.ny) break;
+        if (WALLS && y >= K.ny) break;
         const long long cell = (long long)y * K.pitch + x;
-        const bool at_bottom = (y == 0), at_top = (y == K.ny - 1);
+        const bool at_bottom = WALLS && (y == 0), at_top = WALLS && (y == K.ny - 1);
         const int rs = at_bottom ? r : r - 1;  // south row (mirror ghost at the bottom wall)
         const int rn = at_top ? r : r + 1;     // north row
         const bool dir_b = at_bottom && K.bc_bottom == WALL_DIRICHLET;
@@ -448,12 +458,12 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
         // lagged pressure, so that the momentum and the pressure are sums of small terms
         const real p_p = t.p[r][lane];
         real g[9], dg[9];
-        pull9<SET_G>(K, pin, x, y, cell, g);
+        pull9<SET_G, WALLS>(K, pin, x, y, cell, g);
         real jx = R(0.0), jy = R(0.0), sg = R(0.0);
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             const int ys = y - cy(i);
-            const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+            const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
             const real pps = (i == 0 || wall) ? p_p : t.p[r - cy(i)][lane - cx(i)];
             dg[i] = g[i] + R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0))) * (pps - p_p);
             jx += (real)cx(i) * dg[i];
@@ -518,11 +528,11 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
             // d_i = f_i - w_i phi_st: the stored deviation plus w_i (phi^n(source) - phi_st);
             // stored as f_i* - w_i phi_st
             real f[9];
-            pull9<SET_F>(K, pin, x, y, cell, f);
+            pull9<SET_F, WALLS>(K, pin, x, y, cell, f);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
                 const int ys = y - cy(i);
-                const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+                const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
                 const real php = wall ? phi_p : t.phip[r - cy(i)][lane - cx(i)];
                 const real d = f[i] + wgt(i) * (php - phi_st);
                 const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
@@ -542,7 +552,7 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
             const real bx = (C * ux - C_p * ux_p) + (R(1.0) / R(3.0)) * Rx;
             const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
             real l[9];
-            pull9<SET_L>(K, pin, x, y, cell, l);
+            pull9<SET_L, WALLS>(K, pin, x, y, cell, l);
 #pragma unroll
             for (int i = 0; i < 9; i++) {
                 const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
@@ -563,11 +573,11 @@ __global__ void __launch_bounds__(32 * LB_WARPS) lb_step_kernel(const Consts K, 
             const real src_h = R(1.0) - R(0.5) * om_s;
             const real rcT = rhocp * T;
             real h[9], dh[9], deq[9];
-            pull9<SET_H>(K, pin, x, y, cell, h, T_p);
+            pull9<SET_H, WALLS>(K, pin, x, y, cell, h, T_p);
 #pragma unroll
             for (int i = 1; i < 9; i++) {
                 const int ys = y - cy(i);
-                const bool wall = cy(i) != 0 && (ys < 0 || ys >= K.ny);
+                const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
                 const real Tps = wall ? T_p : t.Tp[r - cy(i)][lane - cx(i)];
                 dh[i] = h[i] + wgt(i) * rr * (Tps - T_st);  // h_i - w_i rr T_st
                 const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
