@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = 360  # 36 populations read + written, 9 lagged fields read + written, FP32
 WORKLOAD = dict(name="impurity_front", nx=4096, ny=4096)
-PROFILE = os.path.join(ROOT, "profiles", "lb_step_kernel_impurity_front.md")
+PROFILE = os.path.join(ROOT, "profiles", "lb_strip_kernel_impurity_front.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2511_09422_gb300", "csrc", "lb_kernels.cuh")
 
 
@@ -181,9 +181,10 @@ def run_gpu(args):
     f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
     cells = nx * ny
     stream = torch.cuda.Stream()
-    # one step = the wall-free launch over the interior tile rows plus the two
-    # launches over the first and last tile rows (a single launch on small lattices)
-    launches_per_step = 3 if (ny - 2) // 30 - 1 >= 1 else 1
+    # one step = the wall-free launch over the interior 32-row segments plus the
+    # two launches over the bands of rows next to the walls (a single launch on
+    # lattices of fewer than 66 rows)
+    launches_per_step = 3 if (ny - 2) // 32 - 1 >= 1 else 1
 
     # ---- device-resident throughput -------------------------------------------------------
     solver = lbfreeze.Solver(w["grid"], w["params"], f32, stream=stream)

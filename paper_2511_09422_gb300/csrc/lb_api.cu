@@ -149,9 +149,42 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     return K;
 }
 
-static dim3 step_grid(const Consts &K)
+#ifndef LB_SEGH
+#define LB_SEGH 32
+#endif
+#ifndef LB_SEGH_W
+#define LB_SEGH_W 4
+#endif
+
+// Strip kernel launches.  The interior rows are cut into segments of LB_SEGH
+// rows: segments 1 .. j_max with (j_max + 1) H + 2 <= ny, whose rows and pull
+// sources (rows ys - 2 .. ye + 1) lie inside the lattice, run the wall-free
+// instantiation.  The rows below (0 .. H - 1) and above ((j_max + 1) H .. ny - 1)
+// run the instantiation with the wall rules in short segments of LB_SEGH_W
+// rows, so that these few rows are spread over many warps.
+template <int MODE>
+static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st)
 {
-    return dim3((K.nx + LB_TX - 1) / LB_TX, (K.ny + LB_TY - 1) / LB_TY, 1);
+    const int H = LB_SEGH, Hw = LB_SEGH_W;
+    static_assert(LB_SEGH % LB_SEGH_W == 0, "segment heights");
+    const unsigned ngroups = (unsigned)(((K.nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW);
+    const dim3 block(32, LB_SW, 1);
+    const int j_max = (K.ny - 2) / H - 1;
+    auto go = [&](bool walls, int seg_base, int nseg, int h) {
+        const dim3 grid(ngroups * (unsigned)nseg, 1, 1);
+        if (walls)
+            lbk::lb_strip_kernel<MODE, true><<<grid, block, lbk::STRIP_SMEM, st>>>(K, B, seg_base, h);
+        else
+            lbk::lb_strip_kernel<MODE, false><<<grid, block, lbk::STRIP_SMEM, st>>>(K, B, seg_base, h);
+    };
+    if (MODE == lbk::MODE_STEP && j_max >= 1) {
+        const int top0 = (j_max + 1) * H;  // first row above the interior segments
+        go(false, 1, j_max, H);
+        go(true, 0, H / Hw, Hw);
+        go(true, top0 / Hw, (K.ny - top0 + Hw - 1) / Hw, Hw);
+    } else {
+        go(true, 0, (K.ny + Hw - 1) / Hw, Hw);
+    }
 }
 
 static int flat_blocks(long long n, int threads)
@@ -266,13 +299,6 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
 {
     if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
     if (h->sticky != LB_OK) return h->sticky;
-    // Tile rows whose halo rows and their pull sources (rows y0 - 2 .. y0 + TY + 1)
-    // all lie inside the lattice run the wall-free instantiation: tile rows
-    // 1 .. j_max with (j_max + 1) TY + 2 <= ny.  The others -- row 0 and rows
-    // j_max + 1 .. nty - 1 -- run the instantiation with the wall rules.
-    const dim3 grid = step_grid(h->K), block(32, LB_WARPS, 1);
-    const int nty = (int)grid.y;
-    const int j_max = (h->K.ny - 2) / LB_TY - 1;
     for (int s = 0; s < n; s++) {
         lbk::Buffers B;
         B.pin = h->pops[h->cur];
@@ -281,17 +307,9 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
         B.aout = h->aux[1 - h->cur];
         B.fields = nullptr;
         B.status = h->status;
-        if (j_max >= 1) {
-            lbk::lb_step_kernel<lbk::MODE_STEP, false>
-                <<<dim3(grid.x, j_max, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 1, 1);
-            lbk::lb_step_kernel<lbk::MODE_STEP, true><<<dim3(grid.x, 1, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 0, 1);
-            lbk::lb_step_kernel<lbk::MODE_STEP, true>
-                <<<dim3(grid.x, nty - 1 - j_max, 1), block, lbk::STEP_SMEM, h->stream>>>(h->K, B, j_max + 1, 1);
-        } else {
-            lbk::lb_step_kernel<lbk::MODE_STEP, true><<<grid, block, lbk::STEP_SMEM, h->stream>>>(h->K, B, 0, 1);
-        }
+        launch_strip<lbk::MODE_STEP>(h->K, B, h->stream);
         cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
+        if (e != cudaSuccess) return cuda_fail(h, e, "lb_strip_kernel launch");
         h->cur = 1 - h->cur;
         h->steps++;
     }
@@ -318,7 +336,7 @@ extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs
     B.aout = nullptr;
     B.fields = h->fields;
     B.status = h->status;
-    lbk::lb_step_kernel<lbk::MODE_FIELDS, true><<<step_grid(K), dim3(32, LB_WARPS, 1), lbk::STEP_SMEM, h->stream>>>(K, B, 0, 1);
+    launch_strip<lbk::MODE_FIELDS>(K, B, h->stream);
     CK(h, cudaGetLastError());
     float *dst[7] = {phi, T, fs, C, ux, uy, p};
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

@@ -1,6 +1,6 @@
 // lb_kernels.cuh -- sm_103a kernels of the fused diffuse-interface LB freezing step.
 //
-// One launch of lb_step_kernel advances the whole lattice by one time step of
+// The launches of lb_strip_kernel over all row segments advance the lattice by one time step of
 // the four coupled D2Q9 sets of arXiv 2511.09422, Sec. 3: phase field f
 // (BGK, Sec. 3.1), pressure-based flow g (BGK, Sec. 3.2), total enthalpy h
 // (two-relaxation-time, Sec. 3.3) and solute l (BGK, Sec. 3.4).
@@ -29,15 +29,15 @@
 // that the large parts -- phi ~ 1, the pressure, T, and the latent enthalpy
 // ~ rho_l L -- cancel analytically instead of in FP32.
 //
-// Tiling: a CTA of 32 x LB_WARPS threads owns an interior tile of 30 x LB_TY
-// cells.  Phase A computes, for the tile plus a one-cell halo (32 x (LB_TY+2)
-// cells, one warp row of 32 lanes per lattice row), the local fields of the
-// step -- T, f_s, mdot, phi, C -- from the pulled populations and stores them
-// with the lagged p and S in shared memory.  Phase B then forms, for the
-// interior cells, the isotropic gradients from shared memory, the forces,
-// velocity and pressure, and collides the four sets.  The halo is recomputed
-// by both neighbouring tiles instead of being exchanged; its population reads
-// are L2 hits, so DRAM sees each byte about once.
+// Strip form (lb_strip_kernel): each warp owns a strip of 30 columns plus a
+// one-column halo on each side (32 lanes) and walks down a segment of rows.
+// Per row y it runs phase A -- the local fields of the step (T, f_s, mdot,
+// phi, C) from the pulled f, h, l -- into per-warp shared-memory rings, and
+// then phase B for row y - 1, whose neighbours are all in the rings: the
+// isotropic gradients, the forces, velocity and pressure, and the collision
+// of the four sets.  The pulled f, h, l are read from global memory once, the
+// halo costs 2 rows per segment and two columns per 30, and the warps of a
+// CTA never synchronise with one another (only __syncwarp).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,18 +49,7 @@
 typedef LB_REAL real;
 #define R(x) ((real)(x))
 
-#ifndef LB_WARPS
-#define LB_WARPS 8
-#endif
-#ifndef LB_TY
-#define LB_TY 30
-#endif
-#ifndef LB_MINBLOCKS
-#define LB_MINBLOCKS 3
-#endif
-#define LB_TX 30
-#define LB_EXT_W 32
-#define LB_EXT_H (LB_TY + 2)
+#define LB_TX 30  // interior columns of a warp strip (32 lanes less a halo column on each side)
 
 namespace lbk {
 
@@ -301,332 +290,458 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     return c;
 }
 
-// Shared-memory tile: the step's local fields on the tile plus a one-cell halo.
-struct Tile {
-    real phip[LB_EXT_H][LB_EXT_W];  // lagged phi (reference of the stored f deviations)
-    real dphi[LB_EXT_H][LB_EXT_W];  // phi - phi_p
-    real Tp[LB_EXT_H][LB_EXT_W];    // lagged T (reference of the stored h deviations)
-    real dT[LB_EXT_H][LB_EXT_W];    // T - T_p
-    real C[LB_EXT_H][LB_EXT_W];
-    real fs[LB_EXT_H][LB_EXT_W];
-    real p[LB_EXT_H][LB_EXT_W];
-    real S[LB_EXT_H][LB_EXT_W];
-    real mdot[LB_EXT_H][LB_EXT_W];
-};
-
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 
 // ---------------------------------------------------------------------------------------
-// The fused step.  MODE_FIELDS runs the same arithmetic up to velocity and
-// pressure and stores the macroscopic fields instead of colliding.
+// Phase B of one interior cell: gradients, forces, velocity, pressure and the
+// collision of the four sets (or, in MODE_FIELDS, the macroscopic fields).  The
+// accessor A supplies the step's local fields of the cell and its neighbours
+// (offsets dy, dx in {-1, 0, 1}, already mirrored at walls) and the cell's
+// pulled f, h, l; g is pulled here.
 // ---------------------------------------------------------------------------------------
-// WALLS = false is the instantiation for tile rows whose extended rows all lie
-// inside the lattice (no wall rule anywhere); the host launches it for the
-// interior tile rows and the WALLS = true one for the first and last.  The
-// tile row of a CTA is ty_base + blockIdx.y * ty_mult.
-template <int MODE, bool WALLS>
-__global__ void __launch_bounds__(32 * LB_WARPS, LB_MINBLOCKS) lb_step_kernel(const Consts K, const Buffers B, int ty_base,
-                                                                              int ty_mult)
+template <int MODE, bool WALLS, class Acc>
+__device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const Acc &A, int x, int y, long long cell)
 {
-    extern __shared__ __align__(16) unsigned char lb_smem[];
-    Tile &t = *reinterpret_cast<Tile *>(lb_smem);
-    const int lane = threadIdx.x;
-    const int warp = threadIdx.y;
-    const int x0 = blockIdx.x * LB_TX;
-    const int y0 = (ty_base + (int)blockIdx.y * ty_mult) * LB_TY;
-    const int ex = x0 - 1 + lane;        // unwrapped abscissa of this lane
-    const int xg = ((ex % K.nx) + K.nx) % K.nx;
-    const float *__restrict__ pin = B.pin;
-    const float *__restrict__ ain = B.ain;
-
-    // ---- phase A: local fields on the extended tile ------------------------------------
-    for (int r = warp; r < LB_EXT_H; r += LB_WARPS) {
-        const int y = y0 - 1 + r;
-        if (WALLS && (y < 0 || y >= K.ny)) continue;
-        const long long cell = (long long)y * K.pitch + xg;
-        const CellA c = cell_a<WALLS>(K, pin, ain, xg, y, cell);
-        t.phip[r][lane] = c.phi_p;
-        t.dphi[r][lane] = c.L.dphi;
-        t.Tp[r][lane] = c.T_p;
-        t.dT[r][lane] = c.L.dT;
-        t.C[r][lane] = c.L.C;
-        t.fs[r][lane] = c.L.fs;
-        t.mdot[r][lane] = c.L.mdot;
-        t.p[r][lane] = __ldg(ain + AUX_P * K.plane + cell);
-        t.S[r][lane] = __ldg(ain + AUX_S * K.plane + cell);
-    }
-    __syncthreads();
-
-    // ---- phase B: gradients, forces, velocity, pressure, collision ----------------------
-    if (lane == 0 || lane == LB_EXT_W - 1 || ex >= K.nx) return;
-    const int x = ex;
     const real rr = K.rr;
-    for (int r = 1 + warp; r <= LB_TY; r += LB_WARPS) {
-        const int y = y0 - 1 + r;
-        if (WALLS && y >= K.ny) break;
-        const long long cell = (long long)y * K.pitch + x;
-        const bool at_bottom = WALLS && (y == 0), at_top = WALLS && (y == K.ny - 1);
-        const int rs = at_bottom ? r : r - 1;  // south row (mirror ghost at the bottom wall)
-        const int rn = at_top ? r : r + 1;     // north row
-        const bool dir_b = at_bottom && K.bc_bottom == WALL_DIRICHLET;
-        const bool dir_t = at_top && K.bc_top == WALL_DIRICHLET;
+    const bool at_bottom = WALLS && (y == 0), at_top = WALLS && (y == K.ny - 1);
+    const int ds = at_bottom ? 0 : -1;  // south row offset (mirror ghost at the bottom wall)
+    const int dn = at_top ? 0 : 1;      // north row offset
+    const bool dir_b = at_bottom && K.bc_bottom == WALL_DIRICHLET;
+    const bool dir_t = at_top && K.bc_top == WALL_DIRICHLET;
 
-        // own fields: phi = phi_p + dphi, T = T_p + dT; phi_st, T_st are the values
-        // written to the lagged fields, which are also the references of the stored
-        // deviations (the parts below the FP32 spacing stay in those deviations)
-        const real phi_p = t.phip[r][lane], dphi = t.dphi[r][lane];
-        const real phi_st = (real)(float)(phi_p + dphi);
-        const real phi_lo = (phi_p - phi_st) + dphi;  // phi - phi_st
-        const real phi = phi_st + phi_lo;
-        const real T_p = t.Tp[r][lane], dT = t.dT[r][lane];
-        const real T_st = (real)(float)(T_p + dT);
-        const real T_lo = (T_p - T_st) + dT;          // T - T_st
-        const real T = T_st + T_lo;
-        const real C = t.C[r][lane], fs = (real)(float)t.fs[r][lane];
-        const real mdot = t.mdot[r][lane];
+    // own fields: phi = phi_p + dphi, T = T_p + dT; phi_st, T_st are the values
+    // written to the lagged fields, which are also the references of the stored
+    // deviations (the parts below the FP32 spacing stay in those deviations)
+    const real phi_p = A.phip(0, 0), dphi = A.dphi(0, 0);
+    const real phi_st = (real)(float)(phi_p + dphi);
+    const real phi_lo = (phi_p - phi_st) + dphi;  // phi - phi_st
+    const real phi = phi_st + phi_lo;
+    const real T_p = A.Tp(0, 0), dT = A.dT(0, 0);
+    const real T_st = (real)(float)(T_p + dT);
+    const real T_lo = (T_p - T_st) + dT;          // T - T_st
+    const real T = T_st + T_lo;
+    const real C = A.C(0, 0), fs = (real)(float)A.fs(0, 0);
+    const real mdot = A.mdot(0, 0);
 
-        // isotropic gradient and Laplacian over the 8 neighbours (order 1..8), from
-        // differences z_i - z_0: grad z = 3 sum w_i c_i (z_i - z_0), lap z = 6 sum w_i (z_i - z_0).
-        // phi and T differences are split into lagged-value and change parts.  Wall rows
-        // are ghosts: mirror, or 2 T_w - T_adjacent for the temperature at a Dirichlet wall.
-        real gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, gPx, gPy, gSx, gSy;
-        {
-            const int lc[9] = {lane, lane + 1, lane, lane - 1, lane, lane + 1, lane - 1, lane - 1, lane + 1};
-            const int rw[9] = {r, r, rn, r, rs, rn, rn, rs, rs};
-            const real f0 = t.fs[r][lane], P0 = t.p[r][lane], S0 = t.S[r][lane];
-            real sx[6] = {0, 0, 0, 0, 0, 0}, sy[6] = {0, 0, 0, 0, 0, 0}, sl = R(0.0);
+    // isotropic gradient and Laplacian over the 8 neighbours (order 1..8), from
+    // differences z_i - z_0: grad z = 3 sum w_i c_i (z_i - z_0), lap z = 6 sum w_i (z_i - z_0).
+    // phi and T differences are split into lagged-value and change parts.  Wall rows
+    // are ghosts: mirror, or 2 T_w - T_adjacent for the temperature at a Dirichlet wall.
+    real gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, gPx, gPy, gSx, gSy;
+    {
+        const int dxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+        const int dyv[9] = {0, 0, dn, 0, ds, dn, dn, ds, ds};
+        const real f0 = A.fs(0, 0), P0 = A.p(0, 0), S0 = A.S(0, 0);
+        real sx[6] = {0, 0, 0, 0, 0, 0}, sy[6] = {0, 0, 0, 0, 0, 0}, sl = R(0.0);
 #pragma unroll
-            for (int i = 1; i < 9; i++) {
-                const int a = rw[i], b = lc[i];
-                const real zph = (t.phip[a][b] - phi_p) + (t.dphi[a][b] - dphi);
-                real zT = (t.Tp[a][b] - T_p) + (t.dT[a][b] - dT);
-                if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
-                    const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
-                    // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
-                    zT = R(2.0) * (Tw - t.Tp[a][b]) + (t.Tp[a][b] - T_p) - (t.dT[a][b] + dT);
-                }
-                const real zv[6] = {zph, zT, t.C[a][b] - C, t.fs[a][b] - f0, t.p[a][b] - P0, t.S[a][b] - S0};
-                const real wcx = wgt(i) * (real)cx(i), wcy = wgt(i) * (real)cy(i);
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    sx[k] += wcx * zv[k];
-                    sy[k] += wcy * zv[k];
-                }
-                sl += R(2.0) * wgt(i) * zph;
+        for (int i = 1; i < 9; i++) {
+            const int a = dyv[i], b = dxv[i];
+            const real zph = (A.phip(a, b) - phi_p) + (A.dphi(a, b) - dphi);
+            real zT = (A.Tp(a, b) - T_p) + (A.dT(a, b) - dT);
+            if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
+                const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
+                // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
+                zT = R(2.0) * (Tw - A.Tp(a, b)) + (A.Tp(a, b) - T_p) - (A.dT(a, b) + dT);
             }
-            gpx = R(3.0) * sx[0]; gpy = R(3.0) * sy[0]; lphi = R(3.0) * sl;
-            gTx = R(3.0) * sx[1]; gTy = R(3.0) * sy[1];
-            gCx = R(3.0) * sx[2]; gCy = R(3.0) * sy[2];
-            gfx = R(3.0) * sx[3]; gfy = R(3.0) * sy[3];
-            gPx = R(3.0) * sx[4]; gPy = R(3.0) * sy[4];
-            gSx = R(3.0) * sx[5]; gSy = R(3.0) * sy[5];
+            const real zv[6] = {zph, zT, A.C(a, b) - C, A.fs(a, b) - f0, A.p(a, b) - P0, A.S(a, b) - S0};
+            const real wcx = wgt(i) * (real)cx(i), wcy = wgt(i) * (real)cy(i);
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                sx[k] += wcx * zv[k];
+                sy[k] += wcy * zv[k];
+            }
+            sl += R(2.0) * wgt(i) * zph;
         }
+        gpx = R(3.0) * sx[0]; gpy = R(3.0) * sy[0]; lphi = R(3.0) * sl;
+        gTx = R(3.0) * sx[1]; gTy = R(3.0) * sy[1];
+        gCx = R(3.0) * sx[2]; gCy = R(3.0) * sy[2];
+        gfx = R(3.0) * sx[3]; gfy = R(3.0) * sy[3];
+        gPx = R(3.0) * sx[4]; gPy = R(3.0) * sy[4];
+        gSx = R(3.0) * sx[5]; gSy = R(3.0) * sy[5];
+    }
 
-        // properties by the linear rule; the density gradient follows from it exactly
-        const real rho = zeta(phi, fs, K.rho_l, K.rho_s, K.rho_g);
-        const real mu = zeta(phi, fs, K.mu_l, K.mu_s, K.mu_g);
-        const real lam = zeta(phi, fs, K.lam_l, K.lam_s, K.lam_g);
-        const real rhocp = zeta(phi, fs, K.rcp_l, K.rcp_s, K.rcp_g);
-        const real dr_phi = R(0.5) * (K.rho_l - K.rho_g), dr_fs = K.rho_s - K.rho_l;
-        const real grx = dr_phi * gpx + dr_fs * gfx, gry = dr_phi * gpy + dr_fs * gfy;
+    // properties by the linear rule; the density gradient follows from it exactly
+    const real rho = zeta(phi, fs, K.rho_l, K.rho_s, K.rho_g);
+    const real mu = zeta(phi, fs, K.mu_l, K.mu_s, K.mu_g);
+    const real lam = zeta(phi, fs, K.lam_l, K.lam_s, K.lam_g);
+    const real rhocp = zeta(phi, fs, K.rcp_l, K.rcp_s, K.rcp_g);
+    const real dr_phi = R(0.5) * (K.rho_l - K.rho_g), dr_fs = K.rho_s - K.rho_l;
+    const real grx = dr_phi * gpx + dr_fs * gfx, gry = dr_phi * gpy + dr_fs * gfy;
 
-        // normal, chemical potential, surface tension and its gradient
-        const real g2 = gpx * gpx + gpy * gpy;
-        const real inv = rsqrt(g2 + R(1e-6));  // regularised normal: smooth away from the interface
-        const real nxv = gpx * inv, nyv = gpy * inv;
-        // chemical potential: the cubic term and the Laplacian nearly cancel across the
-        // interface, so this short expression is evaluated in FP64
-        const double phd = (double)phi_p + (double)dphi;
-        const real muphi = (real)((phd * phd * phd - phd) * (double)K.inv_eps2 - (double)lphi);
-        const real sigma = K.sigma0 + K.sigma_T * (T - K.T_ref) + K.sigma_c * (C - K.c_ref);
-        const real gsx = K.sigma_T * gTx + K.sigma_c * gCx;
-        const real gsy = K.sigma_T * gTy + K.sigma_c * gCy;
+    // normal, chemical potential, surface tension and its gradient
+    const real g2 = gpx * gpx + gpy * gpy;
+    const real inv = rsqrt(g2 + R(1e-6));  // regularised normal: smooth away from the interface
+    const real nxv = gpx * inv, nyv = gpy * inv;
+    // chemical potential: the cubic term and the Laplacian nearly cancel across the
+    // interface, so this short expression is evaluated in FP64
+    const double phd = (double)phi_p + (double)dphi;
+    const real muphi = (real)((phd * phd * phd - phd) * (double)K.inv_eps2 - (double)lphi);
+    const real sigma = K.sigma0 + K.sigma_T * (T - K.T_ref) + K.sigma_c * (C - K.c_ref);
+    const real gsx = K.sigma_T * gTx + K.sigma_c * gCx;
+    const real gsy = K.sigma_T * gTy + K.sigma_c * gCy;
 
-        // Eq. Fs: Marangoni part alpha (|grad phi|^2 grad sigma - (grad sigma . grad phi) grad phi)
-        // plus capillary part alpha sigma mu_phi grad phi, times (1 - f_s) when modulated
-        const real gsgp = gsx * gpx + gsy * gpy;
-        real Fsx = K.alpha * (g2 * gsx - gsgp * gpx) + K.alpha * sigma * muphi * gpx;
-        real Fsy = K.alpha * (g2 * gsy - gsgp * gpy) + K.alpha * sigma * muphi * gpy;
-        if (K.fs_mod) {
-            Fsx *= (R(1.0) - fs);
-            Fsy *= (R(1.0) - fs);
-        }
-        const real Fx = Fsx + rho * K.gx, Fy = Fsy + rho * K.gy;
+    // Eq. Fs: Marangoni part alpha (|grad phi|^2 grad sigma - (grad sigma . grad phi) grad phi)
+    // plus capillary part alpha sigma mu_phi grad phi, times (1 - f_s) when modulated
+    const real gsgp = gsx * gpx + gsy * gpy;
+    real Fsx = K.alpha * (g2 * gsx - gsgp * gpx) + K.alpha * sigma * muphi * gpx;
+    real Fsy = K.alpha * (g2 * gsy - gsgp * gpy) + K.alpha * sigma * muphi * gpy;
+    if (K.fs_mod) {
+        Fsx *= (R(1.0) - fs);
+        Fsy *= (R(1.0) - fs);
+    }
+    const real Fx = Fsx + rho * K.gx, Fy = Fsy + rho * K.gy;
 
-        // flow set: velocity and pressure (Sec. 3.2).  g is stored as deviations from
-        // 3 p^n(s) (w_i - [i = 0]); dg_i = g_i - 3 p_p (w_i - [i = 0]) with p_p the own
-        // lagged pressure, so that the momentum and the pressure are sums of small terms
-        const real p_p = t.p[r][lane];
-        real g[9], dg[9];
-        pull9<SET_G, WALLS>(K, pin, x, y, cell, g);
-        real jx = R(0.0), jy = R(0.0), sg = R(0.0);
+    // flow set: velocity and pressure (Sec. 3.2).  g is stored as deviations from
+    // 3 p^n(s) (w_i - [i = 0]); dg_i = g_i - 3 p_p (w_i - [i = 0]) with p_p the own
+    // lagged pressure, so that the momentum and the pressure are sums of small terms
+    const real p_p = A.p(0, 0);
+    real g[9], dg[9];
+    pull9<SET_G, WALLS>(K, B.pin, x, y, cell, g);
+    real jx = R(0.0), jy = R(0.0), sg = R(0.0);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const int ys = y - cy(i);
+        const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
+        const real pps = (i == 0 || wall) ? p_p : A.p(-cy(i), -cx(i));
+        dg[i] = g[i] + R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0))) * (pps - p_p);
+        jx += (real)cx(i) * dg[i];
+        jy += (real)cy(i) * dg[i];
+        if (i) sg += dg[i];
+    }
+    const real inv_rho = R(1.0) / rho;
+    const real usx = (jx + R(0.5) * Fx) * inv_rho, usy = (jy + R(0.5) * Fy) * inv_rho;
+    const real ffx = -fs * usx, ffy = -fs * usy;       // f = f_s (0 - u*)
+    const real ux = usx + R(0.5) * ffx, uy = usy + R(0.5) * ffy;
+    const real rfx = rho * ffx, rfy = rho * ffy;
+    const real S = rho * mdot + ux * grx + uy * gry;
+    const real Ftx = Fx - gPx + (R(1.0) / R(3.0)) * grx + (R(1.0) / R(3.0)) * gSx;
+    const real Fty = Fy - gPy + (R(1.0) / R(3.0)) * gry + (R(1.0) / R(3.0)) * gSy;
+    const real tau_g = R(0.5) + R(3.0) * mu * inv_rho;
+    const real uu = ux * ux + uy * uy;
+    const real uF = ux * Ftx + uy * Fty;
+    const real G0 = wgt(0) * (S - R(3.0) * uF);
+    const real s0 = wgt(0) * (-R(1.5) * uu);
+    // p = c_s^2/(1 - w_0) [sum_{i>0} g_i + S/2 + tau G_0 + rho s_0(u)] = p_p + dp
+    const real dp = (R(1.0) / R(3.0)) / (R(1.0) - wgt(0)) * (sg + R(0.5) * S + tau_g * G0 + rho * s0);
+    const real p_st = (real)(float)(p_p + dp);
+    const real p_lo = (p_p - p_st) + dp;  // p - p_st
+    const real pr = p_st + p_lo;
+
+    if (MODE == MODE_FIELDS) {
+        float *o = B.fields;
+        const long long P = K.plane;
+        o[0 * P + cell] = phi;
+        o[1 * P + cell] = T;
+        o[2 * P + cell] = fs;
+        o[3 * P + cell] = C;
+        o[4 * P + cell] = ux;
+        o[5 * P + cell] = uy;
+        o[6 * P + cell] = pr;
+        return;
+    }
+
+    const real om_g = R(1.0) / tau_g, src_g = R(1.0) - R(0.5) * om_g;
+    float *__restrict__ pout = B.pout;
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        // deviations from 3 p_st (w_i - [i = 0]), the reference of the stored value
+        const real wp = R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0)));
+        const real d = dg[i] + wp * (p_p - p_st);
+        const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+        const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
+        const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
+        const real deq = wp * p_lo + rho * si;
+        const real Gi = wgt(i) * (S + R(3.0) * ((real)cx(i) * (Fx + rfx) + (real)cy(i) * (Fy + rfy)) +
+                                   R(9.0) * (cu * cF - (R(1.0) / R(3.0)) * uF));
+        pout[(long long)(SET_G * 9 + i) * K.plane + cell] = d - (d - deq) * om_g + src_g * Gi;
+    }
+
+    // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
+    {
+        const real ux_p = __ldg(B.ain + AUX_UX * K.plane + cell), uy_p = __ldg(B.ain + AUX_UY * K.plane + cell);
+        const real kf = (R(1.0) / R(3.0)) * (R(1.0) - phi * phi) * K.inv_s2eps;
+        const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
+        const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
+        const real om = R(1.0) / K.tau_f, src = R(1.0) - R(0.5) * om;
+        // d_i = f_i - w_i phi_st: the stored deviation plus w_i (phi^n(source) - phi_st);
+        // stored as f_i* - w_i phi_st
+        real f[9];
+        A.template pops<SET_F>(K, B.pin, x, y, cell, f, R(0.0));
 #pragma unroll
         for (int i = 0; i < 9; i++) {
             const int ys = y - cy(i);
             const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
-            const real pps = (i == 0 || wall) ? p_p : t.p[r - cy(i)][lane - cx(i)];
-            dg[i] = g[i] + R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0))) * (pps - p_p);
-            jx += (real)cx(i) * dg[i];
-            jy += (real)cy(i) * dg[i];
-            if (i) sg += dg[i];
-        }
-        const real inv_rho = R(1.0) / rho;
-        const real usx = (jx + R(0.5) * Fx) * inv_rho, usy = (jy + R(0.5) * Fy) * inv_rho;
-        const real ffx = -fs * usx, ffy = -fs * usy;       // f = f_s (0 - u*)
-        const real ux = usx + R(0.5) * ffx, uy = usy + R(0.5) * ffy;
-        const real rfx = rho * ffx, rfy = rho * ffy;
-        const real S = rho * mdot + ux * grx + uy * gry;
-        const real Ftx = Fx - gPx + (R(1.0) / R(3.0)) * grx + (R(1.0) / R(3.0)) * gSx;
-        const real Fty = Fy - gPy + (R(1.0) / R(3.0)) * gry + (R(1.0) / R(3.0)) * gSy;
-        const real tau_g = R(0.5) + R(3.0) * mu * inv_rho;
-        const real uu = ux * ux + uy * uy;
-        const real uF = ux * Ftx + uy * Fty;
-        const real G0 = wgt(0) * (S - R(3.0) * uF);
-        const real s0 = wgt(0) * (-R(1.5) * uu);
-        // p = c_s^2/(1 - w_0) [sum_{i>0} g_i + S/2 + tau G_0 + rho s_0(u)] = p_p + dp
-        const real dp = (R(1.0) / R(3.0)) / (R(1.0) - wgt(0)) * (sg + R(0.5) * S + tau_g * G0 + rho * s0);
-        const real p_st = (real)(float)(p_p + dp);
-        const real p_lo = (p_p - p_st) + dp;  // p - p_st
-        const real pr = p_st + p_lo;
-
-        if (MODE == MODE_FIELDS) {
-            float *o = B.fields;
-            const long long P = K.plane;
-            o[0 * P + cell] = phi;
-            o[1 * P + cell] = T;
-            o[2 * P + cell] = fs;
-            o[3 * P + cell] = C;
-            o[4 * P + cell] = ux;
-            o[5 * P + cell] = uy;
-            o[6 * P + cell] = pr;
-            continue;
+            const real php = wall ? phi_p : A.phip(-cy(i), -cx(i));
+            const real d = f[i] + wgt(i) * (php - phi_st);
+            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+            const real deq = wgt(i) * (phi_lo + phi * R(3.0) * cu);  // f_eq - w_i phi_st
+            const real Fi = wgt(i) * R(3.0) * ((real)cx(i) * ax + (real)cy(i) * ay) + wgt(i) * phi * mdot;
+            pout[(long long)(SET_F * 9 + i) * K.plane + cell] = d - (d - deq) * om + src * Fi;
         }
 
-        const real om_g = R(1.0) / tau_g, src_g = R(1.0) - R(0.5) * om_g;
-        float *__restrict__ pout = B.pout;
+        // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
+        const real C_p = __ldg(B.ain + AUX_C * K.plane + cell);
+        const real keff = R(1.0) - fs * (R(1.0) - K.k_p);
+        const real De = fs * K.k_p * K.D_s + (R(1.0) - fs) * K.D_l;
+        const real tau_l = R(0.5) + R(3.0) * De / keff;
+        const real om_l = R(1.0) / tau_l, src_l = R(1.0) - R(0.5) * om_l;
+        const real Rx = (R(1.0) - phi) * C * nxv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfx / keff;
+        const real Ry = (R(1.0) - phi) * C * nyv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfy / keff;
+        const real bx = (C * ux - C_p * ux_p) + (R(1.0) / R(3.0)) * Rx;
+        const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
+        real l[9];
+        A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
 #pragma unroll
         for (int i = 0; i < 9; i++) {
-            // deviations from 3 p_st (w_i - [i = 0]), the reference of the stored value
-            const real wp = R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0)));
-            const real d = dg[i] + wp * (p_p - p_st);
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
-            const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-            const real deq = wp * p_lo + rho * si;
-            const real Gi = wgt(i) * (S + R(3.0) * ((real)cx(i) * (Fx + rfx) + (real)cy(i) * (Fy + rfy)) +
-                                       R(9.0) * (cu * cF - (R(1.0) / R(3.0)) * uF));
-            pout[(long long)(SET_G * 9 + i) * K.plane + cell] = d - (d - deq) * om_g + src_g * Gi;
+            const real leq = wgt(i) * C * (R(1.0) + R(3.0) * cu);
+            const real Li = wgt(i) * R(3.0) * ((real)cx(i) * bx + (real)cy(i) * by);
+            pout[(long long)(SET_L * 9 + i) * K.plane + cell] = l[i] - (l[i] - leq) * om_l + src_l * Li;
         }
+    }
 
-        // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
+    // enthalpy set (Sec. 3.3), two relaxation times: antisymmetric part with
+    // tau_bar = 1/2 + lam/(rho_ref Cp_ref cs2), symmetric part with 1/tau_tilde = 2 - 1/tau_bar;
+    // isotropic source w_i Q weighted with (1 - 1/(2 tau_tilde)).  Everything is formed as
+    // deviations from w_i rr T_st (and the latent reference for i = 0).
+    const real Q = rhocp * T * mdot;
+    {
+        const real tau_hb = R(0.5) + R(3.0) * lam / rr;
+        const real om_a = R(1.0) / tau_hb, om_s = R(2.0) - om_a;
+        const real src_h = R(1.0) - R(0.5) * om_s;
+        const real rcT = rhocp * T;
+        real h[9], dh[9], deq[9];
+        A.template pops<SET_H>(K, B.pin, x, y, cell, h, T_p);
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const int ys = y - cy(i);
+            const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
+            const real Tps = wall ? T_p : A.Tp(-cy(i), -cx(i));
+            dh[i] = h[i] + wgt(i) * rr * (Tps - T_st);  // h_i - w_i rr T_st
+            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+            deq[i] = wgt(i) * (rr * T_lo + rcT * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu));
+        }
+#pragma unroll
+        for (int i = 1; i < 9; i++) {
+            const int j = opp(i);
+            const real hs = R(0.5) * (dh[i] + dh[j]), ha = R(0.5) * (dh[i] - dh[j]);
+            const real es = R(0.5) * (deq[i] + deq[j]), ea = R(0.5) * (deq[i] - deq[j]);
+            pout[(long long)(SET_H * 9 + i) * K.plane + cell] =
+                dh[i] - (ha - ea) * om_a - (hs - es) * om_s + src_h * wgt(i) * Q;
+        }
+        // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
+        // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
+        // moves from w_0 rr T_p + rho_l L (chi_p - fs_p) to w_0 rr T_st + rho_l L (chi_st - f_s)
         {
-            const real ux_p = __ldg(ain + AUX_UX * K.plane + cell), uy_p = __ldg(ain + AUX_UY * K.plane + cell);
-            const real kf = (R(1.0) / R(3.0)) * (R(1.0) - phi * phi) * K.inv_s2eps;
-            const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
-            const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
-            const real om = R(1.0) / K.tau_f, src = R(1.0) - R(0.5) * om;
-            // d_i = f_i - w_i phi_st: the stored deviation plus w_i (phi^n(source) - phi_st);
-            // stored as f_i* - w_i phi_st
-            real f[9];
-            pull9<SET_F, WALLS>(K, pin, x, y, cell, f);
+            const real Q_p = __ldg(B.ain + AUX_Q * K.plane + cell);
+            const real fs_p = __ldg(B.ain + AUX_FS * K.plane + cell);
+            const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
+            const real chi_n = clamp01(R(0.5) * (R(1.0) + phi_st));
+            // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
+            real snz = R(0.0);
 #pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const int ys = y - cy(i);
-                const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
-                const real php = wall ? phi_p : t.phip[r - cy(i)][lane - cx(i)];
-                const real d = f[i] + wgt(i) * (php - phi_st);
-                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-                const real deq = wgt(i) * (phi_lo + phi * R(3.0) * cu);  // f_eq - w_i phi_st
-                const real Fi = wgt(i) * R(3.0) * ((real)cx(i) * ax + (real)cy(i) * ay) + wgt(i) * phi * mdot;
-                pout[(long long)(SET_F * 9 + i) * K.plane + cell] = d - (d - deq) * om + src * Fi;
-            }
-
-            // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
-            const real C_p = __ldg(ain + AUX_C * K.plane + cell);
-            const real keff = R(1.0) - fs * (R(1.0) - K.k_p);
-            const real De = fs * K.k_p * K.D_s + (R(1.0) - fs) * K.D_l;
-            const real tau_l = R(0.5) + R(3.0) * De / keff;
-            const real om_l = R(1.0) / tau_l, src_l = R(1.0) - R(0.5) * om_l;
-            const real Rx = (R(1.0) - phi) * C * nxv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfx / keff;
-            const real Ry = (R(1.0) - phi) * C * nyv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfy / keff;
-            const real bx = (C * ux - C_p * ux_p) + (R(1.0) / R(3.0)) * Rx;
-            const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
-            real l[9];
-            pull9<SET_L, WALLS>(K, pin, x, y, cell, l);
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-                const real leq = wgt(i) * C * (R(1.0) + R(3.0) * cu);
-                const real Li = wgt(i) * R(3.0) * ((real)cx(i) * bx + (real)cy(i) * by);
-                pout[(long long)(SET_L * 9 + i) * K.plane + cell] = l[i] - (l[i] - leq) * om_l + src_l * Li;
-            }
+            for (int i = 1; i < 9; i++) snz += dh[i];
+            const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
+            const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
+            pout[(long long)(SET_H * 9 + 0) * K.plane + cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
         }
+    }
 
-        // enthalpy set (Sec. 3.3), two relaxation times: antisymmetric part with
-        // tau_bar = 1/2 + lam/(rho_ref Cp_ref cs2), symmetric part with 1/tau_tilde = 2 - 1/tau_bar;
-        // isotropic source w_i Q weighted with (1 - 1/(2 tau_tilde)).  Everything is formed as
-        // deviations from w_i rr T_st (and the latent reference for i = 0).
-        const real Q = rhocp * T * mdot;
-        {
-            const real tau_hb = R(0.5) + R(3.0) * lam / rr;
-            const real om_a = R(1.0) / tau_hb, om_s = R(2.0) - om_a;
-            const real src_h = R(1.0) - R(0.5) * om_s;
-            const real rcT = rhocp * T;
-            real h[9], dh[9], deq[9];
-            pull9<SET_H, WALLS>(K, pin, x, y, cell, h, T_p);
-#pragma unroll
-            for (int i = 1; i < 9; i++) {
-                const int ys = y - cy(i);
-                const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
-                const real Tps = wall ? T_p : t.Tp[r - cy(i)][lane - cx(i)];
-                dh[i] = h[i] + wgt(i) * rr * (Tps - T_st);  // h_i - w_i rr T_st
-                const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-                deq[i] = wgt(i) * (rr * T_lo + rcT * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-            }
-#pragma unroll
-            for (int i = 1; i < 9; i++) {
-                const int j = opp(i);
-                const real hs = R(0.5) * (dh[i] + dh[j]), ha = R(0.5) * (dh[i] - dh[j]);
-                const real es = R(0.5) * (deq[i] + deq[j]), ea = R(0.5) * (deq[i] - deq[j]);
-                pout[(long long)(SET_H * 9 + i) * K.plane + cell] =
-                    dh[i] - (ha - ea) * om_a - (hs - es) * om_s + src_h * wgt(i) * Q;
-            }
-            // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
-            // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
-            // moves from w_0 rr T_p + rho_l L (chi_p - fs_p) to w_0 rr T_st + rho_l L (chi_st - f_s)
-            {
-                const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
-                const real fs_p = __ldg(ain + AUX_FS * K.plane + cell);
-                const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
-                const real chi_n = clamp01(R(0.5) * (R(1.0) + phi_st));
-                // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
-                real snz = R(0.0);
-#pragma unroll
-                for (int i = 1; i < 9; i++) snz += dh[i];
-                const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
-                const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
-                pout[(long long)(SET_H * 9 + 0) * K.plane + cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
-            }
-        }
+    // lagged fields for the next step
+    float *__restrict__ aout = B.aout;
+    aout[AUX_FS * K.plane + cell] = fs;
+    aout[AUX_Q * K.plane + cell] = Q;
+    aout[AUX_UX * K.plane + cell] = ux;
+    aout[AUX_UY * K.plane + cell] = uy;
+    aout[AUX_PHI * K.plane + cell] = (float)phi_st;
+    aout[AUX_C * K.plane + cell] = C;
+    aout[AUX_P * K.plane + cell] = (float)p_st;
+    aout[AUX_S * K.plane + cell] = S;
+    aout[AUX_T * K.plane + cell] = (float)T_st;
 
-        // lagged fields for the next step
-        float *__restrict__ aout = B.aout;
-        aout[AUX_FS * K.plane + cell] = fs;
-        aout[AUX_Q * K.plane + cell] = Q;
-        aout[AUX_UX * K.plane + cell] = ux;
-        aout[AUX_UY * K.plane + cell] = uy;
-        aout[AUX_PHI * K.plane + cell] = (float)phi_st;
-        aout[AUX_C * K.plane + cell] = C;
-        aout[AUX_P * K.plane + cell] = (float)p_st;
-        aout[AUX_S * K.plane + cell] = S;
-        aout[AUX_T * K.plane + cell] = (float)T_st;
+    // a non-finite value anywhere in the cell's new state is reported once
+    if (!isfinite(T + phi + C + ux + uy + pr)) atomicOr(B.status, 1u);
+}
 
-        // a non-finite value anywhere in the cell's new state is reported once
-        if (!isfinite(T + phi + C + ux + uy + pr)) atomicOr(B.status, 1u);
+
+
+// ---------------------------------------------------------------------------------------
+// Strip form of the step.  Each warp owns a strip of 30 columns (plus one halo
+// column on each side) and walks down a segment of rows; per row it runs
+// phase A for row y (local fields and the pulled f, h, l into per-warp
+// shared-memory rings) and then phase B for row y - 1, whose neighbours are
+// all in the rings.  The pulled f, h, l are therefore read from global memory
+// once, the y-halo costs 2 rows per segment instead of 2 per 30-row tile,
+// and the warps synchronise only with __syncwarp.  Rings per warp:
+//   lag  lagged phi, T of rows y & 3, columns x0-2 .. x0+31
+//   loc  dphi, dT, C, f_s, p, S, mdot of rows y mod 3, columns x0-1 .. x0+30
+//   pop  the pulled (stored-form) f, h, l of rows y mod 2
+// ---------------------------------------------------------------------------------------
+#ifndef LB_SW
+#define LB_SW 4
+#endif
+#ifndef LB_SMINB
+#define LB_SMINB 4
+#endif
+
+struct WarpRing {
+    float lag[4][2][34];
+    real loc[3][7][32];
+    real pop[2][27][32];
+};
+
+constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
+
+__device__ __forceinline__ int mod3(int v) { return ((v % 3) + 3) % 3; }
+
+// Accessor of phase_b for the strip kernel.
+struct RingAcc {
+    const WarpRing &w;
+    int lane;
+    int sl[3], sg[3], sp;  // loc slots, lag slots (rows y-1, y, y+1), pop slot
+    __device__ real phip(int dy, int dx) const { return w.lag[sg[dy + 1]][0][lane + 1 + dx]; }
+    __device__ real Tp(int dy, int dx) const { return w.lag[sg[dy + 1]][1][lane + 1 + dx]; }
+    __device__ real dphi(int dy, int dx) const { return w.loc[sl[dy + 1]][0][lane + dx]; }
+    __device__ real dT(int dy, int dx) const { return w.loc[sl[dy + 1]][1][lane + dx]; }
+    __device__ real C(int dy, int dx) const { return w.loc[sl[dy + 1]][2][lane + dx]; }
+    __device__ real fs(int dy, int dx) const { return w.loc[sl[dy + 1]][3][lane + dx]; }
+    __device__ real p(int dy, int dx) const { return w.loc[sl[dy + 1]][4][lane + dx]; }
+    __device__ real S(int dy, int dx) const { return w.loc[sl[dy + 1]][5][lane + dx]; }
+    __device__ real mdot(int dy, int dx) const { return w.loc[sl[dy + 1]][6][lane + dx]; }
+    template <int S>
+    __device__ void pops(const Consts &, const float *__restrict__, int, int, long long, real v[9], real) const
+    {
+        constexpr int base = S == SET_F ? 0 : (S == SET_H ? 9 : 18);
+#pragma unroll
+        for (int i = 0; i < 9; i++) v[i] = w.pop[sp][base + i][lane];
+    }
+};
+
+// Lagged phi and T of the cell that wrote the population pulled into direction
+// I at row y, lane column: from the lag ring (own cell at a wall).
+template <int I, bool W>
+__device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int lane, int y, real &ph, real &tt)
+{
+    constexpr int ys_off = -cy(I);
+    const int ys = y + ys_off;
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
+        ph = w.lag[y & 3][0][lane + 1];
+        tt = w.lag[y & 3][1][lane + 1];
+    } else {
+        ph = w.lag[ys & 3][0][lane + 1 - cx(I)];
+        tt = w.lag[ys & 3][1][lane + 1 - cx(I)];
     }
 }
 
-constexpr size_t STEP_SMEM = sizeof(Tile);
+template <bool W>
+__device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w, int lane, int y, real phi_own,
+                                             real T_own, real &dph, real &dtt)
+{
+    real ph[9], tt[9];
+    lag_src<1, W>(K, w, lane, y, ph[1], tt[1]);
+    lag_src<2, W>(K, w, lane, y, ph[2], tt[2]);
+    lag_src<3, W>(K, w, lane, y, ph[3], tt[3]);
+    lag_src<4, W>(K, w, lane, y, ph[4], tt[4]);
+    lag_src<5, W>(K, w, lane, y, ph[5], tt[5]);
+    lag_src<6, W>(K, w, lane, y, ph[6], tt[6]);
+    lag_src<7, W>(K, w, lane, y, ph[7], tt[7]);
+    lag_src<8, W>(K, w, lane, y, ph[8], tt[8]);
+    dph = (wgt(1) * (ph[1] - phi_own) + wgt(2) * (ph[2] - phi_own) + wgt(3) * (ph[3] - phi_own) +
+           wgt(4) * (ph[4] - phi_own)) +
+          (wgt(5) * (ph[5] - phi_own) + wgt(6) * (ph[6] - phi_own) + wgt(7) * (ph[7] - phi_own) +
+           wgt(8) * (ph[8] - phi_own));
+    dtt = (wgt(1) * (tt[1] - T_own) + wgt(2) * (tt[2] - T_own) + wgt(3) * (tt[3] - T_own) + wgt(4) * (tt[4] - T_own)) +
+          (wgt(5) * (tt[5] - T_own) + wgt(6) * (tt[6] - T_own) + wgt(7) * (tt[7] - T_own) + wgt(8) * (tt[8] - T_own));
+}
+
+// WALLS = false: every row ys - 2 .. ye + 1 the segment touches lies inside the
+// lattice.  Segments are seg_h rows high; the launch covers segments seg_base ..
+// seg_base + gridDim.x / ngroups - 1.  MODE_FIELDS runs the same arithmetic up
+// to velocity and pressure and stores the macroscopic fields instead of colliding.
+template <int MODE, bool WALLS>
+__global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Consts K, const Buffers B, int seg_base,
+                                                                        int seg_h)
+{
+    extern __shared__ __align__(16) unsigned char lb_smem[];
+    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
+    const int lane = threadIdx.x;
+    // one-dimensional grid: strip groups of LB_SW strips fastest, then segments
+    const int ngroups = ((K.nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW;
+    const int group = (int)(blockIdx.x % (unsigned)ngroups);
+    const int seg = seg_base + (int)(blockIdx.x / (unsigned)ngroups);
+    const int x0 = (group * LB_SW + (int)threadIdx.y) * LB_TX;
+    if (x0 >= K.nx) return;  // the whole warp: no block-wide synchronisation is used
+    const int ys = seg * seg_h;
+    const int ye = min(ys + seg_h, K.ny);
+    const int ex = x0 - 1 + lane;
+    const int xg = ((ex % K.nx) + K.nx) % K.nx;
+    const bool b_lane = lane >= 1 && lane <= LB_TX && ex < K.nx;
+    const float *__restrict__ pin = B.pin;
+    const float *__restrict__ ain = B.ain;
+    const int xa = (((x0 - 2 + lane) % K.nx) + K.nx) % K.nx;
+    const int xb = (((x0 + 30 + (lane & 1)) % K.nx) + K.nx) % K.nx;
+
+    auto load_lag = [&](int yl) {
+        if (WALLS && (yl < 0 || yl >= K.ny)) return;
+        const long long ro = (long long)yl * K.pitch;
+        w.lag[yl & 3][0][lane] = __ldg(ain + AUX_PHI * K.plane + ro + xa);
+        w.lag[yl & 3][1][lane] = __ldg(ain + AUX_T * K.plane + ro + xa);
+        if (lane < 2) {
+            w.lag[yl & 3][0][32 + lane] = __ldg(ain + AUX_PHI * K.plane + ro + xb);
+            w.lag[yl & 3][1][32 + lane] = __ldg(ain + AUX_T * K.plane + ro + xb);
+        }
+    };
+
+    load_lag(ys - 2);
+    load_lag(ys - 1);
+    load_lag(ys);
+    for (int ya = ys - 1; ya <= ye; ya++) {
+        load_lag(ya + 1);
+        __syncwarp();
+        // ---- phase A, row ya ------------------------------------------------------------
+        if (!WALLS || (ya >= 0 && ya < K.ny)) {
+            const long long cell = (long long)ya * K.pitch + xg;
+            const real phi_p = w.lag[ya & 3][0][lane + 1];
+            const real T_p = w.lag[ya & 3][1][lane + 1];
+            real v[9];
+            real *pp = &w.pop[ya & 1][0][lane];
+            pull9<SET_F, WALLS>(K, pin, xg, ya, cell, v);
+#pragma unroll
+            for (int i = 0; i < 9; i++) pp[(0 + i) * 32] = v[i];
+            real dph, dtt;
+            lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
+            const real delta = sum9(v) + dph;
+            pull9<SET_H, WALLS>(K, pin, xg, ya, cell, v, T_p);
+#pragma unroll
+            for (int i = 0; i < 9; i++) pp[(9 + i) * 32] = v[i];
+            const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
+            const real ed = sum9(v) + K.rr * dtt + R(0.5) * Q_p;
+            pull9<SET_L, WALLS>(K, pin, xg, ya, cell, v);
+#pragma unroll
+            for (int i = 0; i < 9; i++) pp[(18 + i) * 32] = v[i];
+            const real sl = sum9(v);
+            const real fs_p = __ldg(ain + AUX_FS * K.plane + cell);
+            const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
+            const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
+            const int s3 = mod3(ya);
+            w.loc[s3][0][lane] = L.dphi;
+            w.loc[s3][1][lane] = L.dT;
+            w.loc[s3][2][lane] = L.C;
+            w.loc[s3][3][lane] = L.fs;
+            w.loc[s3][4][lane] = __ldg(ain + AUX_P * K.plane + cell);
+            w.loc[s3][5][lane] = __ldg(ain + AUX_S * K.plane + cell);
+            w.loc[s3][6][lane] = L.mdot;
+        }
+        __syncwarp();
+        // ---- phase B, row ya - 1 ----------------------------------------------------------
+        const int yb = ya - 1;
+        if (yb >= ys && yb < ye && b_lane) {
+            const RingAcc A{w, lane, {mod3(yb - 1), mod3(yb), mod3(yb + 1)}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, yb & 1};
+            phase_b<MODE, WALLS>(K, B, A, ex, yb, (long long)yb * K.pitch + ex);
+        }
+        __syncwarp();
+    }
+}
 
 // ---------------------------------------------------------------------------------------
 // Initialisation: equilibria of the initial fields (p = 0), written in natural
