@@ -24,10 +24,10 @@ struct lb_handle {
     float *pops[2] = {nullptr, nullptr};
     float *aux[2] = {nullptr, nullptr};
     float *fields = nullptr;     // 7 planes
-    double *partials = nullptr;  // reduction partials, red_blocks * NRED
+    double *partials = nullptr;  // reduction partials, red_parts * NRED
     double *red_out = nullptr;   // NRED doubles on the device
     unsigned *status = nullptr;
-    int red_blocks = 0;
+    int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
     int cur = 0;
     cudaStream_t stream = nullptr;
     double V0 = 0.0;
@@ -136,10 +136,13 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.T_sol = (real)p->T_sol; K.T_liq = (real)p->T_liq;
     K.k_p = (real)p->k_p; K.D_l = (real)p->D_l; K.D_s = (real)p->D_s;
     K.rr = (real)(p->rho_l * 2.0 * p->cp_s * p->cp_l / (p->cp_s + p->cp_l));
+    K.inv_rr = (real)((p->cp_s + p->cp_l) / (p->rho_l * 2.0 * p->cp_s * p->cp_l));
     K.inv_eps2 = (real)(1.0 / (p->eps * p->eps));
     K.inv_s2eps = (real)(1.0 / (std::sqrt(2.0) * p->eps));
     K.alpha = (real)(3.0 * std::sqrt(2.0) * p->eps / 4.0);
     K.tau_f = (real)(0.5 + 3.0 * p->mobility);
+    K.om_f = (real)(1.0 / (0.5 + 3.0 * p->mobility));
+    K.src_f = (real)(1.0 - 0.5 / (0.5 + 3.0 * p->mobility));
     K.sigma0 = (real)p->sigma0; K.sigma_T = (real)p->sigma_T; K.sigma_c = (real)p->sigma_c;
     K.T_ref = (real)p->T_ref; K.c_ref = (real)p->c_ref;
     K.gx = (real)p->gx; K.gy = (real)p->gy;
@@ -149,42 +152,23 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     return K;
 }
 
-#ifndef LB_SEGH
-#define LB_SEGH 32
-#endif
-#ifndef LB_SEGH_W
-#define LB_SEGH_W 4
-#endif
+// One strip-kernel launch covers the lattice: the two bands next to the walls
+// (blocks first) and the inner segments.  MODE_REDUCE caps the grid at one wave
+// of resident blocks, each block then owning several (strip group, segment)
+// pairs, and writes one partial per warp.
+static unsigned strip_blocks(const Consts &K) { return (unsigned)(lbk::strip_groups(K.nx) * lbk::strip_segments(K.ny)); }
 
-// Strip kernel launches.  The interior rows are cut into segments of LB_SEGH
-// rows: segments 1 .. j_max with (j_max + 1) H + 2 <= ny, whose rows and pull
-// sources (rows ys - 2 .. ye + 1) lie inside the lattice, run the wall-free
-// instantiation.  The rows below (0 .. H - 1) and above ((j_max + 1) H .. ny - 1)
-// run the instantiation with the wall rules in short segments of LB_SEGH_W
-// rows, so that these few rows are spread over many warps.
-template <int MODE>
-static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st)
+static unsigned reduce_blocks(const Consts &K)
 {
-    const int H = LB_SEGH, Hw = LB_SEGH_W;
-    static_assert(LB_SEGH % LB_SEGH_W == 0, "segment heights");
-    const unsigned ngroups = (unsigned)(((K.nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW);
-    const dim3 block(32, LB_SW, 1);
-    const int j_max = (K.ny - 2) / H - 1;
-    auto go = [&](bool walls, int seg_base, int nseg, int h) {
-        const dim3 grid(ngroups * (unsigned)nseg, 1, 1);
-        if (walls)
-            lbk::lb_strip_kernel<MODE, true><<<grid, block, lbk::STRIP_SMEM, st>>>(K, B, seg_base, h);
-        else
-            lbk::lb_strip_kernel<MODE, false><<<grid, block, lbk::STRIP_SMEM, st>>>(K, B, seg_base, h);
-    };
-    if (MODE == lbk::MODE_STEP && j_max >= 1) {
-        const int top0 = (j_max + 1) * H;  // first row above the interior segments
-        go(false, 1, j_max, H);
-        go(true, 0, H / Hw, Hw);
-        go(true, top0 / Hw, (K.ny - top0 + Hw - 1) / Hw, Hw);
-    } else {
-        go(true, 0, (K.ny + Hw - 1) / Hw, Hw);
-    }
+    const unsigned n = strip_blocks(K), cap = 152u * LB_SMINB;
+    return n < cap ? n : cap;
+}
+
+template <int MODE>
+static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials = nullptr)
+{
+    const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks(K) : strip_blocks(K);
+    lbk::lb_strip_kernel<MODE><<<grid, dim3(32, LB_SW, 1), lbk::STRIP_SMEM, st>>>(K, B, partials);
 }
 
 static int flat_blocks(long long n, int threads)
@@ -197,10 +181,16 @@ static int flat_blocks(long long n, int threads)
 static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
 {
     const Consts &K = h->K;
-    lbk::lb_reduce_partial_kernel<<<h->red_blocks, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
-                                                                                    h->partials);
+    lbk::Buffers B;
+    B.pin = h->pops[h->cur];
+    B.pout = nullptr;
+    B.ain = h->aux[h->cur];
+    B.aout = nullptr;
+    B.fields = nullptr;
+    B.status = h->status;
+    launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->partials);
     CK(h, cudaGetLastError());
-    lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_blocks, h->red_out);
+    lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_parts, h->red_out);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * lbk::NRED, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -228,7 +218,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
     const size_t plane_b = sizeof(float) * (size_t)K.plane;
-    h->red_blocks = flat_blocks(n, lbk::RED_THREADS);
+    h->red_parts = (int)reduce_blocks(K) * LB_SW;
 
     auto alloc = [&](void **p, size_t b) -> cudaError_t {
         cudaError_t e = cudaMalloc(p, b);
@@ -239,7 +229,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->pops[k], 36 * plane_b);
     for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->aux[k], lbk::NAUX * plane_b);
     if (e == cudaSuccess) e = alloc((void **)&h->fields, 7 * plane_b);
-    if (e == cudaSuccess) e = alloc((void **)&h->partials, sizeof(double) * lbk::NRED * h->red_blocks);
+    if (e == cudaSuccess) e = alloc((void **)&h->partials, sizeof(double) * lbk::NRED * h->red_parts);
     if (e == cudaSuccess) e = alloc((void **)&h->red_out, sizeof(double) * lbk::NRED);
     if (e == cudaSuccess) e = alloc((void **)&h->status, sizeof(unsigned));
     if (e != cudaSuccess) {

@@ -79,7 +79,8 @@ struct Consts {
     real T_sol, T_liq, k_p, D_l, D_s;
     real rr;                    // rho_ref Cp_ref
     real inv_eps2, inv_s2eps, alpha;
-    real tau_f;
+    real tau_f, om_f, src_f;    // tau_f, 1/tau_f, 1 - 1/(2 tau_f)
+    real inv_rr;                // 1 / (rho_ref Cp_ref)
     real sigma0, sigma_T, sigma_c, T_ref, c_ref, gx, gy;
     real expand;                // 1 - rho_s / rho_l
     int fs_mod, phase_change;
@@ -106,6 +107,11 @@ __device__ __forceinline__ int wrapx(int x, int nx)
 
 __device__ __forceinline__ real clamp01(real v) { return fmin(fmax(v, R(0.0)), R(1.0)); }
 
+// Correctly rounded reciprocal (a division a / b below is a * rcp(b), within
+// one unit in the last place of the quotient).
+__device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
+
 // Bottom-wall temperature at continuous abscissa x.
 __device__ __forceinline__ real wall_T_bottom(const Consts &K, real x)
 {
@@ -122,7 +128,7 @@ __device__ __forceinline__ void invert_enthalpy(const Consts &K, real ed, real T
 {
     const real Al = chi * K.rcp_l + (R(1.0) - chi) * K.rcp_g;
     if (!K.phase_change) {
-        dT = (ed + (K.rr - Al) * T_p) / Al;
+        dT = (ed + (K.rr - Al) * T_p) * rcp(Al);
         fs = R(0.0);
         return;
     }
@@ -132,13 +138,13 @@ __device__ __forceinline__ void invert_enthalpy(const Consts &K, real ed, real T
     const real em_l = ed + K.rr * T_p - K.lat_l * (dchi + fs_p) - Al * K.T_liq;  // e - E_l
     if (em_s < R(0.0)) {
         fs = chi;
-        dT = (ed + lat_p + (K.rr - As) * T_p) / As;
+        dT = (ed + lat_p + (K.rr - As) * T_p) * rcp(As);
     } else if (em_l > R(0.0)) {
         fs = R(0.0);
-        dT = (ed - K.lat_l * (dchi + fs_p) + (K.rr - Al) * T_p) / Al;
+        dT = (ed - K.lat_l * (dchi + fs_p) + (K.rr - Al) * T_p) * rcp(Al);
     } else {
         const real d = Al * K.T_liq - As * K.T_sol + chi * K.latent_l;
-        const real r = (d < R(1e-14) * fmax(R(1.0), fabs(em_s))) ? R(1.0) : em_s / d;
+        const real r = (d < R(1e-14) * fmax(R(1.0), fabs(em_s))) ? R(1.0) : em_s * rcp(d);
         fs = chi * (R(1.0) - r);
         dT = (K.T_sol - T_p) + r * (K.T_liq - K.T_sol);
     }
@@ -258,7 +264,7 @@ __device__ __forceinline__ Local local_fields(const Consts &K, real phi_p, real 
     const real dchi = inside ? R(0.5) * delta : chi - chi_p;
     invert_enthalpy(K, ed, T_p, chi_p, fs_p, chi, dchi, o.dT, o.fs);
     o.mdot = K.phase_change ? K.expand * (o.fs - fs_p) : R(0.0);
-    o.dphi = (delta + R(0.5) * o.mdot * phi_p) / (R(1.0) - R(0.5) * o.mdot);
+    o.dphi = (delta + R(0.5) * o.mdot * phi_p) * rcp(R(1.0) - R(0.5) * o.mdot);
     o.C = sl;
     return o;
 }
@@ -290,7 +296,9 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     return c;
 }
 
-enum { MODE_STEP = 0, MODE_FIELDS = 1 };
+// MODE_STEP collides and streams; MODE_FIELDS stores the macroscopic fields of the
+// current state instead; MODE_REDUCE runs phase A only and sums the diagnostics.
+enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_REDUCE = 2 };
 
 // ---------------------------------------------------------------------------------------
 // Phase B of one interior cell: gradients, forces, velocity, pressure and the
@@ -372,10 +380,12 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     const real g2 = gpx * gpx + gpy * gpy;
     const real inv = rsqrt(g2 + R(1e-6));  // regularised normal: smooth away from the interface
     const real nxv = gpx * inv, nyv = gpy * inv;
-    // chemical potential: the cubic term and the Laplacian nearly cancel across the
-    // interface, so this short expression is evaluated in FP64
-    const double phd = (double)phi_p + (double)dphi;
-    const real muphi = (real)((phd * phd * phd - phd) * (double)K.inv_eps2 - (double)lphi);
+    // chemical potential (phi^3 - phi)/eps^2 - lap phi: the cubic term as
+    // phi (phi - 1)(phi + 1), each factor formed as (phi_st -/+ 1) + phi_lo with
+    // phi_st -/+ 1 exact near the bulk values, so that the term keeps its relative
+    // precision where it is small (phi near +-1)
+    const real phi2m1 = ((phi_st - R(1.0)) + phi_lo) * ((phi_st + R(1.0)) + phi_lo);  // phi^2 - 1
+    const real muphi = phi * phi2m1 * K.inv_eps2 - lphi;
     const real sigma = K.sigma0 + K.sigma_T * (T - K.T_ref) + K.sigma_c * (C - K.c_ref);
     const real gsx = K.sigma_T * gTx + K.sigma_c * gCx;
     const real gsy = K.sigma_T * gTy + K.sigma_c * gCy;
@@ -408,7 +418,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         jy += (real)cy(i) * dg[i];
         if (i) sg += dg[i];
     }
-    const real inv_rho = R(1.0) / rho;
+    const real inv_rho = rcp(rho);
     const real usx = (jx + R(0.5) * Fx) * inv_rho, usy = (jy + R(0.5) * Fy) * inv_rho;
     const real ffx = -fs * usx, ffy = -fs * usy;       // f = f_s (0 - u*)
     const real ux = usx + R(0.5) * ffx, uy = usy + R(0.5) * ffy;
@@ -440,7 +450,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         return;
     }
 
-    const real om_g = R(1.0) / tau_g, src_g = R(1.0) - R(0.5) * om_g;
+    const real om_g = rcp(tau_g), src_g = R(1.0) - R(0.5) * om_g;
     float *__restrict__ pout = B.pout;
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -459,10 +469,10 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
     {
         const real ux_p = __ldg(B.ain + AUX_UX * K.plane + cell), uy_p = __ldg(B.ain + AUX_UY * K.plane + cell);
-        const real kf = (R(1.0) / R(3.0)) * (R(1.0) - phi * phi) * K.inv_s2eps;
+        const real kf = -(R(1.0) / R(3.0)) * phi2m1 * K.inv_s2eps;
         const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
         const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
-        const real om = R(1.0) / K.tau_f, src = R(1.0) - R(0.5) * om;
+        const real om = K.om_f, src = K.src_f;
         // d_i = f_i - w_i phi_st: the stored deviation plus w_i (phi^n(source) - phi_st);
         // stored as f_i* - w_i phi_st
         real f[9];
@@ -482,11 +492,12 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
         const real C_p = __ldg(B.ain + AUX_C * K.plane + cell);
         const real keff = R(1.0) - fs * (R(1.0) - K.k_p);
+        const real inv_keff = rcp(keff);
         const real De = fs * K.k_p * K.D_s + (R(1.0) - fs) * K.D_l;
-        const real tau_l = R(0.5) + R(3.0) * De / keff;
-        const real om_l = R(1.0) / tau_l, src_l = R(1.0) - R(0.5) * om_l;
-        const real Rx = (R(1.0) - phi) * C * nxv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfx / keff;
-        const real Ry = (R(1.0) - phi) * C * nyv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfy / keff;
+        const real tau_l = R(0.5) + R(3.0) * De * inv_keff;
+        const real om_l = rcp(tau_l), src_l = R(1.0) - R(0.5) * om_l;
+        const real Rx = (R(1.0) - phi) * C * nxv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfx * inv_keff;
+        const real Ry = (R(1.0) - phi) * C * nyv * K.inv_s2eps + (K.k_p - R(1.0)) * C * gfy * inv_keff;
         const real bx = (C * ux - C_p * ux_p) + (R(1.0) / R(3.0)) * Rx;
         const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
         real l[9];
@@ -506,8 +517,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // deviations from w_i rr T_st (and the latent reference for i = 0).
     const real Q = rhocp * T * mdot;
     {
-        const real tau_hb = R(0.5) + R(3.0) * lam / rr;
-        const real om_a = R(1.0) / tau_hb, om_s = R(2.0) - om_a;
+        const real tau_hb = R(0.5) + R(3.0) * lam * K.inv_rr;
+        const real om_a = rcp(tau_hb), om_s = R(2.0) - om_a;
         const real src_h = R(1.0) - R(0.5) * om_s;
         const real rcT = rhocp * T;
         real h[9], dh[9], deq[9];
@@ -566,16 +577,15 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
 
 // ---------------------------------------------------------------------------------------
-// Strip form of the step.  Each warp owns a strip of 30 columns (plus one halo
-// column on each side) and walks down a segment of rows; per row it runs
-// phase A for row y (local fields and the pulled f, h, l into per-warp
-// shared-memory rings) and then phase B for row y - 1, whose neighbours are
-// all in the rings.  The pulled f, h, l are therefore read from global memory
-// once, the y-halo costs 2 rows per segment instead of 2 per 30-row tile,
-// and the warps synchronise only with __syncwarp.  Rings per warp:
+// Strip form of the step (see the top of this file).  Rings per warp:
 //   lag  lagged phi, T of rows y & 3, columns x0-2 .. x0+31
 //   loc  dphi, dT, C, f_s, p, S, mdot of rows y mod 3, columns x0-1 .. x0+30
-//   pop  the pulled (stored-form) f, h, l of rows y mod 2
+//   pop  the pulled (stored-form) f, h, l of rows y & 1
+// One launch covers the lattice.  Per group of LB_SW strips it has two bands with
+// the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of LB_SEGH
+// rows inside 2 .. ny-3, whose rows and pull sources (ys - 2 .. ye + 1) all lie
+// inside the lattice and which run without any wall rule.  Blocks are numbered
+// strip group fastest, the two bands first.
 // ---------------------------------------------------------------------------------------
 #ifndef LB_SW
 #define LB_SW 4
@@ -583,6 +593,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #ifndef LB_SMINB
 #define LB_SMINB 4
 #endif
+#ifndef LB_SEGH
+#define LB_SEGH 32
+#endif
+
+constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
 
 struct WarpRing {
     float lag[4][2][34];
@@ -592,7 +607,32 @@ struct WarpRing {
 
 constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
 
+__host__ __device__ inline int strip_groups(int nx) { return ((nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW; }
+__host__ __device__ inline int strip_segments(int ny) { return 2 + (ny >= 5 ? (ny - 4 + LB_SEGH - 1) / LB_SEGH : 0); }
+
+// Rows [ys, ye) of segment s (empty when ys >= ye).
+__device__ __forceinline__ void segment_rows(int ny, int s, int &ys, int &ye)
+{
+    if (s == 0) {
+        ys = 0;
+        ye = min(2, ny);
+    } else if (s == 1) {
+        ys = max(2, ny - 2);
+        ye = ny;
+    } else {
+        ys = 2 + (s - 2) * LB_SEGH;
+        ye = min(ys + LB_SEGH, ny - 2);
+    }
+}
+
 __device__ __forceinline__ int mod3(int v) { return ((v % 3) + 3) % 3; }
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Accessor of phase_b for the strip kernel.
 struct RingAcc {
@@ -654,25 +694,12 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w,
           (wgt(5) * (tt[5] - T_own) + wgt(6) * (tt[6] - T_own) + wgt(7) * (tt[7] - T_own) + wgt(8) * (tt[8] - T_own));
 }
 
-// WALLS = false: every row ys - 2 .. ye + 1 the segment touches lies inside the
-// lattice.  Segments are seg_h rows high; the launch covers segments seg_base ..
-// seg_base + gridDim.x / ngroups - 1.  MODE_FIELDS runs the same arithmetic up
-// to velocity and pressure and stores the macroscopic fields instead of colliding.
+// Phase A / phase B sweep of one warp over rows [ys, ye) of its strip.  WALLS =
+// false: every row ys - 2 .. ye + 1 lies inside the lattice.
 template <int MODE, bool WALLS>
-__global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Consts K, const Buffers B, int seg_base,
-                                                                        int seg_h)
+__device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing &w, int lane, int x0, int ys, int ye,
+                                           double acc[NRED])
 {
-    extern __shared__ __align__(16) unsigned char lb_smem[];
-    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
-    const int lane = threadIdx.x;
-    // one-dimensional grid: strip groups of LB_SW strips fastest, then segments
-    const int ngroups = ((K.nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW;
-    const int group = (int)(blockIdx.x % (unsigned)ngroups);
-    const int seg = seg_base + (int)(blockIdx.x / (unsigned)ngroups);
-    const int x0 = (group * LB_SW + (int)threadIdx.y) * LB_TX;
-    if (x0 >= K.nx) return;  // the whole warp: no block-wide synchronisation is used
-    const int ys = seg * seg_h;
-    const int ye = min(ys + seg_h, K.ny);
     const int ex = x0 - 1 + lane;
     const int xg = ((ex % K.nx) + K.nx) % K.nx;
     const bool b_lane = lane >= 1 && lane <= LB_TX && ex < K.nx;
@@ -692,10 +719,12 @@ __global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Co
         }
     };
 
-    load_lag(ys - 2);
-    load_lag(ys - 1);
-    load_lag(ys);
-    for (int ya = ys - 1; ya <= ye; ya++) {
+    // MODE_REDUCE needs phase A on the segment's own rows only
+    const int ya0 = MODE == MODE_REDUCE ? ys : ys - 1;
+    const int ya1 = MODE == MODE_REDUCE ? ye - 1 : ye;
+    load_lag(ya0 - 1);
+    load_lag(ya0);
+    for (int ya = ya0; ya <= ya1; ya++) {
         load_lag(ya + 1);
         __syncwarp();
         // ---- phase A, row ya ------------------------------------------------------------
@@ -706,40 +735,91 @@ __global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Co
             real v[9];
             real *pp = &w.pop[ya & 1][0][lane];
             pull9<SET_F, WALLS>(K, pin, xg, ya, cell, v);
+            if (MODE != MODE_REDUCE) {
 #pragma unroll
-            for (int i = 0; i < 9; i++) pp[(0 + i) * 32] = v[i];
+                for (int i = 0; i < 9; i++) pp[(0 + i) * 32] = v[i];
+            }
             real dph, dtt;
             lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
             const real delta = sum9(v) + dph;
             pull9<SET_H, WALLS>(K, pin, xg, ya, cell, v, T_p);
+            if (MODE != MODE_REDUCE) {
 #pragma unroll
-            for (int i = 0; i < 9; i++) pp[(9 + i) * 32] = v[i];
+                for (int i = 0; i < 9; i++) pp[(9 + i) * 32] = v[i];
+            }
             const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
             const real ed = sum9(v) + K.rr * dtt + R(0.5) * Q_p;
             pull9<SET_L, WALLS>(K, pin, xg, ya, cell, v);
+            if (MODE != MODE_REDUCE) {
 #pragma unroll
-            for (int i = 0; i < 9; i++) pp[(18 + i) * 32] = v[i];
+                for (int i = 0; i < 9; i++) pp[(18 + i) * 32] = v[i];
+            }
             const real sl = sum9(v);
             const real fs_p = __ldg(ain + AUX_FS * K.plane + cell);
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
-            const int s3 = mod3(ya);
-            w.loc[s3][0][lane] = L.dphi;
-            w.loc[s3][1][lane] = L.dT;
-            w.loc[s3][2][lane] = L.C;
-            w.loc[s3][3][lane] = L.fs;
-            w.loc[s3][4][lane] = __ldg(ain + AUX_P * K.plane + cell);
-            w.loc[s3][5][lane] = __ldg(ain + AUX_S * K.plane + cell);
-            w.loc[s3][6][lane] = L.mdot;
+            if (MODE == MODE_REDUCE) {
+                if (b_lane) {
+                    const double phid = (double)phi_p + (double)L.dphi;
+                    acc[0] += phid;
+                    acc[1] += (double)ed + (double)K.rr * (double)T_p + (double)K.lat_l * ((double)chi_p - (double)fs_p);
+                    acc[2] += (double)L.C;
+                    acc[3] += (double)L.fs;
+                    acc[4] += (double)clamp01(R(0.5) * (R(1.0) + (real)phid));
+                    if (ex == K.nx / 2) acc[5] += (double)L.fs;
+                }
+            } else {
+                const int s3 = mod3(ya);
+                w.loc[s3][0][lane] = L.dphi;
+                w.loc[s3][1][lane] = L.dT;
+                w.loc[s3][2][lane] = L.C;
+                w.loc[s3][3][lane] = L.fs;
+                w.loc[s3][4][lane] = __ldg(ain + AUX_P * K.plane + cell);
+                w.loc[s3][5][lane] = __ldg(ain + AUX_S * K.plane + cell);
+                w.loc[s3][6][lane] = L.mdot;
+            }
         }
         __syncwarp();
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
-        if (yb >= ys && yb < ye && b_lane) {
+        if (MODE != MODE_REDUCE && yb >= ys && yb < ye && b_lane) {
             const RingAcc A{w, lane, {mod3(yb - 1), mod3(yb), mod3(yb + 1)}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, yb & 1};
             phase_b<MODE, WALLS>(K, B, A, ex, yb, (long long)yb * K.pitch + ex);
         }
         __syncwarp();
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Consts K, const Buffers B,
+                                                                        double *__restrict__ partials)
+{
+    extern __shared__ __align__(16) unsigned char lb_smem[];
+    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
+    const int lane = threadIdx.x;
+    const int ngroups = strip_groups(K.nx);
+    const int nblocks = ngroups * strip_segments(K.ny);
+    double acc[NRED] = {0, 0, 0, 0, 0, 0};
+    // a block may own several (group, segment) pairs when the grid is capped
+    for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        const int group = b % ngroups, seg = b / ngroups;
+        const int x0 = (group * LB_SW + (int)threadIdx.y) * LB_TX;
+        int ys, ye;
+        segment_rows(K.ny, seg, ys, ye);
+        if (x0 >= K.nx || ys >= ye) continue;  // the whole warp: warps never synchronise with one another
+        if (seg < 2)
+            strip_rows<MODE, true>(K, B, w, lane, x0, ys, ye, acc);
+        else
+            strip_rows<MODE, false>(K, B, w, lane, x0, ys, ye, acc);
+        __syncwarp();
+    }
+    if (MODE == MODE_REDUCE) {
+        // one partial per warp, in a fixed place: the final pass adds them in order
+#pragma unroll
+        for (int q = 0; q < NRED; q++) {
+            const double s = warp_sum(acc[q]);
+            if (lane == 0) partials[((long long)blockIdx.x * LB_SW + threadIdx.y) * NRED + q] = s;
+        }
     }
 }
 
@@ -831,53 +911,9 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
 }
 
 // ---------------------------------------------------------------------------------------
-// Diagnostics: FP64 sums of phi, rho H, C, f_s, chi and the front column.
-// Pass 1 writes one partial per block (fixed order); pass 2 adds them in order.
+// Diagnostics, final pass: adds the per-warp partials of MODE_REDUCE in a fixed order.
 // ---------------------------------------------------------------------------------------
-constexpr int NRED = 6;
 constexpr int RED_THREADS = 256;
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__global__ void __launch_bounds__(RED_THREADS) lb_reduce_partial_kernel(const Consts K, const float *__restrict__ pin,
-                                                                         const float *__restrict__ ain,
-                                                                         double *__restrict__ partials)
-{
-    __shared__ double sh[RED_THREADS / 32][NRED];
-    const long long n = (long long)K.nx * K.ny;
-    const int xc = K.nx / 2;
-    double acc[NRED] = {0, 0, 0, 0, 0, 0};
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(k / K.nx), x = (int)(k % K.nx);
-        const long long cell = (long long)y * K.pitch + x;
-        const CellA c = cell_a(K, pin, ain, x, y, cell);
-        const Local &L = c.L;
-        const double phid = (double)c.phi_p + (double)L.dphi;
-        acc[0] += phid;
-        acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
-        acc[2] += (double)L.C;
-        acc[3] += (double)L.fs;
-        acc[4] += (double)clamp01(R(0.5) * (R(1.0) + (real)phid));
-        if (x == xc) acc[5] += (double)L.fs;
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NRED; q++) {
-        double s = warp_sum(acc[q]);
-        if (lane == 0) sh[w][q] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < NRED) {
-        double s = 0.0;
-        for (int j = 0; j < RED_THREADS / 32; j++) s += sh[j][threadIdx.x];
-        partials[(long long)blockIdx.x * NRED + threadIdx.x] = s;
-    }
-}
 
 __global__ void __launch_bounds__(RED_THREADS) lb_reduce_final_kernel(const double *__restrict__ partials, int nblocks,
                                                                        double *__restrict__ out)

@@ -118,11 +118,24 @@ def _is_torch(a) -> bool:
     return type(a).__module__.startswith("torch")
 
 
+def _is_cuda_tensor(a) -> bool:
+    return _is_torch(a) and bool(a.is_cuda)
+
+
+def _host_array(v) -> np.ndarray:
+    """A float32 numpy view of host data; a torch CPU tensor (pinned or not) is
+    viewed in place, so a pinned buffer stays the one the copy reads from."""
+    if _is_torch(v):
+        v = v.detach().numpy()
+    return np.asarray(v, dtype=np.float32)
+
+
 class Solver:
     """One lattice on the GPU.
 
     ``fields`` maps phi, T, C (and optionally ux, uy) to ny x nx arrays: numpy
-    arrays (host) or float32 contiguous torch CUDA tensors (device).  ``stream``
+    arrays or torch CPU tensors (host; pinned tensors copy fastest), or float32
+    contiguous torch CUDA tensors (device).  ``stream``
     is a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default
     stream)."""
 
@@ -132,7 +145,7 @@ class Solver:
         n = self.nx * self.ny
         self._grid, self._params = make_grid(grid), make_params(params)
         keep = {}
-        on_device = any(_is_torch(fields.get(k)) for k in ("phi", "T", "C"))
+        on_device = any(_is_cuda_tensor(fields.get(k)) for k in ("phi", "T", "C"))
         for k in ("phi", "T", "C", "ux", "uy"):
             v = fields.get(k)
             if v is None:
@@ -143,7 +156,7 @@ class Solver:
                 if v.numel() != n:
                     raise ValueError("field %s has %d values, expected %d" % (k, v.numel(), n))
             else:
-                v = np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(-1))
+                v = np.ascontiguousarray(_host_array(v).reshape(-1))
                 if v.size != n:
                     raise ValueError("field %s has %d values, expected %d" % (k, v.size, n))
             keep[k] = v
@@ -211,9 +224,35 @@ class Solver:
     def step(self, n: int = 1):
         self._check(load().lb_step(self._h, int(n)))
 
-    def fields(self, device: bool = False, names=FIELD_NAMES):
+    def fields(self, device: bool = False, names=FIELD_NAMES, out=None):
         """Macroscopic fields of the current state as (ny, nx) arrays: numpy on
-        the host, or torch CUDA tensors with ``device=True``."""
+        the host, or torch CUDA tensors with ``device=True``.  ``out`` supplies
+        the destinations instead (a dict of contiguous float32 arrays of nx*ny
+        values: all numpy / torch CPU tensors, e.g. pinned, or all CUDA tensors)."""
+        if out is not None:
+            dev = [_is_cuda_tensor(v) for v in out.values()]
+            if dev and any(dev) != all(dev):
+                raise ValueError("fields(out=...) mixes host and device destinations")
+            device = bool(dev) and all(dev)
+            ptrs = []
+            for k in FIELD_NAMES:
+                v = out.get(k)
+                if v is None:
+                    ptrs.append(None)
+                    continue
+                if device:
+                    ok = v.dtype.__str__() == "torch.float32" and v.is_contiguous() and v.numel() == self.nx * self.ny
+                    ptr = v.data_ptr()
+                else:
+                    h = v.detach().numpy() if _is_torch(v) else v  # a view: the call writes into v
+                    ok = (isinstance(h, np.ndarray) and h.dtype == np.float32 and h.flags["C_CONTIGUOUS"]
+                          and h.size == self.nx * self.ny)
+                    ptr = h.ctypes.data
+                if not ok:
+                    raise ValueError("fields(out=...): %s must be contiguous float32 with nx*ny values" % k)
+                ptrs.append(C.c_void_p(ptr))
+            self._check(load().lb_get_fields(self._h, *ptrs, 1 if device else 0))
+            return out
         if device:
             import torch
             out = {k: torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda") for k in names}

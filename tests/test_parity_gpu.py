@@ -127,12 +127,13 @@ def test_parity_100_steps(oracle_mod, name, make, steps):
 
 
 @pytest.mark.parametrize("shape", [(1, 40), (2, 17), (31, 1), (5, 3), (30, 30), (31, 31), (60, 61),
-                                   (240, 66), (121, 67), (125, 97)])
+                                   (61, 5), (240, 36), (121, 37), (125, 97)])
 def test_parity_edge_shapes(oracle_mod, shape):
     """A one-column lattice (x-periodic onto itself), a one-row lattice (both
     walls on the same row), shapes at and just past a 30-column warp strip and
-    a 4-strip block, and lattices just tall enough (66 rows and up) for the
-    wall-free 32-row segments, with 2, 3 and 33 rows above the last of them.
+    a 4-strip block, and row counts at the edges of the row layout: one inner
+    row (ny = 5), exactly one 32-row inner segment (ny = 36), and a last inner
+    segment of 1 row (ny = 37) or of 29 rows (ny = 97).
     Equal solid and liquid densities: in a one-row lattice the expansion
     source drives phi far above 1 and makes the case ill-conditioned."""
     nx, ny = shape
