@@ -167,6 +167,14 @@ static unsigned reduce_blocks(const Consts &K)
 template <int MODE>
 static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials = nullptr)
 {
+    if (lbk::STRIP_SMEM > 48 * 1024) {  // rings above the default dynamic shared-memory limit need the opt-in
+        static bool opted = false;      // per instantiation (one per mode)
+        if (!opted) {
+            cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbk::STRIP_SMEM);
+            opted = true;
+        }
+    }
     const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks(K) : strip_blocks(K);
     lbk::lb_strip_kernel<MODE><<<grid, dim3(32, LB_SW, 1), lbk::STRIP_SMEM, st>>>(K, B, partials);
 }

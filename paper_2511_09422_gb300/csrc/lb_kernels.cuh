@@ -112,6 +112,21 @@ __device__ __forceinline__ real clamp01(real v) { return fmin(fmax(v, R(0.0)), R
 __device__ __forceinline__ float rcp(float v) { return __frcp_rn(v); }
 __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
 
+// Asynchronous 4-byte global -> shared copies (sm_80+ cp.async, cached in L1):
+// the strip sweep stages the next row's inputs with them, so their latency
+// overlaps the current row's arithmetic without holding registers.
+__device__ __forceinline__ void cp_async4(void *smem, const float *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Bottom-wall temperature at continuous abscissa x.
 __device__ __forceinline__ real wall_T_bottom(const Consts &K, real x)
 {
@@ -178,25 +193,37 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // at a wall (half-way bounce-back).  For the enthalpy at a Dirichlet wall the
 // anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (wall temperature at the
 // link midpoint) is applied in deviation form relative to w rr T_own.
+// pull_src gives the address read, abb_fix the wall rule applied to its value.
+template <int S, int I, bool W>
+__device__ __forceinline__ const float *pull_src(const Consts &K, const float *__restrict__ pin, int x, int y,
+                                                 long long cell)
+{
+    constexpr int ys_off = -cy(I);
+    const int ys = y + ys_off;
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return pin + (long long)(S * 9 + opp(I)) * K.plane + cell;
+    return pin + (long long)(S * 9 + I) * K.plane + (long long)ys * K.pitch + wrapx(x - cx(I), K.nx);
+}
+
+template <int S, int I, bool W>
+__device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, real T_own)
+{
+    constexpr int ys_off = -cy(I);
+    const int ys = y + ys_off;
+    if (S == SET_H && W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
+        const bool bottom = ys < 0;
+        if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
+            const real Tw = bottom ? wall_T_bottom(K, (real)x - R(0.5) * (real)cx(I)) : K.T_top;
+            return -v + R(2.0) * wgt(I) * K.rr * (Tw - T_own);
+        }
+    }
+    return v;
+}
+
 template <int S, int I, bool W>
 __device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
                                      real T_own)
 {
-    constexpr int ys_off = -cy(I);
-    const int ys = y + ys_off;
-    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
-        real v = __ldg(pin + (long long)(S * 9 + opp(I)) * K.plane + cell);
-        if (S == SET_H) {
-            const bool bottom = ys < 0;
-            if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
-                real Tw = bottom ? wall_T_bottom(K, (real)x - R(0.5) * (real)cx(I)) : K.T_top;
-                v = -v + R(2.0) * wgt(I) * K.rr * (Tw - T_own);
-            }
-        }
-        return v;
-    }
-    const int xs = wrapx(x - cx(I), K.nx);
-    return __ldg(pin + (long long)(S * 9 + I) * K.plane + (long long)ys * K.pitch + xs);
+    return abb_fix<S, I, W>(K, __ldg(pull_src<S, I, W>(K, pin, x, y, cell)), x, y, T_own);
 }
 
 // W = false: the caller guarantees that no source row lies beyond a wall.
@@ -296,6 +323,9 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     return c;
 }
 
+// Own-cell lagged values staged for phase B (the accessor's aux(k)).
+enum { AX_Q = 0, AX_FS = 1, AX_UX = 2, AX_UY = 3, AX_C = 4, NAX = 5 };
+
 // MODE_STEP collides and streams; MODE_FIELDS stores the macroscopic fields of the
 // current state instead; MODE_REDUCE runs phase A only and sums the diagnostics.
 enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_REDUCE = 2 };
@@ -305,7 +335,7 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_REDUCE = 2 };
 // collision of the four sets (or, in MODE_FIELDS, the macroscopic fields).  The
 // accessor A supplies the step's local fields of the cell and its neighbours
 // (offsets dy, dx in {-1, 0, 1}, already mirrored at walls) and the cell's
-// pulled f, h, l; g is pulled here.
+// pulled f, h, l and g, and its own lagged Q, f_s, u and C.
 // ---------------------------------------------------------------------------------------
 template <int MODE, bool WALLS, class Acc>
 __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const Acc &A, int x, int y, long long cell)
@@ -406,7 +436,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // lagged pressure, so that the momentum and the pressure are sums of small terms
     const real p_p = A.p(0, 0);
     real g[9], dg[9];
-    pull9<SET_G, WALLS>(K, B.pin, x, y, cell, g);
+    A.gpops(g);
     real jx = R(0.0), jy = R(0.0), sg = R(0.0);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -468,7 +498,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
     // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
     {
-        const real ux_p = __ldg(B.ain + AUX_UX * K.plane + cell), uy_p = __ldg(B.ain + AUX_UY * K.plane + cell);
+        const real ux_p = A.aux(AX_UX), uy_p = A.aux(AX_UY);
         const real kf = -(R(1.0) / R(3.0)) * phi2m1 * K.inv_s2eps;
         const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
         const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
@@ -490,7 +520,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         }
 
         // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
-        const real C_p = __ldg(B.ain + AUX_C * K.plane + cell);
+        const real C_p = A.aux(AX_C);
         const real keff = R(1.0) - fs * (R(1.0) - K.k_p);
         const real inv_keff = rcp(keff);
         const real De = fs * K.k_p * K.D_s + (R(1.0) - fs) * K.D_l;
@@ -544,8 +574,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
         // moves from w_0 rr T_p + rho_l L (chi_p - fs_p) to w_0 rr T_st + rho_l L (chi_st - f_s)
         {
-            const real Q_p = __ldg(B.ain + AUX_Q * K.plane + cell);
-            const real fs_p = __ldg(B.ain + AUX_FS * K.plane + cell);
+            const real Q_p = A.aux(AX_Q);
+            const real fs_p = A.aux(AX_FS);
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const real chi_n = clamp01(R(0.5) * (R(1.0) + phi_st));
             // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
@@ -577,10 +607,16 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
 
 // ---------------------------------------------------------------------------------------
-// Strip form of the step (see the top of this file).  Rings per warp:
-//   lag  lagged phi, T of rows y & 3, columns x0-2 .. x0+31
-//   loc  dphi, dT, C, f_s, p, S, mdot of rows y mod 3, columns x0-1 .. x0+30
-//   pop  the pulled (stored-form) f, h, l of rows y & 1
+// Strip form of the step (see the top of this file).  Every global value a
+// warp needs is staged into its rings by cp.async one row ahead of its use:
+// while the warp computes phase A of row y and phase B of row y - 1, the
+// copies for phase A of row y + 1 (and phase B of row y) are in flight.
+// Rings per warp (columns x0-2 .. x0+31 for lag, the warp's 32 lanes otherwise):
+//   lag  lagged phi, T                                     rows y & 7
+//   loc  dphi, dT, C, f_s, mdot (phase A) and staged p, S   rows y & 3
+//   pop  staged pulls of f, h, l (stored form)              rows y mod 3
+//   ax   staged own-cell Q, f_s, u_x, u_y, C                rows y mod 3
+//   gp   staged pulls of g                                  rows y & 1
 // One launch covers the lattice.  Per group of LB_SW strips it has two bands with
 // the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of LB_SEGH
 // rows inside 2 .. ny-3, whose rows and pull sources (ys - 2 .. ye + 1) all lie
@@ -588,7 +624,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 // strip group fastest, the two bands first.
 // ---------------------------------------------------------------------------------------
 #ifndef LB_SW
-#define LB_SW 4
+#define LB_SW 2
 #endif
 #ifndef LB_SMINB
 #define LB_SMINB 4
@@ -600,9 +636,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
 
 struct WarpRing {
-    float lag[4][2][34];
-    real loc[3][7][32];
-    real pop[2][27][32];
+    float lag[8][2][34];
+    real loc[4][7][32];
+    float pop[3][27][32];
+    float ax[3][NAX][32];
+    float gp[2][9][32];
 };
 
 constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
@@ -638,7 +676,7 @@ __device__ __forceinline__ double warp_sum(double v)
 struct RingAcc {
     const WarpRing &w;
     int lane;
-    int sl[3], sg[3], sp;  // loc slots, lag slots (rows y-1, y, y+1), pop slot
+    int sl[3], sg[3], sp, sgp;  // loc slots, lag slots (rows y-1, y, y+1), pop / ax slot, gp slot
     __device__ real phip(int dy, int dx) const { return w.lag[sg[dy + 1]][0][lane + 1 + dx]; }
     __device__ real Tp(int dy, int dx) const { return w.lag[sg[dy + 1]][1][lane + 1 + dx]; }
     __device__ real dphi(int dy, int dx) const { return w.loc[sl[dy + 1]][0][lane + dx]; }
@@ -655,7 +693,51 @@ struct RingAcc {
 #pragma unroll
         for (int i = 0; i < 9; i++) v[i] = w.pop[sp][base + i][lane];
     }
+    __device__ void gpops(real v[9]) const
+    {
+#pragma unroll
+        for (int i = 0; i < 9; i++) v[i] = w.gp[sgp][i][lane];
+    }
+    __device__ real aux(int k) const { return w.ax[sp][k][lane]; }
 };
+
+// Stage the 9 pulls of set S at (x, y) into dst[i * 32] (raw source values;
+// the anti-bounce-back rule is applied when they are read).
+template <int S, bool W>
+__device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
+                                       float *dst)
+{
+    cp_async4(dst + 0 * 32, pull_src<S, 0, W>(K, pin, x, y, cell));
+    cp_async4(dst + 1 * 32, pull_src<S, 1, W>(K, pin, x, y, cell));
+    cp_async4(dst + 2 * 32, pull_src<S, 2, W>(K, pin, x, y, cell));
+    cp_async4(dst + 3 * 32, pull_src<S, 3, W>(K, pin, x, y, cell));
+    cp_async4(dst + 4 * 32, pull_src<S, 4, W>(K, pin, x, y, cell));
+    cp_async4(dst + 5 * 32, pull_src<S, 5, W>(K, pin, x, y, cell));
+    cp_async4(dst + 6 * 32, pull_src<S, 6, W>(K, pin, x, y, cell));
+    cp_async4(dst + 7 * 32, pull_src<S, 7, W>(K, pin, x, y, cell));
+    cp_async4(dst + 8 * 32, pull_src<S, 8, W>(K, pin, x, y, cell));
+}
+
+// Apply the enthalpy wall rule to staged pulls in place (W only).
+template <bool W>
+__device__ __forceinline__ void abb_fix9(const Consts &K, float *v, int x, int y, real T_own)
+{
+    if (!W) return;
+    v[1 * 32] = abb_fix<SET_H, 1, W>(K, v[1 * 32], x, y, T_own);
+    v[2 * 32] = abb_fix<SET_H, 2, W>(K, v[2 * 32], x, y, T_own);
+    v[3 * 32] = abb_fix<SET_H, 3, W>(K, v[3 * 32], x, y, T_own);
+    v[4 * 32] = abb_fix<SET_H, 4, W>(K, v[4 * 32], x, y, T_own);
+    v[5 * 32] = abb_fix<SET_H, 5, W>(K, v[5 * 32], x, y, T_own);
+    v[6 * 32] = abb_fix<SET_H, 6, W>(K, v[6 * 32], x, y, T_own);
+    v[7 * 32] = abb_fix<SET_H, 7, W>(K, v[7 * 32], x, y, T_own);
+    v[8 * 32] = abb_fix<SET_H, 8, W>(K, v[8 * 32], x, y, T_own);
+}
+
+__device__ __forceinline__ real sum9s(const float *v)
+{
+    return v[0] + ((v[1 * 32] + v[2 * 32]) + (v[3 * 32] + v[4 * 32])) +
+           ((v[5 * 32] + v[6 * 32]) + (v[7 * 32] + v[8 * 32]));
+}
 
 // Lagged phi and T of the cell that wrote the population pulled into direction
 // I at row y, lane column: from the lag ring (own cell at a wall).
@@ -665,11 +747,11 @@ __device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int 
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
     if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
-        ph = w.lag[y & 3][0][lane + 1];
-        tt = w.lag[y & 3][1][lane + 1];
+        ph = w.lag[y & 7][0][lane + 1];
+        tt = w.lag[y & 7][1][lane + 1];
     } else {
-        ph = w.lag[ys & 3][0][lane + 1 - cx(I)];
-        tt = w.lag[ys & 3][1][lane + 1 - cx(I)];
+        ph = w.lag[ys & 7][0][lane + 1 - cx(I)];
+        tt = w.lag[ys & 7][1][lane + 1 - cx(I)];
     }
 }
 
@@ -700,6 +782,7 @@ template <int MODE, bool WALLS>
 __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing &w, int lane, int x0, int ys, int ye,
                                            double acc[NRED])
 {
+    constexpr bool PB = MODE != MODE_REDUCE;  // phase B follows phase A
     const int ex = x0 - 1 + lane;
     const int xg = ((ex % K.nx) + K.nx) % K.nx;
     const bool b_lane = lane >= 1 && lane <= LB_TX && ex < K.nx;
@@ -708,54 +791,71 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     const int xa = (((x0 - 2 + lane) % K.nx) + K.nx) % K.nx;
     const int xb = (((x0 + 30 + (lane & 1)) % K.nx) + K.nx) % K.nx;
 
-    auto load_lag = [&](int yl) {
+    auto stage_lag = [&](int yl) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
         const long long ro = (long long)yl * K.pitch;
-        w.lag[yl & 3][0][lane] = __ldg(ain + AUX_PHI * K.plane + ro + xa);
-        w.lag[yl & 3][1][lane] = __ldg(ain + AUX_T * K.plane + ro + xa);
+        cp_async4(&w.lag[yl & 7][0][lane], ain + AUX_PHI * K.plane + ro + xa);
+        cp_async4(&w.lag[yl & 7][1][lane], ain + AUX_T * K.plane + ro + xa);
         if (lane < 2) {
-            w.lag[yl & 3][0][32 + lane] = __ldg(ain + AUX_PHI * K.plane + ro + xb);
-            w.lag[yl & 3][1][32 + lane] = __ldg(ain + AUX_T * K.plane + ro + xb);
+            cp_async4(&w.lag[yl & 7][0][32 + lane], ain + AUX_PHI * K.plane + ro + xb);
+            cp_async4(&w.lag[yl & 7][1][32 + lane], ain + AUX_T * K.plane + ro + xb);
         }
     };
+    // phase-A inputs of row y, and the own-cell lagged values phase B needs
+    auto stage_a = [&](int y) {
+        if (WALLS && (y < 0 || y >= K.ny)) return;
+        const long long cell = (long long)y * K.pitch + xg;
+        float *pp = &w.pop[mod3(y)][0][lane];
+        stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
+        stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * 32);
+        stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * 32);
+        float *pa = &w.ax[mod3(y)][0][lane];
+        cp_async4(pa + AX_Q * 32, ain + AUX_Q * K.plane + cell);
+        cp_async4(pa + AX_FS * 32, ain + AUX_FS * K.plane + cell);
+        if (PB) {
+            cp_async4(pa + AX_UX * 32, ain + AUX_UX * K.plane + cell);
+            cp_async4(pa + AX_UY * 32, ain + AUX_UY * K.plane + cell);
+            cp_async4(pa + AX_C * 32, ain + AUX_C * K.plane + cell);
+            cp_async4(&w.loc[y & 3][4][lane], ain + AUX_P * K.plane + cell);
+            cp_async4(&w.loc[y & 3][5][lane], ain + AUX_S * K.plane + cell);
+        }
+    };
+    // pulled g of row y, for its phase B one iteration later
+    auto stage_g = [&](int y) {
+        if (!PB || !b_lane || y < ys || y >= ye) return;
+        stage9<SET_G, WALLS>(K, pin, ex, y, (long long)y * K.pitch + ex, &w.gp[y & 1][0][lane]);
+    };
 
-    // MODE_REDUCE needs phase A on the segment's own rows only
-    const int ya0 = MODE == MODE_REDUCE ? ys : ys - 1;
-    const int ya1 = MODE == MODE_REDUCE ? ye - 1 : ye;
-    load_lag(ya0 - 1);
-    load_lag(ya0);
+    const int ya0 = PB ? ys - 1 : ys;
+    const int ya1 = PB ? ye : ye - 1;
+    stage_lag(ya0 - 1);
+    stage_lag(ya0);
+    stage_lag(ya0 + 1);
+    stage_a(ya0);
+    cp_async_commit();
     for (int ya = ya0; ya <= ya1; ya++) {
-        load_lag(ya + 1);
+        if (ya < ya1) {
+            stage_lag(ya + 2);
+            stage_a(ya + 1);
+        }
+        stage_g(ya);
+        cp_async_commit();
+        cp_async_wait<1>();  // everything staged for row ya (and g of row ya - 1) has landed
         __syncwarp();
         // ---- phase A, row ya ------------------------------------------------------------
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
-            const long long cell = (long long)ya * K.pitch + xg;
-            const real phi_p = w.lag[ya & 3][0][lane + 1];
-            const real T_p = w.lag[ya & 3][1][lane + 1];
-            real v[9];
-            real *pp = &w.pop[ya & 1][0][lane];
-            pull9<SET_F, WALLS>(K, pin, xg, ya, cell, v);
-            if (MODE != MODE_REDUCE) {
-#pragma unroll
-                for (int i = 0; i < 9; i++) pp[(0 + i) * 32] = v[i];
-            }
+            const int s3 = mod3(ya);
+            const real phi_p = w.lag[ya & 7][0][lane + 1];
+            const real T_p = w.lag[ya & 7][1][lane + 1];
+            float *pp = &w.pop[s3][0][lane];
             real dph, dtt;
             lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
-            const real delta = sum9(v) + dph;
-            pull9<SET_H, WALLS>(K, pin, xg, ya, cell, v, T_p);
-            if (MODE != MODE_REDUCE) {
-#pragma unroll
-                for (int i = 0; i < 9; i++) pp[(9 + i) * 32] = v[i];
-            }
-            const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
-            const real ed = sum9(v) + K.rr * dtt + R(0.5) * Q_p;
-            pull9<SET_L, WALLS>(K, pin, xg, ya, cell, v);
-            if (MODE != MODE_REDUCE) {
-#pragma unroll
-                for (int i = 0; i < 9; i++) pp[(18 + i) * 32] = v[i];
-            }
-            const real sl = sum9(v);
-            const real fs_p = __ldg(ain + AUX_FS * K.plane + cell);
+            const real delta = sum9s(pp) + dph;
+            abb_fix9<WALLS>(K, pp + 9 * 32, xg, ya, T_p);  // phase B reads the corrected values
+            const real Q_p = w.ax[s3][AX_Q][lane];
+            const real ed = sum9s(pp + 9 * 32) + K.rr * dtt + R(0.5) * Q_p;
+            const real sl = sum9s(pp + 18 * 32);
+            const real fs_p = w.ax[s3][AX_FS][lane];
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
             if (MODE == MODE_REDUCE) {
@@ -769,25 +869,26 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                     if (ex == K.nx / 2) acc[5] += (double)L.fs;
                 }
             } else {
-                const int s3 = mod3(ya);
-                w.loc[s3][0][lane] = L.dphi;
-                w.loc[s3][1][lane] = L.dT;
-                w.loc[s3][2][lane] = L.C;
-                w.loc[s3][3][lane] = L.fs;
-                w.loc[s3][4][lane] = __ldg(ain + AUX_P * K.plane + cell);
-                w.loc[s3][5][lane] = __ldg(ain + AUX_S * K.plane + cell);
-                w.loc[s3][6][lane] = L.mdot;
+                const int s4 = ya & 3;
+                w.loc[s4][0][lane] = L.dphi;
+                w.loc[s4][1][lane] = L.dT;
+                w.loc[s4][2][lane] = L.C;
+                w.loc[s4][3][lane] = L.fs;
+                w.loc[s4][6][lane] = L.mdot;
             }
         }
         __syncwarp();
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
-        if (MODE != MODE_REDUCE && yb >= ys && yb < ye && b_lane) {
-            const RingAcc A{w, lane, {mod3(yb - 1), mod3(yb), mod3(yb + 1)}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, yb & 1};
+        if (PB && yb >= ys && yb < ye && b_lane) {
+            const RingAcc A{w, lane, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
+                            mod3(yb), yb & 1};
             phase_b<MODE, WALLS>(K, B, A, ex, yb, (long long)yb * K.pitch + ex);
         }
         __syncwarp();
     }
+    cp_async_wait<0>();
+    __syncwarp();
 }
 
 template <int MODE>
