@@ -105,7 +105,8 @@ typedef struct lb_handle lb_handle;
  * populations equal to the equilibria of the initial fields with p = 0,
  * the enthalpy from (T, chi) by the inverse of Eq. Hfl.
  * Returns LB_ERR_INVALID_ARG for null pointers, nx or ny < 1, nx*ny above
- * LB_MAX_CELLS, eps <= 0, non-positive densities, a relaxation time <= 1/2
+ * LB_MAX_CELLS, a padded plane (nx rounded up to a multiple of 32, times ny)
+ * of 2^31 floats or more, eps <= 0, non-positive densities, a relaxation time <= 1/2
  * anywhere in the property range, or divu_mode != 0.  *out is set only on
  * success.  Synchronises the device. */
 lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init,

@@ -96,6 +96,8 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
 {
     if (g->nx < 1 || g->ny < 1) return "nx and ny must be >= 1";
     if ((long)g->nx * (long)g->ny > LB_MAX_CELLS) return "lattice larger than LB_MAX_CELLS";
+    if ((long)((g->nx + 31) / 32 * 32) * (long)g->ny >= (1L << 31))
+        return "padded plane (nx rounded up to 32, times ny) of 2^31 floats or more";
     if (g->bc_bottom < 0 || g->bc_bottom > 1 || g->bc_top < 0 || g->bc_top > 1) return "unknown wall type";
     if (!finite_all(p)) return "non-finite parameter";
     if (!(p->eps > 0)) return "eps must be > 0";
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Co
     const int xc = K.nx / 2;
     double acc[lbk::NRED] = {0, 0, 0, 0, 0, 0};
     for (int x = threadIdx.x; x < K.nx; x += blockDim.x) {
-        const long long cell = (long long)y * K.pitch + x;
+        const int cell = y * K.pitch + x;
         const lbk::CellA c = lbk::cell_a(K, pin, ain, x, y, cell);
         const double phid = (double)c.phi_p + (double)c.L.dphi;
         acc[0] += phid;

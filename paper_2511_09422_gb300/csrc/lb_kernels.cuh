@@ -105,6 +105,14 @@ __device__ __forceinline__ int wrapx(int x, int nx)
     return x < 0 ? x + nx : (x >= nx ? x - nx : x);
 }
 
+// Start of plane k of a buffer.  A plane holds fewer than 2^31 floats (the
+// host rejects larger ones), so offsets within a plane are 32-bit.
+template <class T>
+__device__ __forceinline__ T *plane_ptr(T *base, int k, const Consts &K)
+{
+    return base + (size_t)(unsigned)K.plane * (unsigned)k;
+}
+
 __device__ __forceinline__ real clamp01(real v) { return fmin(fmax(v, R(0.0)), R(1.0)); }
 
 // Correctly rounded reciprocal (a division a / b below is a * rcp(b), within
@@ -195,13 +203,12 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // link midpoint) is applied in deviation form relative to w rr T_own.
 // pull_src gives the address read, abb_fix the wall rule applied to its value.
 template <int S, int I, bool W>
-__device__ __forceinline__ const float *pull_src(const Consts &K, const float *__restrict__ pin, int x, int y,
-                                                 long long cell)
+__device__ __forceinline__ const float *pull_src(const Consts &K, const float *__restrict__ pin, int x, int y, int cell)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return pin + (long long)(S * 9 + opp(I)) * K.plane + cell;
-    return pin + (long long)(S * 9 + I) * K.plane + (long long)ys * K.pitch + wrapx(x - cx(I), K.nx);
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return plane_ptr(pin, S * 9 + opp(I), K) + cell;
+    return plane_ptr(pin, S * 9 + I, K) + (ys * K.pitch + wrapx(x - cx(I), K.nx));
 }
 
 template <int S, int I, bool W>
@@ -220,7 +227,7 @@ __device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, r
 }
 
 template <int S, int I, bool W>
-__device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
+__device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
                                      real T_own)
 {
     return abb_fix<S, I, W>(K, __ldg(pull_src<S, I, W>(K, pin, x, y, cell)), x, y, T_own);
@@ -228,7 +235,7 @@ __device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ 
 
 // W = false: the caller guarantees that no source row lies beyond a wall.
 template <int S, bool W = true>
-__device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell, real v[9],
+__device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell, real v[9],
                                       real T_own = R(0.0))
 {
     v[0] = pull<S, 0, W>(K, pin, x, y, cell, T_own);
@@ -245,19 +252,19 @@ __device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__
 // Lagged field (plane A) of the cell that wrote the population pulled into
 // direction I at (x, y) (the own cell at a wall).
 template <int A, int I, bool W>
-__device__ __forceinline__ real aux_src(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell)
+__device__ __forceinline__ real aux_src(const Consts &K, const float *__restrict__ ain, int x, int y, int cell)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    const float *a = ain + (long long)A * K.plane;
+    const float *a = plane_ptr(ain, A, K);
     if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return __ldg(a + cell);
-    return __ldg(a + (long long)ys * K.pitch + wrapx(x - cx(I), K.nx));
+    return __ldg(a + (ys * K.pitch + wrapx(x - cx(I), K.nx)));
 }
 
 // sum_{i>0} w_i (z^n(source_i) - z^n(x)) of a lagged field: the reference
 // offsets of the pulled deviations relative to the own lagged value.
 template <int A, bool W = true>
-__device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__restrict__ ain, int x, int y, long long cell,
+__device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__restrict__ ain, int x, int y, int cell,
                                             real own)
 {
     return (wgt(1) * (aux_src<A, 1, W>(K, ain, x, y, cell) - own) + wgt(2) * (aux_src<A, 2, W>(K, ain, x, y, cell) - own) +
@@ -304,18 +311,18 @@ struct CellA {
 
 template <bool W = true>
 __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict__ pin, const float *__restrict__ ain,
-                                        int x, int y, long long cell)
+                                        int x, int y, int cell)
 {
     CellA c;
     real v[9];
-    c.phi_p = __ldg(ain + AUX_PHI * K.plane + cell);
-    c.T_p = __ldg(ain + AUX_T * K.plane + cell);
-    c.fs_p = __ldg(ain + AUX_FS * K.plane + cell);
+    c.phi_p = __ldg(plane_ptr(ain, AUX_PHI, K) + cell);
+    c.T_p = __ldg(plane_ptr(ain, AUX_T, K) + cell);
+    c.fs_p = __ldg(plane_ptr(ain, AUX_FS, K) + cell);
     c.chi_p = clamp01(R(0.5) * (R(1.0) + c.phi_p));
     pull9<SET_F, W>(K, pin, x, y, cell, v);
     const real delta = sum9(v) + aux_dev_sum<AUX_PHI, W>(K, ain, x, y, cell, c.phi_p);
     pull9<SET_H, W>(K, pin, x, y, cell, v, c.T_p);
-    const real Q_p = __ldg(ain + AUX_Q * K.plane + cell);
+    const real Q_p = __ldg(plane_ptr(ain, AUX_Q, K) + cell);
     c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T, W>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
     pull9<SET_L, W>(K, pin, x, y, cell, v);
     const real sl = sum9(v);
@@ -338,7 +345,7 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_REDUCE = 2 };
 // pulled f, h, l and g, and its own lagged Q, f_s, u and C.
 // ---------------------------------------------------------------------------------------
 template <int MODE, bool WALLS, class Acc>
-__device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const Acc &A, int x, int y, long long cell)
+__device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const Acc &A, int x, int y, int cell)
 {
     const real rr = K.rr;
     const bool at_bottom = WALLS && (y == 0), at_top = WALLS && (y == K.ny - 1);
@@ -469,31 +476,48 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
     if (MODE == MODE_FIELDS) {
         float *o = B.fields;
-        const long long P = K.plane;
-        o[0 * P + cell] = phi;
-        o[1 * P + cell] = T;
-        o[2 * P + cell] = fs;
-        o[3 * P + cell] = C;
-        o[4 * P + cell] = ux;
-        o[5 * P + cell] = uy;
-        o[6 * P + cell] = pr;
+        plane_ptr(o, 0, K)[cell] = phi;
+        plane_ptr(o, 1, K)[cell] = T;
+        plane_ptr(o, 2, K)[cell] = fs;
+        plane_ptr(o, 3, K)[cell] = C;
+        plane_ptr(o, 4, K)[cell] = ux;
+        plane_ptr(o, 5, K)[cell] = uy;
+        plane_ptr(o, 6, K)[cell] = pr;
         return;
     }
 
+    // The collisions run over the rest direction and the four pairs (i, opp(i))
+    // with c_opp = -c_i: every equilibrium and source term splits into a part
+    // even in c_i, shared by the pair, and an odd part that changes sign.
+    constexpr int PAIR[4] = {1, 2, 5, 6};
+
+    // flow set (Sec. 3.2); d_i = g_i - 3 p_st (w_i - [i = 0]) is formed from the
+    // stored deviation, the reference of the stored value being 3 p_st (w_i - [i = 0])
     const real om_g = rcp(tau_g), src_g = R(1.0) - R(0.5) * om_g;
     float *__restrict__ pout = B.pout;
+    {
+        const real dpp = p_p - p_st;
+        const real Fqx = Fx + rfx, Fqy = Fy + rfy;  // F + rho f
+        {
+            const real wp = R(3.0) * (wgt(0) - R(1.0));
+            const real d = dg[0] + wp * dpp;
+            const real deq = wp * p_lo + rho * (wgt(0) * (-R(1.5) * uu));
+            const real G0 = wgt(0) * (S - R(3.0) * uF);
+            plane_ptr(pout, SET_G * 9 + 0, K)[cell] = d - (d - deq) * om_g + src_g * G0;
+        }
 #pragma unroll
-    for (int i = 0; i < 9; i++) {
-        // deviations from 3 p_st (w_i - [i = 0]), the reference of the stored value
-        const real wp = R(3.0) * (wgt(i) - (i == 0 ? R(1.0) : R(0.0)));
-        const real d = dg[i] + wp * (p_p - p_st);
-        const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-        const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
-        const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-        const real deq = wp * p_lo + rho * si;
-        const real Gi = wgt(i) * (S + R(3.0) * ((real)cx(i) * (Fx + rfx) + (real)cy(i) * (Fy + rfy)) +
-                                   R(9.0) * (cu * cF - (R(1.0) / R(3.0)) * uF));
-        pout[(long long)(SET_G * 9 + i) * K.plane + cell] = d - (d - deq) * om_g + src_g * Gi;
+        for (int q = 0; q < 4; q++) {
+            const int i = PAIR[q], j = opp(i);
+            const real w = wgt(i), w3 = R(3.0) * w;
+            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
+            const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
+            const real cG = (real)cx(i) * Fqx + (real)cy(i) * Fqy;
+            const real eq_e = w3 * p_lo + rho * w * (R(4.5) * cu * cu - R(1.5) * uu), eq_o = rho * w3 * cu;
+            const real G_e = w * (S + R(9.0) * (cu * cF) - R(3.0) * uF), G_o = w3 * cG;
+            const real di = dg[i] + w3 * dpp, dj = dg[j] + w3 * dpp;
+            plane_ptr(pout, SET_G * 9 + i, K)[cell] = di - (di - (eq_e + eq_o)) * om_g + src_g * (G_e + G_o);
+            plane_ptr(pout, SET_G * 9 + j, K)[cell] = dj - (dj - (eq_e - eq_o)) * om_g + src_g * (G_e - G_o);
+        }
     }
 
     // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
@@ -507,16 +531,25 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         // stored as f_i* - w_i phi_st
         real f[9];
         A.template pops<SET_F>(K, B.pin, x, y, cell, f, R(0.0));
+        {
+            const real d = f[0] + wgt(0) * (phi_p - phi_st);
+            const real deq = wgt(0) * phi_lo;
+            plane_ptr(pout, SET_F * 9 + 0, K)[cell] = d - (d - deq) * om + src * (wgt(0) * phi * mdot);
+        }
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
-            const int ys = y - cy(i);
-            const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
-            const real php = wall ? phi_p : A.phip(-cy(i), -cx(i));
-            const real d = f[i] + wgt(i) * (php - phi_st);
+        for (int q = 0; q < 4; q++) {
+            const int i = PAIR[q], j = opp(i);
+            const real w = wgt(i), w3 = R(3.0) * w;
+            const int ysi = y - cy(i), ysj = y - cy(j);
+            const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
+            const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
+            const real di = f[i] + w * ((wall_i ? phi_p : A.phip(-cy(i), -cx(i))) - phi_st);
+            const real dj = f[j] + w * ((wall_j ? phi_p : A.phip(-cy(j), -cx(j))) - phi_st);
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real deq = wgt(i) * (phi_lo + phi * R(3.0) * cu);  // f_eq - w_i phi_st
-            const real Fi = wgt(i) * R(3.0) * ((real)cx(i) * ax + (real)cy(i) * ay) + wgt(i) * phi * mdot;
-            pout[(long long)(SET_F * 9 + i) * K.plane + cell] = d - (d - deq) * om + src * Fi;
+            const real eq_e = w * phi_lo, eq_o = w3 * phi * cu;  // f_eq - w phi_st
+            const real F_e = w * phi * mdot, F_o = w3 * ((real)cx(i) * ax + (real)cy(i) * ay);
+            plane_ptr(pout, SET_F * 9 + i, K)[cell] = di - (di - (eq_e + eq_o)) * om + src * (F_e + F_o);
+            plane_ptr(pout, SET_F * 9 + j, K)[cell] = dj - (dj - (eq_e - eq_o)) * om + src * (F_e - F_o);
         }
 
         // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
@@ -532,43 +565,50 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
         real l[9];
         A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
+        plane_ptr(pout, SET_L * 9 + 0, K)[cell] = l[0] - (l[0] - wgt(0) * C) * om_l;
 #pragma unroll
-        for (int i = 0; i < 9; i++) {
+        for (int q = 0; q < 4; q++) {
+            const int i = PAIR[q], j = opp(i);
+            const real w = wgt(i), w3 = R(3.0) * w;
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real leq = wgt(i) * C * (R(1.0) + R(3.0) * cu);
-            const real Li = wgt(i) * R(3.0) * ((real)cx(i) * bx + (real)cy(i) * by);
-            pout[(long long)(SET_L * 9 + i) * K.plane + cell] = l[i] - (l[i] - leq) * om_l + src_l * Li;
+            const real eq_e = w * C, eq_o = w3 * C * cu;
+            const real L_o = w3 * ((real)cx(i) * bx + (real)cy(i) * by);
+            plane_ptr(pout, SET_L * 9 + i, K)[cell] = l[i] - (l[i] - (eq_e + eq_o)) * om_l + src_l * L_o;
+            plane_ptr(pout, SET_L * 9 + j, K)[cell] = l[j] - (l[j] - (eq_e - eq_o)) * om_l - src_l * L_o;
         }
     }
 
     // enthalpy set (Sec. 3.3), two relaxation times: antisymmetric part with
     // tau_bar = 1/2 + lam/(rho_ref Cp_ref cs2), symmetric part with 1/tau_tilde = 2 - 1/tau_bar;
     // isotropic source w_i Q weighted with (1 - 1/(2 tau_tilde)).  Everything is formed as
-    // deviations from w_i rr T_st (and the latent reference for i = 0).
+    // deviations from w_i rr T_st (and the latent reference for i = 0).  For a pair the
+    // symmetric and antisymmetric equilibrium parts are the even and odd parts above.
     const real Q = rhocp * T * mdot;
     {
         const real tau_hb = R(0.5) + R(3.0) * lam * K.inv_rr;
         const real om_a = rcp(tau_hb), om_s = R(2.0) - om_a;
         const real src_h = R(1.0) - R(0.5) * om_s;
         const real rcT = rhocp * T;
-        real h[9], dh[9], deq[9];
+        real h[9];
         A.template pops<SET_H>(K, B.pin, x, y, cell, h, T_p);
+        real snz = R(0.0);  // sum_{i>0} (h_i - w_i rr T_st)
 #pragma unroll
-        for (int i = 1; i < 9; i++) {
-            const int ys = y - cy(i);
-            const bool wall = WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny);
-            const real Tps = wall ? T_p : A.Tp(-cy(i), -cx(i));
-            dh[i] = h[i] + wgt(i) * rr * (Tps - T_st);  // h_i - w_i rr T_st
+        for (int q = 0; q < 4; q++) {
+            const int i = PAIR[q], j = opp(i);
+            const real w = wgt(i);
+            const int ysi = y - cy(i), ysj = y - cy(j);
+            const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
+            const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
+            const real dhi = h[i] + w * rr * ((wall_i ? T_p : A.Tp(-cy(i), -cx(i))) - T_st);
+            const real dhj = h[j] + w * rr * ((wall_j ? T_p : A.Tp(-cy(j), -cx(j))) - T_st);
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            deq[i] = wgt(i) * (rr * T_lo + rcT * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu));
-        }
-#pragma unroll
-        for (int i = 1; i < 9; i++) {
-            const int j = opp(i);
-            const real hs = R(0.5) * (dh[i] + dh[j]), ha = R(0.5) * (dh[i] - dh[j]);
-            const real es = R(0.5) * (deq[i] + deq[j]), ea = R(0.5) * (deq[i] - deq[j]);
-            pout[(long long)(SET_H * 9 + i) * K.plane + cell] =
-                dh[i] - (ha - ea) * om_a - (hs - es) * om_s + src_h * wgt(i) * Q;
+            const real es = w * (rr * T_lo + rcT * (R(4.5) * cu * cu - R(1.5) * uu));
+            const real ea = w * rcT * R(3.0) * cu;
+            const real hs = R(0.5) * (dhi + dhj), ha = R(0.5) * (dhi - dhj);
+            const real rel_s = (hs - es) * om_s, rel_a = (ha - ea) * om_a, srcq = src_h * w * Q;
+            plane_ptr(pout, SET_H * 9 + i, K)[cell] = dhi - rel_a - rel_s + srcq;
+            plane_ptr(pout, SET_H * 9 + j, K)[cell] = dhj + rel_a - rel_s + srcq;
+            snz += dhi + dhj;
         }
         // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
         // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
@@ -579,26 +619,23 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const real chi_n = clamp01(R(0.5) * (R(1.0) + phi_st));
             // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
-            real snz = R(0.0);
-#pragma unroll
-            for (int i = 1; i < 9; i++) snz += dh[i];
             const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
             const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
-            pout[(long long)(SET_H * 9 + 0) * K.plane + cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
+            plane_ptr(pout, SET_H * 9 + 0, K)[cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
         }
     }
 
     // lagged fields for the next step
     float *__restrict__ aout = B.aout;
-    aout[AUX_FS * K.plane + cell] = fs;
-    aout[AUX_Q * K.plane + cell] = Q;
-    aout[AUX_UX * K.plane + cell] = ux;
-    aout[AUX_UY * K.plane + cell] = uy;
-    aout[AUX_PHI * K.plane + cell] = (float)phi_st;
-    aout[AUX_C * K.plane + cell] = C;
-    aout[AUX_P * K.plane + cell] = (float)p_st;
-    aout[AUX_S * K.plane + cell] = S;
-    aout[AUX_T * K.plane + cell] = (float)T_st;
+    plane_ptr(aout, AUX_FS, K)[cell] = fs;
+    plane_ptr(aout, AUX_Q, K)[cell] = Q;
+    plane_ptr(aout, AUX_UX, K)[cell] = ux;
+    plane_ptr(aout, AUX_UY, K)[cell] = uy;
+    plane_ptr(aout, AUX_PHI, K)[cell] = (float)phi_st;
+    plane_ptr(aout, AUX_C, K)[cell] = C;
+    plane_ptr(aout, AUX_P, K)[cell] = (float)p_st;
+    plane_ptr(aout, AUX_S, K)[cell] = S;
+    plane_ptr(aout, AUX_T, K)[cell] = (float)T_st;
 
     // a non-finite value anywhere in the cell's new state is reported once
     if (!isfinite(T + phi + C + ux + uy + pr)) atomicOr(B.status, 1u);
@@ -704,7 +741,7 @@ struct RingAcc {
 // Stage the 9 pulls of set S at (x, y) into dst[i * 32] (raw source values;
 // the anti-bounce-back rule is applied when they are read).
 template <int S, bool W>
-__device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, long long cell,
+__device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
                                        float *dst)
 {
     cp_async4(dst + 0 * 32, pull_src<S, 0, W>(K, pin, x, y, cell));
@@ -793,37 +830,37 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
 
     auto stage_lag = [&](int yl) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
-        const long long ro = (long long)yl * K.pitch;
-        cp_async4(&w.lag[yl & 7][0][lane], ain + AUX_PHI * K.plane + ro + xa);
-        cp_async4(&w.lag[yl & 7][1][lane], ain + AUX_T * K.plane + ro + xa);
+        const int ro = yl * K.pitch;
+        cp_async4(&w.lag[yl & 7][0][lane], plane_ptr(ain, AUX_PHI, K) + (ro + xa));
+        cp_async4(&w.lag[yl & 7][1][lane], plane_ptr(ain, AUX_T, K) + (ro + xa));
         if (lane < 2) {
-            cp_async4(&w.lag[yl & 7][0][32 + lane], ain + AUX_PHI * K.plane + ro + xb);
-            cp_async4(&w.lag[yl & 7][1][32 + lane], ain + AUX_T * K.plane + ro + xb);
+            cp_async4(&w.lag[yl & 7][0][32 + lane], plane_ptr(ain, AUX_PHI, K) + (ro + xb));
+            cp_async4(&w.lag[yl & 7][1][32 + lane], plane_ptr(ain, AUX_T, K) + (ro + xb));
         }
     };
     // phase-A inputs of row y, and the own-cell lagged values phase B needs
     auto stage_a = [&](int y) {
         if (WALLS && (y < 0 || y >= K.ny)) return;
-        const long long cell = (long long)y * K.pitch + xg;
+        const int cell = y * K.pitch + xg;
         float *pp = &w.pop[mod3(y)][0][lane];
         stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
         stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * 32);
         stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * 32);
         float *pa = &w.ax[mod3(y)][0][lane];
-        cp_async4(pa + AX_Q * 32, ain + AUX_Q * K.plane + cell);
-        cp_async4(pa + AX_FS * 32, ain + AUX_FS * K.plane + cell);
+        cp_async4(pa + AX_Q * 32, plane_ptr(ain, AUX_Q, K) + cell);
+        cp_async4(pa + AX_FS * 32, plane_ptr(ain, AUX_FS, K) + cell);
         if (PB) {
-            cp_async4(pa + AX_UX * 32, ain + AUX_UX * K.plane + cell);
-            cp_async4(pa + AX_UY * 32, ain + AUX_UY * K.plane + cell);
-            cp_async4(pa + AX_C * 32, ain + AUX_C * K.plane + cell);
-            cp_async4(&w.loc[y & 3][4][lane], ain + AUX_P * K.plane + cell);
-            cp_async4(&w.loc[y & 3][5][lane], ain + AUX_S * K.plane + cell);
+            cp_async4(pa + AX_UX * 32, plane_ptr(ain, AUX_UX, K) + cell);
+            cp_async4(pa + AX_UY * 32, plane_ptr(ain, AUX_UY, K) + cell);
+            cp_async4(pa + AX_C * 32, plane_ptr(ain, AUX_C, K) + cell);
+            cp_async4(&w.loc[y & 3][4][lane], plane_ptr(ain, AUX_P, K) + cell);
+            cp_async4(&w.loc[y & 3][5][lane], plane_ptr(ain, AUX_S, K) + cell);
         }
     };
     // pulled g of row y, for its phase B one iteration later
     auto stage_g = [&](int y) {
         if (!PB || !b_lane || y < ys || y >= ye) return;
-        stage9<SET_G, WALLS>(K, pin, ex, y, (long long)y * K.pitch + ex, &w.gp[y & 1][0][lane]);
+        stage9<SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, &w.gp[y & 1][0][lane]);
     };
 
     const int ya0 = PB ? ys - 1 : ys;
@@ -883,7 +920,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (PB && yb >= ys && yb < ye && b_lane) {
             const RingAcc A{w, lane, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
                             mod3(yb), yb & 1};
-            phase_b<MODE, WALLS>(K, B, A, ex, yb, (long long)yb * K.pitch + ex);
+            phase_b<MODE, WALLS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
         __syncwarp();
     }

@@ -71,6 +71,7 @@ def _create(lib, grid, params, n, phi=True):
 
 @pytest.mark.parametrize("bad", [
     dict(grid=dict(nx=0)), dict(grid=dict(ny=0)), dict(grid=dict(nx=1 << 15, ny=1 << 15)),
+    dict(grid=dict(nx=1, ny=1 << 26)),
     dict(params=dict(eps=0.0)), dict(params=dict(rho_g=0.0)), dict(params=dict(mu_l=0.0)),
     dict(params=dict(mobility=-1.0)), dict(params=dict(lam_s=0.0)), dict(params=dict(D_l=0.0)),
     dict(params=dict(divu_mode=1)), dict(params=dict(sigma0=float("nan"))),
