@@ -42,11 +42,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// Compute type of the step's arithmetic (storage is FP32 regardless).
-#ifndef LB_REAL
-#define LB_REAL float
-#endif
-typedef LB_REAL real;
+// Arithmetic type of the step (FP32; the diagnostics sums are FP64).
+typedef float real;
 #define R(x) ((real)(x))
 
 #define LB_TX 30  // interior columns of a warp strip (32 lanes less a halo column on each side)
@@ -381,14 +378,15 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #pragma unroll
         for (int i = 1; i < 9; i++) {
             const int a = dyv[i], b = dxv[i];
-            const real zph = (A.phip(a, b) - phi_p) + (A.dphi(a, b) - dphi);
-            real zT = (A.Tp(a, b) - T_p) + (A.dT(a, b) - dT);
+            const float2 lg = A.lagv(a, b), dd = A.ddv(a, b), cf = A.cfv(a, b), ps = A.psv(a, b);
+            const real zph = (lg.x - phi_p) + (dd.x - dphi);
+            real zT = (lg.y - T_p) + (dd.y - dT);
             if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
                 const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
                 // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
-                zT = R(2.0) * (Tw - A.Tp(a, b)) + (A.Tp(a, b) - T_p) - (A.dT(a, b) + dT);
+                zT = R(2.0) * (Tw - lg.y) + (lg.y - T_p) - (dd.y + dT);
             }
-            const real zv[6] = {zph, zT, A.C(a, b) - C, A.fs(a, b) - f0, A.p(a, b) - P0, A.S(a, b) - S0};
+            const real zv[6] = {zph, zT, cf.x - C, cf.y - f0, ps.x - P0, ps.y - S0};
             const real wcx = wgt(i) * (real)cx(i), wcy = wgt(i) * (real)cy(i);
 #pragma unroll
             for (int k = 0; k < 6; k++) {
@@ -649,8 +647,9 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 // while the warp computes phase A of row y and phase B of row y - 1, the
 // copies for phase A of row y + 1 (and phase B of row y) are in flight.
 // Rings per warp (columns x0-2 .. x0+31 for lag, the warp's 32 lanes otherwise):
-//   lag  lagged phi, T                                     rows y & 7
-//   loc  dphi, dT, C, f_s, mdot (phase A) and staged p, S   rows y & 3
+//   lag  lagged (phi, T) pairs                             rows y & 7
+//   dd, cf, md  (dphi, dT), (C, f_s), mdot from phase A     rows y & 3
+//   ps   staged lagged (p, S) pairs                        rows y & 3
 //   pop  staged pulls of f, h, l (stored form)              rows y mod 3
 //   ax   staged own-cell Q, f_s, u_x, u_y, C                rows y mod 3
 //   gp   staged pulls of g                                  rows y & 1
@@ -673,8 +672,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
 
 struct WarpRing {
-    float lag[8][2][34];
-    real loc[4][7][32];
+    float2 lag[8][34];  // (phi, T) lagged
+    float2 dd[4][32];   // (dphi, dT)
+    float2 cf[4][32];   // (C, f_s)
+    float2 ps[4][32];   // (p, S) lagged, staged
+    float md[4][32];    // mdot
     float pop[3][27][32];
     float ax[3][NAX][32];
     float gp[2][9][32];
@@ -714,15 +716,20 @@ struct RingAcc {
     const WarpRing &w;
     int lane;
     int sl[3], sg[3], sp, sgp;  // loc slots, lag slots (rows y-1, y, y+1), pop / ax slot, gp slot
-    __device__ real phip(int dy, int dx) const { return w.lag[sg[dy + 1]][0][lane + 1 + dx]; }
-    __device__ real Tp(int dy, int dx) const { return w.lag[sg[dy + 1]][1][lane + 1 + dx]; }
-    __device__ real dphi(int dy, int dx) const { return w.loc[sl[dy + 1]][0][lane + dx]; }
-    __device__ real dT(int dy, int dx) const { return w.loc[sl[dy + 1]][1][lane + dx]; }
-    __device__ real C(int dy, int dx) const { return w.loc[sl[dy + 1]][2][lane + dx]; }
-    __device__ real fs(int dy, int dx) const { return w.loc[sl[dy + 1]][3][lane + dx]; }
-    __device__ real p(int dy, int dx) const { return w.loc[sl[dy + 1]][4][lane + dx]; }
-    __device__ real S(int dy, int dx) const { return w.loc[sl[dy + 1]][5][lane + dx]; }
-    __device__ real mdot(int dy, int dx) const { return w.loc[sl[dy + 1]][6][lane + dx]; }
+    // pairs read together (one 64-bit shared load each)
+    __device__ float2 lagv(int dy, int dx) const { return w.lag[sg[dy + 1]][lane + 1 + dx]; }
+    __device__ float2 ddv(int dy, int dx) const { return w.dd[sl[dy + 1]][lane + dx]; }
+    __device__ float2 cfv(int dy, int dx) const { return w.cf[sl[dy + 1]][lane + dx]; }
+    __device__ float2 psv(int dy, int dx) const { return w.ps[sl[dy + 1]][lane + dx]; }
+    __device__ real phip(int dy, int dx) const { return lagv(dy, dx).x; }
+    __device__ real Tp(int dy, int dx) const { return lagv(dy, dx).y; }
+    __device__ real dphi(int dy, int dx) const { return ddv(dy, dx).x; }
+    __device__ real dT(int dy, int dx) const { return ddv(dy, dx).y; }
+    __device__ real C(int dy, int dx) const { return cfv(dy, dx).x; }
+    __device__ real fs(int dy, int dx) const { return cfv(dy, dx).y; }
+    __device__ real p(int dy, int dx) const { return psv(dy, dx).x; }
+    __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
+    __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
     template <int S>
     __device__ void pops(const Consts &, const float *__restrict__, int, int, long long, real v[9], real) const
     {
@@ -783,13 +790,9 @@ __device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int 
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
-        ph = w.lag[y & 7][0][lane + 1];
-        tt = w.lag[y & 7][1][lane + 1];
-    } else {
-        ph = w.lag[ys & 7][0][lane + 1 - cx(I)];
-        tt = w.lag[ys & 7][1][lane + 1 - cx(I)];
-    }
+    const float2 v = (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) ? w.lag[y & 7][lane + 1] : w.lag[ys & 7][lane + 1 - cx(I)];
+    ph = v.x;
+    tt = v.y;
 }
 
 template <bool W>
@@ -831,11 +834,11 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     auto stage_lag = [&](int yl) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
         const int ro = yl * K.pitch;
-        cp_async4(&w.lag[yl & 7][0][lane], plane_ptr(ain, AUX_PHI, K) + (ro + xa));
-        cp_async4(&w.lag[yl & 7][1][lane], plane_ptr(ain, AUX_T, K) + (ro + xa));
+        cp_async4(&w.lag[yl & 7][lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xa));
+        cp_async4(&w.lag[yl & 7][lane].y, plane_ptr(ain, AUX_T, K) + (ro + xa));
         if (lane < 2) {
-            cp_async4(&w.lag[yl & 7][0][32 + lane], plane_ptr(ain, AUX_PHI, K) + (ro + xb));
-            cp_async4(&w.lag[yl & 7][1][32 + lane], plane_ptr(ain, AUX_T, K) + (ro + xb));
+            cp_async4(&w.lag[yl & 7][32 + lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xb));
+            cp_async4(&w.lag[yl & 7][32 + lane].y, plane_ptr(ain, AUX_T, K) + (ro + xb));
         }
     };
     // phase-A inputs of row y, and the own-cell lagged values phase B needs
@@ -853,8 +856,8 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             cp_async4(pa + AX_UX * 32, plane_ptr(ain, AUX_UX, K) + cell);
             cp_async4(pa + AX_UY * 32, plane_ptr(ain, AUX_UY, K) + cell);
             cp_async4(pa + AX_C * 32, plane_ptr(ain, AUX_C, K) + cell);
-            cp_async4(&w.loc[y & 3][4][lane], plane_ptr(ain, AUX_P, K) + cell);
-            cp_async4(&w.loc[y & 3][5][lane], plane_ptr(ain, AUX_S, K) + cell);
+            cp_async4(&w.ps[y & 3][lane].x, plane_ptr(ain, AUX_P, K) + cell);
+            cp_async4(&w.ps[y & 3][lane].y, plane_ptr(ain, AUX_S, K) + cell);
         }
     };
     // pulled g of row y, for its phase B one iteration later
@@ -882,8 +885,8 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         // ---- phase A, row ya ------------------------------------------------------------
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
             const int s3 = mod3(ya);
-            const real phi_p = w.lag[ya & 7][0][lane + 1];
-            const real T_p = w.lag[ya & 7][1][lane + 1];
+            const float2 lag0 = w.lag[ya & 7][lane + 1];
+            const real phi_p = lag0.x, T_p = lag0.y;
             float *pp = &w.pop[s3][0][lane];
             real dph, dtt;
             lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
@@ -907,11 +910,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                 }
             } else {
                 const int s4 = ya & 3;
-                w.loc[s4][0][lane] = L.dphi;
-                w.loc[s4][1][lane] = L.dT;
-                w.loc[s4][2][lane] = L.C;
-                w.loc[s4][3][lane] = L.fs;
-                w.loc[s4][6][lane] = L.mdot;
+                w.dd[s4][lane] = make_float2(L.dphi, L.dT);
+                w.cf[s4][lane] = make_float2(L.C, L.fs);
+                w.md[s4][lane] = L.mdot;
             }
         }
         __syncwarp();
@@ -928,9 +929,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     __syncwarp();
 }
 
+#ifdef LB_MAXNREG
+#define LB_STRIP_BOUNDS __maxnreg__(LB_MAXNREG)
+#else
+#define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, LB_SMINB)
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(32 * LB_SW, LB_SMINB) lb_strip_kernel(const Consts K, const Buffers B,
-                                                                        double *__restrict__ partials)
+__global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B, double *__restrict__ partials)
 {
     extern __shared__ __align__(16) unsigned char lb_smem[];
     WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
