@@ -132,6 +132,49 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Packed FP32 pairs for the sm_100+ f32x2 instructions, which add, subtract,
+// multiply or fuse-multiply-add both halves of a 64-bit register at once
+// (each half rounded as its FP32 counterpart).
+typedef unsigned long long pf2;
+__device__ __forceinline__ pf2 pk2(float lo, float hi)
+{
+    pf2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(__float_as_uint(lo)), "r"(__float_as_uint(hi)));
+    return r;
+}
+__device__ __forceinline__ pf2 pk2(float2 v) { return pk2(v.x, v.y); }
+__device__ __forceinline__ pf2 splat2(float v) { return pk2(v, v); }
+__device__ __forceinline__ float2 up2(pf2 v)
+{
+    unsigned lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
+    return make_float2(__uint_as_float(lo), __uint_as_float(hi));
+}
+__device__ __forceinline__ pf2 add2(pf2 a, pf2 b)
+{
+    pf2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 sub2(pf2 a, pf2 b)
+{
+    pf2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 mul2(pf2 a, pf2 b)
+{
+    pf2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ pf2 fma2(pf2 a, pf2 b, pf2 c)  // a * b + c
+{
+    pf2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // Bottom-wall temperature at continuous abscissa x.
 __device__ __forceinline__ real wall_T_bottom(const Consts &K, real x)
 {
@@ -371,36 +414,53 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // are ghosts: mirror, or 2 T_w - T_adjacent for the temperature at a Dirichlet wall.
     real gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, gPx, gPy, gSx, gSy;
     {
+        // the six fields run as three packed pairs: (phi, T), (C, f_s), (p, S)
         const int dxv[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
         const int dyv[9] = {0, 0, dn, 0, ds, dn, dn, ds, ds};
-        const real f0 = A.fs(0, 0), P0 = A.p(0, 0), S0 = A.S(0, 0);
-        real sx[6] = {0, 0, 0, 0, 0, 0}, sy[6] = {0, 0, 0, 0, 0, 0}, sl = R(0.0);
+        const pf2 lag0 = pk2(phi_p, T_p), dd0 = pk2(dphi, dT);
+        const pf2 cf0 = pk2(A.cfv(0, 0)), ps0 = pk2(A.psv(0, 0));
+        pf2 sx01 = 0, sy01 = 0, sx23 = 0, sy23 = 0, sx45 = 0, sy45 = 0;  // bit pattern of (0, 0)
+        real sl = R(0.0);
 #pragma unroll
         for (int i = 1; i < 9; i++) {
             const int a = dyv[i], b = dxv[i];
-            const float2 lg = A.lagv(a, b), dd = A.ddv(a, b), cf = A.cfv(a, b), ps = A.psv(a, b);
-            const real zph = (lg.x - phi_p) + (dd.x - dphi);
-            real zT = (lg.y - T_p) + (dd.y - dT);
-            if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
-                const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
-                // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
-                zT = R(2.0) * (Tw - lg.y) + (lg.y - T_p) - (dd.y + dT);
+            const float2 lg = A.lagv(a, b), dd = A.ddv(a, b);
+            pf2 z01;  // (phi_i - phi_0, T_i - T_0)
+            if (!WALLS) {
+                z01 = add2(sub2(pk2(lg), lag0), sub2(pk2(dd), dd0));
+            } else {
+                const real zph = (lg.x - phi_p) + (dd.x - dphi);
+                real zT = (lg.y - T_p) + (dd.y - dT);
+                if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
+                    const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;
+                    // ghost - T_0 = 2 T_w - T_adj - T_0 = 2 (T_w - Tp_adj) + (Tp_adj - Tp_0) - dT_adj - dT_0
+                    zT = R(2.0) * (Tw - lg.y) + (lg.y - T_p) - (dd.y + dT);
+                }
+                z01 = pk2(zph, zT);
             }
-            const real zv[6] = {zph, zT, cf.x - C, cf.y - f0, ps.x - P0, ps.y - S0};
-            const real wcx = wgt(i) * (real)cx(i), wcy = wgt(i) * (real)cy(i);
-#pragma unroll
-            for (int k = 0; k < 6; k++) {
-                sx[k] += wcx * zv[k];
-                sy[k] += wcy * zv[k];
+            const pf2 z23 = sub2(pk2(A.cfv(a, b)), cf0), z45 = sub2(pk2(A.psv(a, b)), ps0);
+            if (cx(i) != 0) {
+                const pf2 w = splat2(wgt(i) * (real)cx(i));
+                sx01 = fma2(w, z01, sx01);
+                sx23 = fma2(w, z23, sx23);
+                sx45 = fma2(w, z45, sx45);
             }
-            sl += R(2.0) * wgt(i) * zph;
+            if (cy(i) != 0) {
+                const pf2 w = splat2(wgt(i) * (real)cy(i));
+                sy01 = fma2(w, z01, sy01);
+                sy23 = fma2(w, z23, sy23);
+                sy45 = fma2(w, z45, sy45);
+            }
+            sl += R(2.0) * wgt(i) * up2(z01).x;
         }
-        gpx = R(3.0) * sx[0]; gpy = R(3.0) * sy[0]; lphi = R(3.0) * sl;
-        gTx = R(3.0) * sx[1]; gTy = R(3.0) * sy[1];
-        gCx = R(3.0) * sx[2]; gCy = R(3.0) * sy[2];
-        gfx = R(3.0) * sx[3]; gfy = R(3.0) * sy[3];
-        gPx = R(3.0) * sx[4]; gPy = R(3.0) * sy[4];
-        gSx = R(3.0) * sx[5]; gSy = R(3.0) * sy[5];
+        const float2 gx01 = up2(sx01), gy01 = up2(sy01), gx23 = up2(sx23), gy23 = up2(sy23);
+        const float2 gx45 = up2(sx45), gy45 = up2(sy45);
+        gpx = R(3.0) * gx01.x; gpy = R(3.0) * gy01.x; lphi = R(3.0) * sl;
+        gTx = R(3.0) * gx01.y; gTy = R(3.0) * gy01.y;
+        gCx = R(3.0) * gx23.x; gCy = R(3.0) * gy23.x;
+        gfx = R(3.0) * gx23.y; gfy = R(3.0) * gy23.y;
+        gPx = R(3.0) * gx45.x; gPy = R(3.0) * gy45.x;
+        gSx = R(3.0) * gx45.y; gSy = R(3.0) * gy45.y;
     }
 
     // properties by the linear rule; the density gradient follows from it exactly
@@ -488,6 +548,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // with c_opp = -c_i: every equilibrium and source term splits into a part
     // even in c_i, shared by the pair, and an odd part that changes sign.
     constexpr int PAIR[4] = {1, 2, 5, 6};
+    // packed (i, opp(i)) halves: even part + (+1, -1) x odd part
+    const pf2 SGN = pk2(R(1.0), R(-1.0));
 
     // flow set (Sec. 3.2); d_i = g_i - 3 p_st (w_i - [i = 0]) is formed from the
     // stored deviation, the reference of the stored value being 3 p_st (w_i - [i = 0])
@@ -512,9 +574,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real cG = (real)cx(i) * Fqx + (real)cy(i) * Fqy;
             const real eq_e = w3 * p_lo + rho * w * (R(4.5) * cu * cu - R(1.5) * uu), eq_o = rho * w3 * cu;
             const real G_e = w * (S + R(9.0) * (cu * cF) - R(3.0) * uF), G_o = w3 * cG;
-            const real di = dg[i] + w3 * dpp, dj = dg[j] + w3 * dpp;
-            plane_ptr(pout, SET_G * 9 + i, K)[cell] = di - (di - (eq_e + eq_o)) * om_g + src_g * (G_e + G_o);
-            plane_ptr(pout, SET_G * 9 + j, K)[cell] = dj - (dj - (eq_e - eq_o)) * om_g + src_g * (G_e - G_o);
+            const pf2 d2 = fma2(splat2(w3), splat2(dpp), pk2(dg[i], dg[j]));
+            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e)), G2 = fma2(splat2(G_o), SGN, splat2(G_e));
+            const float2 o = up2(fma2(splat2(src_g), G2, fma2(sub2(eq2, d2), splat2(om_g), d2)));
+            plane_ptr(pout, SET_G * 9 + i, K)[cell] = o.x;
+            plane_ptr(pout, SET_G * 9 + j, K)[cell] = o.y;
         }
     }
 
@@ -541,13 +605,15 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const int ysi = y - cy(i), ysj = y - cy(j);
             const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
             const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
-            const real di = f[i] + w * ((wall_i ? phi_p : A.phip(-cy(i), -cx(i))) - phi_st);
-            const real dj = f[j] + w * ((wall_j ? phi_p : A.phip(-cy(j), -cx(j))) - phi_st);
+            const pf2 php2 = pk2(wall_i ? phi_p : A.phip(-cy(i), -cx(i)), wall_j ? phi_p : A.phip(-cy(j), -cx(j)));
+            const pf2 d2 = fma2(splat2(w), sub2(php2, splat2(phi_st)), pk2(f[i], f[j]));
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
             const real eq_e = w * phi_lo, eq_o = w3 * phi * cu;  // f_eq - w phi_st
             const real F_e = w * phi * mdot, F_o = w3 * ((real)cx(i) * ax + (real)cy(i) * ay);
-            plane_ptr(pout, SET_F * 9 + i, K)[cell] = di - (di - (eq_e + eq_o)) * om + src * (F_e + F_o);
-            plane_ptr(pout, SET_F * 9 + j, K)[cell] = dj - (dj - (eq_e - eq_o)) * om + src * (F_e - F_o);
+            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e)), F2 = fma2(splat2(F_o), SGN, splat2(F_e));
+            const float2 o = up2(fma2(splat2(src), F2, fma2(sub2(eq2, d2), splat2(om), d2)));
+            plane_ptr(pout, SET_F * 9 + i, K)[cell] = o.x;
+            plane_ptr(pout, SET_F * 9 + j, K)[cell] = o.y;
         }
 
         // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
@@ -571,8 +637,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
             const real eq_e = w * C, eq_o = w3 * C * cu;
             const real L_o = w3 * ((real)cx(i) * bx + (real)cy(i) * by);
-            plane_ptr(pout, SET_L * 9 + i, K)[cell] = l[i] - (l[i] - (eq_e + eq_o)) * om_l + src_l * L_o;
-            plane_ptr(pout, SET_L * 9 + j, K)[cell] = l[j] - (l[j] - (eq_e - eq_o)) * om_l - src_l * L_o;
+            const pf2 l2 = pk2(l[i], l[j]);
+            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e));
+            const float2 o = up2(fma2(splat2(src_l * L_o), SGN, fma2(sub2(eq2, l2), splat2(om_l), l2)));
+            plane_ptr(pout, SET_L * 9 + i, K)[cell] = o.x;
+            plane_ptr(pout, SET_L * 9 + j, K)[cell] = o.y;
         }
     }
 
@@ -597,16 +666,19 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const int ysi = y - cy(i), ysj = y - cy(j);
             const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
             const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
-            const real dhi = h[i] + w * rr * ((wall_i ? T_p : A.Tp(-cy(i), -cx(i))) - T_st);
-            const real dhj = h[j] + w * rr * ((wall_j ? T_p : A.Tp(-cy(j), -cx(j))) - T_st);
+            const pf2 Tps2 = pk2(wall_i ? T_p : A.Tp(-cy(i), -cx(i)), wall_j ? T_p : A.Tp(-cy(j), -cx(j)));
+            const pf2 dh2 = fma2(splat2(w * rr), sub2(Tps2, splat2(T_st)), pk2(h[i], h[j]));
+            const float2 dh = up2(dh2);
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
             const real es = w * (rr * T_lo + rcT * (R(4.5) * cu * cu - R(1.5) * uu));
             const real ea = w * rcT * R(3.0) * cu;
-            const real hs = R(0.5) * (dhi + dhj), ha = R(0.5) * (dhi - dhj);
+            const real hs = R(0.5) * (dh.x + dh.y), ha = R(0.5) * (dh.x - dh.y);
             const real rel_s = (hs - es) * om_s, rel_a = (ha - ea) * om_a, srcq = src_h * w * Q;
-            plane_ptr(pout, SET_H * 9 + i, K)[cell] = dhi - rel_a - rel_s + srcq;
-            plane_ptr(pout, SET_H * 9 + j, K)[cell] = dhj + rel_a - rel_s + srcq;
-            snz += dhi + dhj;
+            // (dh_i - rel_a, dh_j + rel_a) - rel_s + srcq
+            const float2 o = up2(add2(dh2, fma2(splat2(rel_a), pk2(R(-1.0), R(1.0)), splat2(srcq - rel_s))));
+            plane_ptr(pout, SET_H * 9 + i, K)[cell] = o.x;
+            plane_ptr(pout, SET_H * 9 + j, K)[cell] = o.y;
+            snz += dh.x + dh.y;
         }
         // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
         // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
