@@ -914,14 +914,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         }
     };
     // phase-A inputs of row y, and the own-cell lagged values phase B needs
-    auto stage_a = [&](int y) {
+    auto stage_a = [&](int y, int s3) {  // s3 = y mod 3
         if (WALLS && (y < 0 || y >= K.ny)) return;
         const int cell = y * K.pitch + xg;
-        float *pp = &w.pop[mod3(y)][0][lane];
+        float *pp = &w.pop[s3][0][lane];
         stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
         stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * 32);
         stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * 32);
-        float *pa = &w.ax[mod3(y)][0][lane];
+        float *pa = &w.ax[s3][0][lane];
         cp_async4(pa + AX_Q * 32, plane_ptr(ain, AUX_Q, K) + cell);
         cp_async4(pa + AX_FS * 32, plane_ptr(ain, AUX_FS, K) + cell);
         if (PB) {
@@ -943,12 +943,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     stage_lag(ya0 - 1);
     stage_lag(ya0);
     stage_lag(ya0 + 1);
-    stage_a(ya0);
+    int s3 = mod3(ya0);  // ya mod 3, advanced with the loop
+    stage_a(ya0, s3);
     cp_async_commit();
-    for (int ya = ya0; ya <= ya1; ya++) {
+    for (int ya = ya0; ya <= ya1; ya++, s3 = s3 == 2 ? 0 : s3 + 1) {
+        const int s3n = s3 == 2 ? 0 : s3 + 1, s3p = s3 == 0 ? 2 : s3 - 1;  // (ya + 1), (ya - 1) mod 3
         if (ya < ya1) {
             stage_lag(ya + 2);
-            stage_a(ya + 1);
+            stage_a(ya + 1, s3n);
         }
         stage_g(ya);
         cp_async_commit();
@@ -956,7 +958,6 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         __syncwarp();
         // ---- phase A, row ya ------------------------------------------------------------
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
-            const int s3 = mod3(ya);
             const float2 lag0 = w.lag[ya & 7][lane + 1];
             const real phi_p = lag0.x, T_p = lag0.y;
             float *pp = &w.pop[s3][0][lane];
@@ -992,7 +993,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         const int yb = ya - 1;
         if (PB && yb >= ys && yb < ye && b_lane) {
             const RingAcc A{w, lane, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
-                            mod3(yb), yb & 1};
+                            s3p, yb & 1};
             phase_b<MODE, WALLS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
         __syncwarp();
