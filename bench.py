@@ -161,6 +161,57 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
+    """Instance-steps/s of the droplet sweep: the batched persistent launch
+    (autotuned segment heights, CUDA graph) against the same instances stepped
+    one lattice at a time with the single-lattice launch."""
+    sweep = W.droplet_sweep(n=args.batch)
+    for w in sweep:
+        w["fields"] = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
+    n = len(sweep)
+    b = lbfreeze.Batch(sweep, stream=stream)
+    choice = b.tune(trials=3)
+    cells = b.cells
+    K = args.batch_steps
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(run):
+        run(2)  # warm-up (an even count keeps the instances in step)
+        stream.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run(K)
+        e1.record(stream)
+        e1.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    inst = [b.instance(i) for i in range(n)]
+
+    def sequential(k):
+        for s in inst:
+            s.step(k)
+
+    ms_b = timed(b.step)
+    ms_s = timed(sequential)
+    b.close()
+    v_b = ws * n * K / (ms_b * 1e-3)
+    v_s = ws * n * K / (ms_s * 1e-3)
+    return {"metric": "instance-steps/s", "value": round(v_b, 1), "unit": "instance-steps/s",
+            "workload": "droplet sweep: %d instances, side U[128,512], R U[0.2,0.35] side, Ste U[0.05,0.5], "
+                        "Ma U[0,50], C0 U[0,0.1], seed 20251109" % n,
+            "instances": n, "cells": cells, "steps": K, "mlups": round(ws * cells * K / (ms_b * 1e-3) / 1e6, 1),
+            "seg_rows_by_class": choice, "launches_per_step": 1,
+            "sequential": {"value": round(v_s, 1), "mlups": round(ws * cells * K / (ms_s * 1e-3) / 1e6, 1),
+                           "launches_per_step": n},
+            "speedup": round(v_b / v_s, 3)}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -226,6 +277,11 @@ def run_gpu(args):
     if ws > 1:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = ws * cells * args.steps / float(te.item()) / 1e6
+
+    # ---- batched form: a sweep of independent droplets in one launch per step -----------
+    batched = None
+    if args.batch > 0:
+        batched = _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist if ws > 1 else None)
     h2d = sum(v.numel() * 4 for v in pin_in.values()) / args.steps
     d2h = 8 * 8 + sum(v.numel() * 4 for v in pin_out.values()) / args.steps
 
@@ -259,6 +315,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d),
                 "d2h_bytes_per_step": round(d2h)},
         "gpu_launches": args.steps * launches_per_step,
+        "batched": batched,
         "clocks": clk.summary(),
         "check": {"sum_phi": red[0], "sum_C": red[2], "front": red[5]},
     }
@@ -275,6 +332,8 @@ def main():
     ap.add_argument("--impl", default="lbfreeze", choices=["lbfreeze", "reference"])
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=256, help="droplet-sweep instances of the batched leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -165,6 +165,53 @@ lb_status lb_load(lb_handle *h, const char *path);
 /* Free the handle and its device memory; NULL is a no-op. */
 void lb_destroy(lb_handle *h);
 
+/* ---- Batched instances -------------------------------------------------------
+ * Many independent lattices ("instances", each with its own lb_grid, lb_params
+ * and initial fields, as in a parameter sweep over droplets of uneven sizes)
+ * advanced together: one persistent kernel launch per step covers all of them,
+ * its warps taking (instance, 30-column strip, row segment) work items from a
+ * shared counter.  Every instance evolves exactly as a single-lattice handle
+ * created from the same inputs (bit for bit).  The paper runs its cases one at
+ * a time; this is the throughput form of the same step (Sec. 3). */
+typedef struct lb_batch lb_batch;
+
+/* Create n >= 1 instances: grids[i], params[i], init[i] as for lb_create (the
+ * same checks and errors; a failure names the instance in
+ * lb_batch_last_error(NULL)).  Synchronises the device. */
+lb_status lb_batch_create(int n, const lb_grid *grids, const lb_params *params, const lb_fields *init,
+                          lb_batch **out);
+
+/* Stream for the batch and all of its instances (NULL: legacy default stream). */
+lb_status lb_batch_set_stream(lb_batch *b, void *cuda_stream);
+
+/* Enqueue n >= 0 steps of every instance.  Pairs of steps are replayed from a
+ * CUDA graph captured on first use (lb_batch_use_graph(b, 0) launches them one
+ * by one instead).  Asynchronous.  Returns LB_ERR_INVALID_ARG if instances were
+ * stepped separately (lb_step on an instance handle) by different counts. */
+lb_status lb_batch_step(lb_batch *b, int n);
+lb_status lb_batch_use_graph(lb_batch *b, int on);
+
+/* Autotuner: for each size class (lattice rows < 192, < 320, >= 320) time
+ * `trials` batched launches with inner row segments of 8, 16, 32 and 64 rows
+ * and keep the fastest; seg_rows (3 ints, may be NULL) receives the choice per
+ * class (0 for an empty class).  The trial launches do not advance the state.
+ * Synchronises the stream. */
+lb_status lb_batch_tune(lb_batch *b, int trials, int seg_rows[3]);
+
+/* Handle of instance i (0 <= i < n), owned by the batch: use it with
+ * lb_get_fields, lb_reduce, lb_save..., but do not destroy it. */
+lb_status lb_batch_instance(lb_batch *b, int i, lb_handle **out);
+
+/* Number of instances and total cells (either pointer may be NULL). */
+lb_status lb_batch_size(const lb_batch *b, int *n, long long *cells);
+
+/* Message of the last failure on the batch (or of the last failed
+ * lb_batch_create when b is NULL); never NULL. */
+const char *lb_batch_last_error(const lb_batch *b);
+
+/* Free the batch and all of its instances; NULL is a no-op. */
+void lb_batch_destroy(lb_batch *b);
+
 /* Static description of a status code. */
 const char *lb_error_string(int status);
 

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "lb_kernels.cuh"
 #include "lbfreeze.h"
@@ -27,6 +28,9 @@ struct lb_handle {
     double *partials = nullptr;  // reduction partials, red_parts * NRED
     double *red_out = nullptr;   // NRED doubles on the device
     unsigned *status = nullptr;
+    lbk::StepRec *rec = nullptr;          // the step kernel's record of this lattice
+    unsigned long long *counter = nullptr;  // the step kernel's work counters (2)
+    long long nitems = 0;                   // work items of one step
     int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
     int cur = 0;
     cudaStream_t stream = nullptr;
@@ -150,6 +154,7 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.gx = (real)p->gx; K.gy = (real)p->gy;
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
+    K.segh = LB_SEGH;
     K.phase_change = p->phase_change_on ? 1 : 0;
     return K;
 }
@@ -158,7 +163,10 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
 // (blocks first) and the inner segments.  MODE_REDUCE caps the grid at one wave
 // of resident blocks, each block then owning several (strip group, segment)
 // pairs, and writes one partial per warp.
-static unsigned strip_blocks(const Consts &K) { return (unsigned)(lbk::strip_groups(K.nx) * lbk::strip_segments(K.ny)); }
+static unsigned strip_blocks(const Consts &K)
+{
+    return (unsigned)(lbk::strip_groups(K.nx) * lbk::strip_segments(K.ny, K.segh));
+}
 
 static unsigned reduce_blocks(const Consts &K)
 {
@@ -188,6 +196,42 @@ static int flat_blocks(long long n, int threads)
     return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
+// Record of lattice h for the step kernel, its work items numbered from item0;
+// returns the number of items.
+static long long fill_record(const lb_handle *h, lbk::StepRec &r, long long item0)
+{
+    r.K = h->K;
+    for (int p = 0; p < 2; p++) {
+        r.B[p].pin = h->pops[p];
+        r.B[p].pout = h->pops[1 - p];
+        r.B[p].ain = h->aux[p];
+        r.B[p].aout = h->aux[1 - p];
+        r.B[p].fields = nullptr;
+        r.B[p].status = h->status;
+    }
+    r.nstrip = (h->K.nx + LB_TX - 1) / LB_TX;
+    r.item0 = item0;
+    return (long long)r.nstrip * lbk::strip_segments(h->K.ny, h->K.segh);
+}
+
+// One step of ninst lattices (records rec, nitems work items in all) from buffer
+// `parity`: a persistent launch of at most one wave of resident blocks.
+static cudaError_t launch_step(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
+                               unsigned long long *counter, cudaStream_t st)
+{
+    if (lbk::STEP_SMEM > 48 * 1024) {
+        static bool opted = false;
+        if (!opted) {
+            cudaFuncSetAttribute(lbk::lb_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbk::STEP_SMEM);
+            opted = true;
+        }
+    }
+    const long long wave = 152LL * LB_SMINB, need = (nitems + LB_SW - 1) / LB_SW;
+    const unsigned grid = (unsigned)(need < wave ? (need < 1 ? 1 : need) : wave);
+    lbk::lb_step_kernel<<<grid, dim3(32, LB_SW, 1), lbk::STEP_SMEM, st>>>(rec, ninst, nitems, parity, counter);
+    return cudaGetLastError();
+}
+
 static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
 {
     const Consts &K = h->K;
@@ -209,7 +253,8 @@ static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
 
 static void free_all(lb_handle *h)
 {
-    void *ptrs[] = {h->pops[0], h->pops[1], h->aux[0], h->aux[1], h->fields, h->partials, h->red_out, h->status};
+    void *ptrs[] = {h->pops[0], h->pops[1], h->aux[0], h->aux[1], h->fields, h->partials, h->red_out, h->status,
+                    h->rec,     h->counter};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -242,6 +287,8 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     if (e == cudaSuccess) e = alloc((void **)&h->partials, sizeof(double) * lbk::NRED * h->red_parts);
     if (e == cudaSuccess) e = alloc((void **)&h->red_out, sizeof(double) * lbk::NRED);
     if (e == cudaSuccess) e = alloc((void **)&h->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = alloc((void **)&h->rec, sizeof(lbk::StepRec));
+    if (e == cudaSuccess) e = alloc((void **)&h->counter, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         lb_status s = cuda_fail(nullptr, e, "cudaMalloc");
         cudaGetLastError();
@@ -256,7 +303,11 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     lb_status st = LB_OK;
     do {
         cudaError_t me = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->stream);
-        if (me != cudaSuccess) { st = cuda_fail(h, me, "cudaMemsetAsync"); break; }
+        if (me == cudaSuccess) me = cudaMemsetAsync(h->counter, 0, 2 * sizeof(unsigned long long), h->stream);
+        lbk::StepRec rec;
+        h->nitems = fill_record(h, rec, 0);
+        if (me == cudaSuccess) me = cudaMemcpyAsync(h->rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, h->stream);
+        if (me != cudaSuccess) { st = cuda_fail(h, me, "step record"); break; }
         for (int k = 0; k < 5; k++) {
             if (!src[k]) continue;
             float *d = h->fields + (size_t)k * K.plane;
@@ -300,16 +351,8 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
     if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
     if (h->sticky != LB_OK) return h->sticky;
     for (int s = 0; s < n; s++) {
-        lbk::Buffers B;
-        B.pin = h->pops[h->cur];
-        B.pout = h->pops[1 - h->cur];
-        B.ain = h->aux[h->cur];
-        B.aout = h->aux[1 - h->cur];
-        B.fields = nullptr;
-        B.status = h->status;
-        launch_strip<lbk::MODE_STEP>(h->K, B, h->stream);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(h, e, "lb_strip_kernel launch");
+        cudaError_t e = launch_step(h->rec, 1, h->nitems, h->cur, h->counter, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
         h->cur = 1 - h->cur;
         h->steps++;
     }
@@ -565,4 +608,240 @@ extern "C" lb_status lb_reduce_noalloc(lb_handle *h, double out[8])
     for (int k = 0; k < 6; k++) finite = finite && std::isfinite(r[k]);
     if (status || !finite) return fail(h, LB_ERR_UNSTABLE, "non-finite value in the lattice state");
     return LB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched instances: independent lattices advanced by one persistent launch per step.
+// The instances are ordinary handles owned by the batch, so the per-handle calls
+// (fields, diagnostics, checkpoints) work on each of them.
+// ---------------------------------------------------------------------------------------
+struct lb_batch {
+    std::vector<lb_handle *> h;
+    std::vector<lbk::StepRec> inst;
+    lbk::StepRec *d_inst = nullptr;
+    unsigned long long *d_counter = nullptr;
+    long long nitems = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;                   // stream used to capture the step graphs
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // two steps, starting from buffer 0 or 1
+    bool use_graph = true;
+    lb_status sticky = LB_OK;
+    std::string err;
+};
+
+static std::string g_batch_create_error;
+
+static lb_status bfail(lb_batch *b, lb_status s, const std::string &msg)
+{
+    if (b) {
+        if (b->sticky == LB_OK && (s == LB_ERR_CUDA || s == LB_ERR_UNSTABLE)) b->sticky = s;
+        b->err = msg;
+    } else {
+        g_batch_create_error = msg;
+    }
+    return s;
+}
+
+#define BCK(b, call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void drop_graphs(lb_batch *b)
+{
+    for (auto &g : b->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Size class of an instance for the autotuner: by lattice rows.
+static int size_class(const lb_handle *h) { return h->K.ny < 192 ? 0 : (h->K.ny < 320 ? 1 : 2); }
+
+// Rebuild the work list and the device copy of the per-instance records.
+static lb_status upload_instances(lb_batch *b)
+{
+    long long item = 0;
+    for (size_t i = 0; i < b->h.size(); i++) item += fill_record(b->h[i], b->inst[i], item);
+    b->nitems = item;
+    BCK(b, cudaMemcpy(b->d_inst, b->inst.data(), sizeof(lbk::StepRec) * b->inst.size(), cudaMemcpyHostToDevice));
+    drop_graphs(b);
+    return LB_OK;
+}
+
+// One batched step from buffer `parity` on stream st.
+static lb_status launch_batch(lb_batch *b, int parity, cudaStream_t st)
+{
+    BCK(b, launch_step(b->d_inst, (int)b->h.size(), b->nitems, parity, b->d_counter, st));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_create(int n, const lb_grid *grids, const lb_params *params, const lb_fields *init,
+                                     lb_batch **out)
+{
+    if (n < 1 || !grids || !params || !init || !out) return bfail(nullptr, LB_ERR_INVALID_ARG, "null argument or n < 1");
+    lb_batch *b = new lb_batch();
+    for (int i = 0; i < n; i++) {
+        lb_handle *h = nullptr;
+        lb_status s = lb_create(&grids[i], &params[i], &init[i], &h);
+        if (s != LB_OK) {
+            std::string why = "instance " + std::to_string(i) + ": " + lb_last_error(nullptr);
+            lb_batch_destroy(b);
+            return bfail(nullptr, s, why);
+        }
+        b->h.push_back(h);
+    }
+    b->inst.resize(n);
+    lb_status s = LB_OK;
+    cudaError_t e = cudaMalloc((void **)&b->d_inst, sizeof(lbk::StepRec) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_counter, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) s = bfail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, cudaGetErrorString(e));
+    if (s == LB_OK) {
+        s = upload_instances(b);
+        if (s != LB_OK) g_batch_create_error = b->err;
+    }
+    if (s != LB_OK) {
+        lb_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_set_stream(lb_batch *b, void *cuda_stream)
+{
+    if (!b) return LB_ERR_INVALID_ARG;
+    b->stream = (cudaStream_t)cuda_stream;
+    for (lb_handle *h : b->h) h->stream = b->stream;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_use_graph(lb_batch *b, int on)
+{
+    if (!b) return LB_ERR_INVALID_ARG;
+    b->use_graph = on != 0;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_step(lb_batch *b, int n)
+{
+    if (!b || n < 0) return bfail(b, LB_ERR_INVALID_ARG, "null batch or negative step count");
+    if (b->sticky != LB_OK) return b->sticky;
+    const int p = b->h[0]->cur;
+    for (lb_handle *h : b->h) {
+        if (h->sticky != LB_OK) return bfail(b, h->sticky, "an instance is in an error state: " + h->err);
+        if (h->cur != p) return bfail(b, LB_ERR_INVALID_ARG, "instances were stepped separately and are out of step");
+    }
+    int done = 0;
+    if (b->use_graph && n >= 2) {
+        if (!b->gexec[p]) {
+            cudaGraph_t g = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            lb_status s1 = launch_batch(b, p, b->cap);
+            lb_status s2 = s1 == LB_OK ? launch_batch(b, 1 - p, b->cap) : s1;
+            cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+            if (s2 != LB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s2;
+            }
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&b->gexec[p], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        for (; done + 2 <= n; done += 2) BCK(b, cudaGraphLaunch(b->gexec[p], b->stream));
+    }
+    for (int par = (p + done) & 1; done < n; done++, par ^= 1) {
+        lb_status s = launch_batch(b, par, b->stream);
+        if (s != LB_OK) return s;
+    }
+    for (lb_handle *h : b->h) {
+        h->cur = (h->cur + n) & 1;
+        h->steps += n;
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_tune(lb_batch *b, int trials, int seg_rows[3])
+{
+    if (!b || trials < 1) return bfail(b, LB_ERR_INVALID_ARG, "null batch or trials < 1");
+    if (b->sticky != LB_OK) return b->sticky;
+    const int cand[4] = {8, 16, 32, 64};
+    const int p = b->h[0]->cur;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    lb_status st = LB_OK;
+    int best_all[3] = {0, 0, 0};
+    for (int c = 0; c < 3 && st == LB_OK; c++) {
+        bool any = false;
+        for (lb_handle *h : b->h) any = any || size_class(h) == c;
+        if (!any) continue;
+        float best_ms = 0.0f;
+        int best = 0;
+        for (int k = 0; k < 4 && st == LB_OK; k++) {
+            for (lb_handle *h : b->h)
+                if (size_class(h) == c) h->K.segh = cand[k];
+            st = upload_instances(b);
+            // trial launches read the current buffer and write the other one, which the
+            // next real step overwrites: the state does not move
+            if (st == LB_OK) st = launch_batch(b, p, b->stream);
+            if (st != LB_OK) break;
+            cudaEventRecord(e0, b->stream);
+            for (int t = 0; t < trials && st == LB_OK; t++) st = launch_batch(b, p, b->stream);
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = bfail(b, LB_ERR_CUDA, "tuning timing");
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best == 0 || ms < best_ms) {
+                best_ms = ms;
+                best = cand[k];
+            }
+        }
+        for (lb_handle *h : b->h)
+            if (size_class(h) == c) h->K.segh = best;
+        best_all[c] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == LB_OK) st = upload_instances(b);
+    if (seg_rows)
+        for (int c = 0; c < 3; c++) seg_rows[c] = best_all[c];
+    return st;
+}
+
+extern "C" lb_status lb_batch_instance(lb_batch *b, int i, lb_handle **out)
+{
+    if (!b || !out || i < 0 || i >= (int)b->h.size()) return bfail(b, LB_ERR_INVALID_ARG, "bad instance index");
+    *out = b->h[i];
+    return LB_OK;
+}
+
+extern "C" lb_status lb_batch_size(const lb_batch *b, int *n, long long *cells)
+{
+    if (!b) return LB_ERR_INVALID_ARG;
+    if (n) *n = (int)b->h.size();
+    if (cells) {
+        long long c = 0;
+        for (const lb_handle *h : b->h) c += (long long)h->K.nx * h->K.ny;
+        *cells = c;
+    }
+    return LB_OK;
+}
+
+extern "C" const char *lb_batch_last_error(const lb_batch *b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+extern "C" void lb_batch_destroy(lb_batch *b)
+{
+    if (!b) return;
+    drop_graphs(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->d_inst) cudaFree(b->d_inst);
+    if (b->d_counter) cudaFree(b->d_counter);
+    for (lb_handle *h : b->h) lb_destroy(h);
+    delete b;
 }

@@ -1,9 +1,11 @@
 // lb_kernels.cuh -- sm_103a kernels of the fused diffuse-interface LB freezing step.
 //
-// The launches of lb_strip_kernel over all row segments advance the lattice by one time step of
-// the four coupled D2Q9 sets of arXiv 2511.09422, Sec. 3: phase field f
-// (BGK, Sec. 3.1), pressure-based flow g (BGK, Sec. 3.2), total enthalpy h
-// (two-relaxation-time, Sec. 3.3) and solute l (BGK, Sec. 3.4).
+// One launch of lb_step_kernel advances a lattice -- or a batch of independent
+// lattices -- by one time step of the four coupled D2Q9 sets of arXiv
+// 2511.09422, Sec. 3: phase field f (BGK, Sec. 3.1), pressure-based flow g
+// (BGK, Sec. 3.2), total enthalpy h (two-relaxation-time, Sec. 3.3) and solute
+// l (BGK, Sec. 3.4).  lb_strip_kernel runs the same sweep to read out the
+// macroscopic fields or the diagnostics sums.
 //
 // Memory layout (HBM): structure of arrays.  Every population direction and
 // every lagged field is a plane of pitch*ny floats (row pitch a multiple of
@@ -29,7 +31,7 @@
 // that the large parts -- phi ~ 1, the pressure, T, and the latent enthalpy
 // ~ rho_l L -- cancel analytically instead of in FP32.
 //
-// Strip form (lb_strip_kernel): each warp owns a strip of 30 columns plus a
+// Strip form (lb_step_kernel, lb_strip_kernel): each warp owns a strip of 30 columns plus a
 // one-column halo on each side (32 lanes) and walks down a segment of rows.
 // Per row y it runs phase A -- the local fields of the step (T, f_s, mdot,
 // phi, C) from the pulled f, h, l -- into per-warp shared-memory rings, and
@@ -81,6 +83,7 @@ struct Consts {
     real sigma0, sigma_T, sigma_c, T_ref, c_ref, gx, gy;
     real expand;                // 1 - rho_s / rho_l
     int fs_mod, phase_change;
+    int segh;                   // rows of an inner segment of the strip sweep
 };
 
 struct Buffers {
@@ -726,7 +729,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 //   ax   staged own-cell Q, f_s, u_x, u_y, C                rows y mod 3
 //   gp   staged pulls of g                                  rows y & 1
 // One launch covers the lattice.  Per group of LB_SW strips it has two bands with
-// the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of LB_SEGH
+// the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of K.segh
 // rows inside 2 .. ny-3, whose rows and pull sources (ys - 2 .. ye + 1) all lie
 // inside the lattice and which run without any wall rule.  Blocks are numbered
 // strip group fastest, the two bands first.
@@ -738,7 +741,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #define LB_SMINB 4
 #endif
 #ifndef LB_SEGH
-#define LB_SEGH 32
+#define LB_SEGH 32  // inner segment height of single-lattice handles
 #endif
 
 constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
@@ -757,10 +760,10 @@ struct WarpRing {
 constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
 
 __host__ __device__ inline int strip_groups(int nx) { return ((nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW; }
-__host__ __device__ inline int strip_segments(int ny) { return 2 + (ny >= 5 ? (ny - 4 + LB_SEGH - 1) / LB_SEGH : 0); }
+__host__ __device__ inline int strip_segments(int ny, int segh) { return 2 + (ny >= 5 ? (ny - 4 + segh - 1) / segh : 0); }
 
-// Rows [ys, ye) of segment s (empty when ys >= ye).
-__device__ __forceinline__ void segment_rows(int ny, int s, int &ys, int &ye)
+// Rows [ys, ye) of segment s (empty when ys >= ye); inner segments of segh rows.
+__device__ __forceinline__ void segment_rows(int ny, int segh, int s, int &ys, int &ye)
 {
     if (s == 0) {
         ys = 0;
@@ -769,8 +772,8 @@ __device__ __forceinline__ void segment_rows(int ny, int s, int &ys, int &ye)
         ys = max(2, ny - 2);
         ye = ny;
     } else {
-        ys = 2 + (s - 2) * LB_SEGH;
-        ye = min(ys + LB_SEGH, ny - 2);
+        ys = 2 + (s - 2) * segh;
+        ye = min(ys + segh, ny - 2);
     }
 }
 
@@ -1015,14 +1018,14 @@ __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B,
     WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
     const int lane = threadIdx.x;
     const int ngroups = strip_groups(K.nx);
-    const int nblocks = ngroups * strip_segments(K.ny);
+    const int nblocks = ngroups * strip_segments(K.ny, K.segh);
     double acc[NRED] = {0, 0, 0, 0, 0, 0};
     // a block may own several (group, segment) pairs when the grid is capped
     for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
         const int group = b % ngroups, seg = b / ngroups;
         const int x0 = (group * LB_SW + (int)threadIdx.y) * LB_TX;
         int ys, ye;
-        segment_rows(K.ny, seg, ys, ye);
+        segment_rows(K.ny, K.segh, seg, ys, ye);
         if (x0 >= K.nx || ys >= ye) continue;  // the whole warp: warps never synchronise with one another
         if (seg < 2)
             strip_rows<MODE, true>(K, B, w, lane, x0, ys, ye, acc);
@@ -1037,6 +1040,71 @@ __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B,
             const double s = warp_sum(acc[q]);
             if (lane == 0) partials[((long long)blockIdx.x * LB_SW + threadIdx.y) * NRED + q] = s;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// The step: one persistent launch advances one lattice or a batch of many
+// independent lattices (instances) by one time step.  The work items are
+// (instance, warp strip, row segment), numbered instance by instance from
+// item0; warps claim them from an atomic counter, so uneven instance sizes
+// balance dynamically.  counter[0] counts claimed items and counter[1] the
+// warps that found the list empty; the last of those resets both, so every
+// launch starts from zero without a separate reset.  The constants of an instance are
+// read from its read-only record in global memory (cached; no shared-memory
+// aliasing with the rings to hold the compiler back).  Each item computes
+// exactly what the single-lattice launch computes for that strip and segment,
+// so the result does not depend on which warp takes which item.
+// ---------------------------------------------------------------------------------------
+struct StepRec {
+    Consts K;
+    Buffers B[2];     // [0]: first buffer -> second, [1]: the reverse
+    int nstrip;       // warp strips of the instance
+    long long item0;  // first work item of the instance
+};
+
+constexpr size_t STEP_SMEM = STRIP_SMEM;
+
+__global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst, int ninst, long long nitems,
+                                                int parity, unsigned long long *__restrict__ counter)
+{
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * blockDim.y;
+    extern __shared__ __align__(16) unsigned char lb_smem[];
+    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
+    const int lane = threadIdx.x;
+    double acc[NRED];  // unused in MODE_STEP
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1ULL);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= (unsigned long long)nitems) {
+            if (lane == 0 && atomicAdd(counter + 1, 1ULL) == nwarps - 1) {
+                counter[0] = 0;  // every warp is done claiming: ready for the next launch
+                counter[1] = 0;
+            }
+            break;
+        }
+        int lo = 0, hi = ninst - 1;  // last instance with item0 <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (inst[mid].item0 <= (long long)item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const Consts K = inst[lo].K;  // by value: the fields the sweep uses stay in registers
+        const Buffers B = inst[lo].B[parity];
+        const long long local = (long long)item - inst[lo].item0;
+        const int nstrip = inst[lo].nstrip;
+        const int strip = (int)(local % nstrip), seg = (int)(local / nstrip);
+        int ys, ye;
+        segment_rows(K.ny, K.segh, seg, ys, ye);
+        if (ys >= ye) continue;
+        if (seg < 2)
+            strip_rows<MODE_STEP, true>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
+        else
+            strip_rows<MODE_STEP, false>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
+        __syncwarp();
     }
 }
 

@@ -53,7 +53,9 @@ _lib = None
 _lock = threading.Lock()
 
 EXPORTS = ("lb_create", "lb_set_stream", "lb_step", "lb_get_fields", "lb_reduce", "lb_steps_taken",
-           "lb_save", "lb_load", "lb_destroy", "lb_error_string", "lb_last_error", "lb_device_bytes")
+           "lb_save", "lb_load", "lb_destroy", "lb_error_string", "lb_last_error", "lb_device_bytes",
+           "lb_batch_create", "lb_batch_set_stream", "lb_batch_step", "lb_batch_use_graph", "lb_batch_tune",
+           "lb_batch_instance", "lb_batch_size", "lb_batch_last_error", "lb_batch_destroy")
 
 
 def library_path() -> str:
@@ -94,6 +96,25 @@ def load(path: str | None = None):
         L.lb_last_error.argtypes = [C.c_void_p]
         L.lb_device_bytes.restype = C.c_size_t
         L.lb_device_bytes.argtypes = [C.c_void_p]
+        L.lb_batch_create.restype = C.c_int
+        L.lb_batch_create.argtypes = [C.c_int, C.POINTER(lb_grid), C.POINTER(lb_params), C.POINTER(lb_fields),
+                                      C.POINTER(C.c_void_p)]
+        L.lb_batch_set_stream.restype = C.c_int
+        L.lb_batch_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.lb_batch_step.restype = C.c_int
+        L.lb_batch_step.argtypes = [C.c_void_p, C.c_int]
+        L.lb_batch_use_graph.restype = C.c_int
+        L.lb_batch_use_graph.argtypes = [C.c_void_p, C.c_int]
+        L.lb_batch_tune.restype = C.c_int
+        L.lb_batch_tune.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int)]
+        L.lb_batch_instance.restype = C.c_int
+        L.lb_batch_instance.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+        L.lb_batch_size.restype = C.c_int
+        L.lb_batch_size.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+        L.lb_batch_last_error.restype = C.c_char_p
+        L.lb_batch_last_error.argtypes = [C.c_void_p]
+        L.lb_batch_destroy.restype = None
+        L.lb_batch_destroy.argtypes = [C.c_void_p]
         _lib = L
         return _lib
 
@@ -189,7 +210,20 @@ class Solver:
         self._stream_obj = stream
         self._check(load().lb_set_stream(self._h, C.c_void_p(int(ptr) if ptr else 0)))
 
+    @classmethod
+    def _view(cls, handle: int, nx: int, ny: int, owner) -> "Solver":
+        """A Solver over a handle owned elsewhere (a batch instance); close() leaves it alone."""
+        s = cls.__new__(cls)
+        s.nx, s.ny = nx, ny
+        s._h = C.c_void_p(handle)
+        s._stream_obj = None
+        s._owner = owner
+        return s
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._h = C.c_void_p()
+            return
         if getattr(self, "_h", None) is not None and self._h.value:
             load().lb_destroy(self._h)
             self._h = C.c_void_p()
@@ -277,3 +311,94 @@ class Solver:
 
 def from_workload(w: dict, stream=None) -> Solver:
     return Solver(w["grid"], w["params"], w["fields"], stream=stream)
+
+
+class Batch:
+    """Independent lattices advanced together by one persistent launch per step.
+
+    ``workloads`` is a list of dicts with ``grid``, ``params`` and ``fields``
+    (host arrays, as for Solver).  ``instance(i)`` gives a Solver view of
+    instance i for fields / reduce / save; the batch owns it."""
+
+    def __init__(self, workloads, stream=None):
+        L = load()
+        n = len(workloads)
+        if n < 1:
+            raise ValueError("a batch needs at least one instance")
+        grids = (lb_grid * n)()
+        params = (lb_params * n)()
+        fields = (lb_fields * n)()
+        self._keep = []
+        self.shapes = []
+        for i, w in enumerate(workloads):
+            g = w["grid"]
+            nx, ny = int(g["nx"]), int(g["ny"])
+            grids[i] = make_grid(g)
+            params[i] = make_params(w["params"])
+            f = lb_fields()
+            for k in ("phi", "T", "C", "ux", "uy"):
+                v = w["fields"].get(k)
+                if v is None:
+                    setattr(f, k, None)
+                    continue
+                v = np.ascontiguousarray(_host_array(v).reshape(-1))
+                if v.size != nx * ny:
+                    raise ValueError("instance %d: field %s has %d values, expected %d" % (i, k, v.size, nx * ny))
+                self._keep.append(v)
+                setattr(f, k, v.ctypes.data_as(_fp))
+            f.on_device = 0
+            fields[i] = f
+            self.shapes.append((nx, ny))
+        h = C.c_void_p()
+        st = L.lb_batch_create(n, grids, params, fields, C.byref(h))
+        if st != LB_OK:
+            raise LbError(st, L.lb_batch_last_error(None).decode())
+        self._keep = []
+        self._h = h
+        self.n = n
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, st: int):
+        if st != LB_OK:
+            raise LbError(st, load().lb_batch_last_error(self._h).decode())
+
+    def set_stream(self, stream):
+        ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+        self._stream_obj = stream
+        self._check(load().lb_batch_set_stream(self._h, C.c_void_p(int(ptr) if ptr else 0)))
+
+    def step(self, n: int = 1):
+        self._check(load().lb_batch_step(self._h, int(n)))
+
+    def use_graph(self, on: bool):
+        self._check(load().lb_batch_use_graph(self._h, 1 if on else 0))
+
+    def tune(self, trials: int = 5):
+        """Autotune the inner segment height per size class; returns the choices."""
+        out = (C.c_int * 3)()
+        self._check(load().lb_batch_tune(self._h, int(trials), out))
+        return list(out)
+
+    def instance(self, i: int) -> Solver:
+        h = C.c_void_p()
+        self._check(load().lb_batch_instance(self._h, int(i), C.byref(h)))
+        nx, ny = self.shapes[i]
+        return Solver._view(h.value, nx, ny, self)
+
+    @property
+    def cells(self) -> int:
+        c = C.c_longlong()
+        self._check(load().lb_batch_size(self._h, None, C.byref(c)))
+        return int(c.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lb_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -222,6 +222,30 @@ def static_droplet(nx=96, ny=96, radius=20.0, sigma=0.01, rho_g=1.0, steps=4000)
                 fields=_fields(phi, T, C), steps=steps, meta=dict(radius=radius, sigma=sigma))
 
 
+def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, steps=1000) -> list:
+    """A parameter sweep of independent freezing sessile droplets (the batched
+    workload): square lattices with side uniform in [side_min, side_max],
+    radius uniform in [0.2, 0.35] of the side, Stefan number uniform in
+    [0.05, 0.5], Ma_T = Ma_C uniform in [0, 50], initial solute uniform in
+    [0, 0.1], all drawn from numpy's default_rng(seed).  Contact angle 90
+    degrees for all (the only wetting condition implemented), gas density
+    ratio 0.1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(side_min, side_max + 1))
+        radius = float(rng.uniform(0.2, 0.35)) * side
+        ste = float(rng.uniform(0.05, 0.5))
+        ma = float(rng.uniform(0.0, 50.0))
+        c0 = float(rng.uniform(0.0, 0.1))
+        w = sessile_droplet(nx=side, ny=side, radius=radius, rho_g=rho_g, ste=ste, c0=c0, ma_T=ma, ma_C=ma)
+        w["name"] = "sweep_%03d_%d" % (i, side)
+        w["steps"] = steps
+        w["meta"].update(side=side)
+        out.append(w)
+    return out
+
+
 WORKLOADS = {
     "stefan_layer": stefan_layer,
     "thermocapillary_channel": thermocapillary_channel,

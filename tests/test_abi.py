@@ -100,3 +100,17 @@ def test_workloads_are_seeded():
         assert np.array_equal(a["fields"][k], b["fields"][k])
     c = W.parity_droplet(nx=32, ny=32, seed=1)
     assert not np.array_equal(a["fields"]["T"], c["fields"]["T"])
+
+
+def test_droplet_sweep_is_seeded_and_in_range():
+    a = W.droplet_sweep(n=12)
+    b = W.droplet_sweep(n=12)
+    for wa, wb in zip(a, b):
+        assert wa["grid"] == wb["grid"] and wa["params"] == wb["params"]
+        for k in wa["fields"]:
+            assert np.array_equal(wa["fields"][k], wb["fields"][k])
+        side = wa["grid"]["nx"]
+        assert wa["grid"]["ny"] == side and 128 <= side <= 512
+        assert 0.2 * side <= wa["meta"]["radius"] <= 0.35 * side
+        assert 0.05 <= wa["meta"]["ste"] <= 0.5 and 0.0 <= wa["meta"]["c0"] <= 0.1
+    assert len({w["grid"]["nx"] for w in a}) > 6  # uneven sizes
