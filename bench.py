@@ -31,7 +31,7 @@ sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = 360  # 36 populations read + written, 9 lagged fields read + written, FP32
 WORKLOAD = dict(name="impurity_front", nx=4096, ny=4096)
-PROFILE = os.path.join(ROOT, "profiles", "lb_strip_kernel_impurity_front.md")
+PROFILE = os.path.join(ROOT, "profiles", "lb_step_kernel_impurity_front.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2511_09422_gb300", "csrc", "lb_kernels.cuh")
 
 
