@@ -549,15 +549,26 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
     // The collisions run over the rest direction and the four pairs (i, opp(i))
     // with c_opp = -c_i: every equilibrium and source term splits into a part
-    // even in c_i, shared by the pair, and an odd part that changes sign.
-    constexpr int PAIR[4] = {1, 2, 5, 6};
-    // packed (i, opp(i)) halves: even part + (+1, -1) x odd part
-    const pf2 SGN = pk2(R(1.0), R(-1.0));
+    // even in c_i, shared by the pair, and an odd part that changes sign.  The
+    // pairs go two at a time, (1, 2) and (5, 6) -- each two of equal weight -- as
+    // packed f32x2 values: "p" holds directions (a, a + 1), "m" their opposites.
+    float *__restrict__ pout = B.pout;
+    auto store4 = [&](int set, int a, const pf2 vp, const pf2 vm) {
+        const float2 op = up2(vp), om2 = up2(vm);
+        plane_ptr(pout, set * 9 + a, K)[cell] = op.x;
+        plane_ptr(pout, set * 9 + a + 1, K)[cell] = op.y;
+        plane_ptr(pout, set * 9 + opp(a), K)[cell] = om2.x;
+        plane_ptr(pout, set * 9 + opp(a + 1), K)[cell] = om2.y;
+    };
+    // (c_a . v, c_{a+1} . v)
+    auto cdot2 = [](int a, real vx, real vy) {
+        return pk2((real)cx(a) * vx + (real)cy(a) * vy, (real)cx(a + 1) * vx + (real)cy(a + 1) * vy);
+    };
+    const pf2 u2 = splat2(R(-1.5) * uu);
 
     // flow set (Sec. 3.2); d_i = g_i - 3 p_st (w_i - [i = 0]) is formed from the
     // stored deviation, the reference of the stored value being 3 p_st (w_i - [i = 0])
     const real om_g = rcp(tau_g), src_g = R(1.0) - R(0.5) * om_g;
-    float *__restrict__ pout = B.pout;
     {
         const real dpp = p_p - p_st;
         const real Fqx = Fx + rfx, Fqy = Fy + rfy;  // F + rho f
@@ -569,19 +580,19 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             plane_ptr(pout, SET_G * 9 + 0, K)[cell] = d - (d - deq) * om_g + src_g * G0;
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = PAIR[q], j = opp(i);
-            const real w = wgt(i), w3 = R(3.0) * w;
-            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real cF = (real)cx(i) * Ftx + (real)cy(i) * Fty;
-            const real cG = (real)cx(i) * Fqx + (real)cy(i) * Fqy;
-            const real eq_e = w3 * p_lo + rho * w * (R(4.5) * cu * cu - R(1.5) * uu), eq_o = rho * w3 * cu;
-            const real G_e = w * (S + R(9.0) * (cu * cF) - R(3.0) * uF), G_o = w3 * cG;
-            const pf2 d2 = fma2(splat2(w3), splat2(dpp), pk2(dg[i], dg[j]));
-            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e)), G2 = fma2(splat2(G_o), SGN, splat2(G_e));
-            const float2 o = up2(fma2(splat2(src_g), G2, fma2(sub2(eq2, d2), splat2(om_g), d2)));
-            plane_ptr(pout, SET_G * 9 + i, K)[cell] = o.x;
-            plane_ptr(pout, SET_G * 9 + j, K)[cell] = o.y;
+        for (int q = 0; q < 2; q++) {
+            const int a = q == 0 ? 1 : 5;
+            const real w = wgt(a), w3 = R(3.0) * w;
+            const pf2 cu = cdot2(a, ux, uy), cF = cdot2(a, Ftx, Fty), cG = cdot2(a, Fqx, Fqy);
+            const pf2 eq_e = fma2(splat2(rho * w), fma2(splat2(R(4.5)), mul2(cu, cu), u2), splat2(w3 * p_lo));
+            const pf2 eq_o = mul2(splat2(rho * w3), cu);
+            const pf2 G_e = fma2(splat2(R(9.0) * w), mul2(cu, cF), splat2(w * (S - R(3.0) * uF)));
+            const pf2 G_o = mul2(splat2(w3), cG);
+            const pf2 sh = splat2(w3 * dpp);
+            const pf2 dp = add2(pk2(dg[a], dg[a + 1]), sh), dm = add2(pk2(dg[opp(a)], dg[opp(a + 1)]), sh);
+            const pf2 sg = splat2(src_g), og = splat2(om_g);
+            store4(SET_G, a, fma2(sg, add2(G_e, G_o), fma2(sub2(add2(eq_e, eq_o), dp), og, dp)),
+                   fma2(sg, sub2(G_e, G_o), fma2(sub2(sub2(eq_e, eq_o), dm), og, dm)));
         }
     }
 
@@ -601,22 +612,23 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real deq = wgt(0) * phi_lo;
             plane_ptr(pout, SET_F * 9 + 0, K)[cell] = d - (d - deq) * om + src * (wgt(0) * phi * mdot);
         }
+        // lagged phi of the cell that wrote the population pulled into direction i (own cell at a wall)
+        auto php = [&](int i) {
+            const int ys = y - cy(i);
+            return (WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny)) ? phi_p : A.phip(-cy(i), -cx(i));
+        };
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = PAIR[q], j = opp(i);
-            const real w = wgt(i), w3 = R(3.0) * w;
-            const int ysi = y - cy(i), ysj = y - cy(j);
-            const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
-            const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
-            const pf2 php2 = pk2(wall_i ? phi_p : A.phip(-cy(i), -cx(i)), wall_j ? phi_p : A.phip(-cy(j), -cx(j)));
-            const pf2 d2 = fma2(splat2(w), sub2(php2, splat2(phi_st)), pk2(f[i], f[j]));
-            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real eq_e = w * phi_lo, eq_o = w3 * phi * cu;  // f_eq - w phi_st
-            const real F_e = w * phi * mdot, F_o = w3 * ((real)cx(i) * ax + (real)cy(i) * ay);
-            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e)), F2 = fma2(splat2(F_o), SGN, splat2(F_e));
-            const float2 o = up2(fma2(splat2(src), F2, fma2(sub2(eq2, d2), splat2(om), d2)));
-            plane_ptr(pout, SET_F * 9 + i, K)[cell] = o.x;
-            plane_ptr(pout, SET_F * 9 + j, K)[cell] = o.y;
+        for (int q = 0; q < 2; q++) {
+            const int a = q == 0 ? 1 : 5;
+            const real w = wgt(a), w3 = R(3.0) * w;
+            const pf2 ws = splat2(w), ps = splat2(phi_st);
+            const pf2 dp = fma2(ws, sub2(pk2(php(a), php(a + 1)), ps), pk2(f[a], f[a + 1]));
+            const pf2 dm = fma2(ws, sub2(pk2(php(opp(a)), php(opp(a + 1))), ps), pk2(f[opp(a)], f[opp(a + 1)]));
+            const pf2 eq_e = splat2(w * phi_lo), eq_o = mul2(splat2(w3 * phi), cdot2(a, ux, uy));  // f_eq - w phi_st
+            const pf2 F_e = splat2(w * phi * mdot), F_o = mul2(splat2(w3), cdot2(a, ax, ay));
+            const pf2 sf = splat2(src), of = splat2(om);
+            store4(SET_F, a, fma2(sf, add2(F_e, F_o), fma2(sub2(add2(eq_e, eq_o), dp), of, dp)),
+                   fma2(sf, sub2(F_e, F_o), fma2(sub2(sub2(eq_e, eq_o), dm), of, dm)));
         }
 
         // solute set (Sec. 3.4): R = (1-phi) C n/(sqrt2 eps) - (k_p - 1) C grad(1 - f_s)/k_eff
@@ -634,17 +646,14 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
         plane_ptr(pout, SET_L * 9 + 0, K)[cell] = l[0] - (l[0] - wgt(0) * C) * om_l;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = PAIR[q], j = opp(i);
-            const real w = wgt(i), w3 = R(3.0) * w;
-            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real eq_e = w * C, eq_o = w3 * C * cu;
-            const real L_o = w3 * ((real)cx(i) * bx + (real)cy(i) * by);
-            const pf2 l2 = pk2(l[i], l[j]);
-            const pf2 eq2 = fma2(splat2(eq_o), SGN, splat2(eq_e));
-            const float2 o = up2(fma2(splat2(src_l * L_o), SGN, fma2(sub2(eq2, l2), splat2(om_l), l2)));
-            plane_ptr(pout, SET_L * 9 + i, K)[cell] = o.x;
-            plane_ptr(pout, SET_L * 9 + j, K)[cell] = o.y;
+        for (int q = 0; q < 2; q++) {
+            const int a = q == 0 ? 1 : 5;
+            const real w = wgt(a), w3 = R(3.0) * w;
+            const pf2 eq_e = splat2(w * C), eq_o = mul2(splat2(w3 * C), cdot2(a, ux, uy));
+            const pf2 sL = mul2(splat2(src_l * w3), cdot2(a, bx, by));  // src_l L_i, odd
+            const pf2 lp = pk2(l[a], l[a + 1]), lm = pk2(l[opp(a)], l[opp(a + 1)]), ol = splat2(om_l);
+            store4(SET_L, a, add2(fma2(sub2(add2(eq_e, eq_o), lp), ol, lp), sL),
+                   sub2(fma2(sub2(sub2(eq_e, eq_o), lm), ol, lm), sL));
         }
     }
 
@@ -661,28 +670,30 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         const real rcT = rhocp * T;
         real h[9];
         A.template pops<SET_H>(K, B.pin, x, y, cell, h, T_p);
-        real snz = R(0.0);  // sum_{i>0} (h_i - w_i rr T_st)
+        auto Tps = [&](int i) {
+            const int ys = y - cy(i);
+            return (WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny)) ? T_p : A.Tp(-cy(i), -cx(i));
+        };
+        pf2 snz2 = 0;  // sum_{i>0} (h_i - w_i rr T_st), two halves
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int i = PAIR[q], j = opp(i);
-            const real w = wgt(i);
-            const int ysi = y - cy(i), ysj = y - cy(j);
-            const bool wall_i = WALLS && cy(i) != 0 && (ysi < 0 || ysi >= K.ny);
-            const bool wall_j = WALLS && cy(j) != 0 && (ysj < 0 || ysj >= K.ny);
-            const pf2 Tps2 = pk2(wall_i ? T_p : A.Tp(-cy(i), -cx(i)), wall_j ? T_p : A.Tp(-cy(j), -cx(j)));
-            const pf2 dh2 = fma2(splat2(w * rr), sub2(Tps2, splat2(T_st)), pk2(h[i], h[j]));
-            const float2 dh = up2(dh2);
-            const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
-            const real es = w * (rr * T_lo + rcT * (R(4.5) * cu * cu - R(1.5) * uu));
-            const real ea = w * rcT * R(3.0) * cu;
-            const real hs = R(0.5) * (dh.x + dh.y), ha = R(0.5) * (dh.x - dh.y);
-            const real rel_s = (hs - es) * om_s, rel_a = (ha - ea) * om_a, srcq = src_h * w * Q;
-            // (dh_i - rel_a, dh_j + rel_a) - rel_s + srcq
-            const float2 o = up2(add2(dh2, fma2(splat2(rel_a), pk2(R(-1.0), R(1.0)), splat2(srcq - rel_s))));
-            plane_ptr(pout, SET_H * 9 + i, K)[cell] = o.x;
-            plane_ptr(pout, SET_H * 9 + j, K)[cell] = o.y;
-            snz += dh.x + dh.y;
+        for (int q = 0; q < 2; q++) {
+            const int a = q == 0 ? 1 : 5;
+            const real w = wgt(a);
+            const pf2 wr = splat2(w * rr), ts = splat2(T_st);
+            const pf2 dhp = fma2(wr, sub2(pk2(Tps(a), Tps(a + 1)), ts), pk2(h[a], h[a + 1]));
+            const pf2 dhm = fma2(wr, sub2(pk2(Tps(opp(a)), Tps(opp(a + 1))), ts), pk2(h[opp(a)], h[opp(a + 1)]));
+            const pf2 cu = cdot2(a, ux, uy);
+            const pf2 es = fma2(splat2(w * rcT), fma2(splat2(R(4.5)), mul2(cu, cu), u2), splat2(w * rr * T_lo));
+            const pf2 ea = mul2(splat2(w * rcT * R(3.0)), cu);
+            const pf2 half = splat2(R(0.5));
+            const pf2 hs = mul2(half, add2(dhp, dhm)), ha = mul2(half, sub2(dhp, dhm));
+            const pf2 rel_s = mul2(sub2(hs, es), splat2(om_s)), rel_a = mul2(sub2(ha, ea), splat2(om_a));
+            const pf2 base = sub2(splat2(src_h * w * Q), rel_s);
+            store4(SET_H, a, add2(sub2(dhp, rel_a), base), add2(add2(dhm, rel_a), base));
+            snz2 = add2(snz2, add2(dhp, dhm));
         }
+        const float2 snzv = up2(snz2);
+        const real snz = snzv.x + snzv.y;
         // rest population: h_0 - h_eq_0 = -(sum_{i>0} h_i + Q^{n-1}/2) + (1 - w_0) rr T
         // + w_0 rho Cp T 3 u.u/2 exactly (sum_i h_eq_i = rho H); the stored reference
         // moves from w_0 rr T_p + rho_l L (chi_p - fs_p) to w_0 rr T_st + rho_l L (chi_st - f_s)
