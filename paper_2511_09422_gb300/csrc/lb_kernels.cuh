@@ -128,6 +128,12 @@ __device__ __forceinline__ void cp_async4(void *smem, const float *gmem)
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// 16-byte form, cached in L2 only: both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem, const float *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait()
@@ -736,9 +742,9 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 //   lag  lagged (phi, T) pairs                             rows y & 7
 //   dd, cf, md  (dphi, dT), (C, f_s), mdot from phase A     rows y & 3
 //   ps   staged lagged (p, S) pairs                        rows y & 3
-//   pop  staged pulls of f, h, l (stored form)              rows y mod 3
-//   ax   staged own-cell Q, f_s, u_x, u_y, C                rows y mod 3
-//   gp   staged pulls of g                                  rows y & 1
+//   pop  staged pulls of f, h, l (stored form), windows    rows y mod 3
+//   ax   staged own-cell Q, f_s, u_x, u_y, C, windows       rows y mod 3
+//   gp   staged pulls of g, windows                         rows y & 1
 // One launch covers the lattice.  Per group of LB_SW strips it has two bands with
 // the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of K.segh
 // rows inside 2 .. ny-3, whose rows and pull sources (ys - 2 .. ye + 1) all lie
@@ -757,15 +763,20 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
 constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
 
+// Staged planes are windows of WW columns starting at a 16-byte boundary x_lo
+// <= x0 - 2; lane l (column x0 - 1 + l) finds the value pulled into direction i
+// at index l + off - c_ix, off = x0 - 1 - x_lo (in 1 .. 4).
+constexpr int WW = 40;
+
 struct WarpRing {
-    float2 lag[8][34];  // (phi, T) lagged
-    float2 dd[4][32];   // (dphi, dT)
-    float2 cf[4][32];   // (C, f_s)
-    float2 ps[4][32];   // (p, S) lagged, staged
-    float md[4][32];    // mdot
-    float pop[3][27][32];
-    float ax[3][NAX][32];
-    float gp[2][9][32];
+    float2 lag[8][34];    // (phi, T) lagged
+    float2 dd[4][32];     // (dphi, dT)
+    float2 cf[4][32];     // (C, f_s)
+    float2 ps[4][32];     // (p, S) lagged, staged
+    float md[4][32];      // mdot
+    float pop[3][27][WW];  // staged pulls of f (0..8), h (9..17), l (18..26)
+    float ax[3][NAX][WW];  // staged own-cell Q, f_s, u_x, u_y, C
+    float gp[2][9][WW];    // staged pulls of g
 };
 
 constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
@@ -800,7 +811,7 @@ __device__ __forceinline__ double warp_sum(double v)
 // Accessor of phase_b for the strip kernel.
 struct RingAcc {
     const WarpRing &w;
-    int lane;
+    int lane, off;              // off: window offset of the staged planes
     int sl[3], sg[3], sp, sgp;  // loc slots, lag slots (rows y-1, y, y+1), pop / ax slot, gp slot
     // pairs read together (one 64-bit shared load each)
     __device__ float2 lagv(int dy, int dx) const { return w.lag[sg[dy + 1]][lane + 1 + dx]; }
@@ -819,33 +830,34 @@ struct RingAcc {
     template <int S>
     __device__ void pops(const Consts &, const float *__restrict__, int, int, long long, real v[9], real) const
     {
-        constexpr int base = S == SET_F ? 0 : (S == SET_H ? 9 : 18);
+        const float *p = &w.pop[sp][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][lane + off];
 #pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = w.pop[sp][base + i][lane];
+        for (int i = 0; i < 9; i++) v[i] = p[i * WW - cx(i)];
     }
     __device__ void gpops(real v[9]) const
     {
+        const float *p = &w.gp[sgp][0][lane + off];
 #pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = w.gp[sgp][i][lane];
+        for (int i = 0; i < 9; i++) v[i] = p[i * WW - cx(i)];
     }
-    __device__ real aux(int k) const { return w.ax[sp][k][lane]; }
+    __device__ real aux(int k) const { return w.ax[sp][k][lane + off]; }
 };
 
-// Stage the 9 pulls of set S at (x, y) into dst[i * 32] (raw source values;
-// the anti-bounce-back rule is applied when they are read).
+// Stage the 9 pulls of set S at (x, y) one lane at a time into dst[i WW - c_ix]
+// (raw source values; the anti-bounce-back rule is applied when they are read).
 template <int S, bool W>
 __device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
                                        float *dst)
 {
-    cp_async4(dst + 0 * 32, pull_src<S, 0, W>(K, pin, x, y, cell));
-    cp_async4(dst + 1 * 32, pull_src<S, 1, W>(K, pin, x, y, cell));
-    cp_async4(dst + 2 * 32, pull_src<S, 2, W>(K, pin, x, y, cell));
-    cp_async4(dst + 3 * 32, pull_src<S, 3, W>(K, pin, x, y, cell));
-    cp_async4(dst + 4 * 32, pull_src<S, 4, W>(K, pin, x, y, cell));
-    cp_async4(dst + 5 * 32, pull_src<S, 5, W>(K, pin, x, y, cell));
-    cp_async4(dst + 6 * 32, pull_src<S, 6, W>(K, pin, x, y, cell));
-    cp_async4(dst + 7 * 32, pull_src<S, 7, W>(K, pin, x, y, cell));
-    cp_async4(dst + 8 * 32, pull_src<S, 8, W>(K, pin, x, y, cell));
+    cp_async4(dst + 0 * WW - cx(0), pull_src<S, 0, W>(K, pin, x, y, cell));
+    cp_async4(dst + 1 * WW - cx(1), pull_src<S, 1, W>(K, pin, x, y, cell));
+    cp_async4(dst + 2 * WW - cx(2), pull_src<S, 2, W>(K, pin, x, y, cell));
+    cp_async4(dst + 3 * WW - cx(3), pull_src<S, 3, W>(K, pin, x, y, cell));
+    cp_async4(dst + 4 * WW - cx(4), pull_src<S, 4, W>(K, pin, x, y, cell));
+    cp_async4(dst + 5 * WW - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
+    cp_async4(dst + 6 * WW - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
+    cp_async4(dst + 7 * WW - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
+    cp_async4(dst + 8 * WW - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
 }
 
 // Apply the enthalpy wall rule to staged pulls in place (W only).
@@ -853,20 +865,21 @@ template <bool W>
 __device__ __forceinline__ void abb_fix9(const Consts &K, float *v, int x, int y, real T_own)
 {
     if (!W) return;
-    v[1 * 32] = abb_fix<SET_H, 1, W>(K, v[1 * 32], x, y, T_own);
-    v[2 * 32] = abb_fix<SET_H, 2, W>(K, v[2 * 32], x, y, T_own);
-    v[3 * 32] = abb_fix<SET_H, 3, W>(K, v[3 * 32], x, y, T_own);
-    v[4 * 32] = abb_fix<SET_H, 4, W>(K, v[4 * 32], x, y, T_own);
-    v[5 * 32] = abb_fix<SET_H, 5, W>(K, v[5 * 32], x, y, T_own);
-    v[6 * 32] = abb_fix<SET_H, 6, W>(K, v[6 * 32], x, y, T_own);
-    v[7 * 32] = abb_fix<SET_H, 7, W>(K, v[7 * 32], x, y, T_own);
-    v[8 * 32] = abb_fix<SET_H, 8, W>(K, v[8 * 32], x, y, T_own);
+    v[1 * WW - cx(1)] = abb_fix<SET_H, 1, W>(K, v[1 * WW - cx(1)], x, y, T_own);
+    v[2 * WW - cx(2)] = abb_fix<SET_H, 2, W>(K, v[2 * WW - cx(2)], x, y, T_own);
+    v[3 * WW - cx(3)] = abb_fix<SET_H, 3, W>(K, v[3 * WW - cx(3)], x, y, T_own);
+    v[4 * WW - cx(4)] = abb_fix<SET_H, 4, W>(K, v[4 * WW - cx(4)], x, y, T_own);
+    v[5 * WW - cx(5)] = abb_fix<SET_H, 5, W>(K, v[5 * WW - cx(5)], x, y, T_own);
+    v[6 * WW - cx(6)] = abb_fix<SET_H, 6, W>(K, v[6 * WW - cx(6)], x, y, T_own);
+    v[7 * WW - cx(7)] = abb_fix<SET_H, 7, W>(K, v[7 * WW - cx(7)], x, y, T_own);
+    v[8 * WW - cx(8)] = abb_fix<SET_H, 8, W>(K, v[8 * WW - cx(8)], x, y, T_own);
 }
 
+// Sum of the 9 staged pulls of a set, v at the set's first window, lane + off.
 __device__ __forceinline__ real sum9s(const float *v)
 {
-    return v[0] + ((v[1 * 32] + v[2 * 32]) + (v[3 * 32] + v[4 * 32])) +
-           ((v[5 * 32] + v[6 * 32]) + (v[7 * 32] + v[8 * 32]));
+    return v[0] + ((v[1 * WW - 1] + v[2 * WW]) + (v[3 * WW + 1] + v[4 * WW])) +
+           ((v[5 * WW - 1] + v[6 * WW + 1]) + (v[7 * WW + 1] + v[8 * WW - 1]));
 }
 
 // Lagged phi and T of the cell that wrote the population pulled into direction
@@ -916,6 +929,16 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     const float *__restrict__ ain = B.ain;
     const int xa = (((x0 - 2 + lane) % K.nx) + K.nx) % K.nx;
     const int xb = (((x0 + 30 + (lane & 1)) % K.nx) + K.nx) % K.nx;
+    // Staging form.  Inner segments of strips whose window [x_lo, x_lo + WW) lies
+    // inside the lattice row copy whole windows in 16-byte chunks (lanes in groups
+    // of 10, one window per group; lanes 30, 31 idle); the wall bands and the
+    // strips at the x ends copy one value per lane (pull rules, periodic wrap)
+    // into the same layout.
+    const int x_lo = (x0 - 2) & ~3;
+    const bool win = !WALLS && x0 >= 2 && x_lo + WW <= K.nx;
+    const int off = win ? x0 - 1 - x_lo : 4;
+    const int wg = lane / 10, wpart = lane - 10 * wg;
+    const int wcol = x_lo + 4 * wpart;
 
     auto stage_lag = [&](int yl) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
@@ -931,25 +954,56 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     auto stage_a = [&](int y, int s3) {  // s3 = y mod 3
         if (WALLS && (y < 0 || y >= K.ny)) return;
         const int cell = y * K.pitch + xg;
-        float *pp = &w.pop[s3][0][lane];
-        stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
-        stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * 32);
-        stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * 32);
-        float *pa = &w.ax[s3][0][lane];
-        cp_async4(pa + AX_Q * 32, plane_ptr(ain, AUX_Q, K) + cell);
-        cp_async4(pa + AX_FS * 32, plane_ptr(ain, AUX_FS, K) + cell);
+        if (win) {
+            if (wg < 3) {
+                // group wg: set f, h or l; one window per direction, rows y - c_iy
+                const float *src = plane_ptr(pin, wg == 0 ? SET_F * 9 : (wg == 1 ? SET_H * 9 : SET_L * 9), K) + wcol;
+                float *dst = &w.pop[s3][9 * wg][4 * wpart];
+#pragma unroll
+                for (int i = 0; i < 9; i++) cp_async16(dst + i * WW, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
+                // own-cell lagged values: windows Q, f_s, u_x (first copy), u_y, C (second)
+                const int k0 = wg, k1 = wg + 3;
+                const int a0 = k0 == 0 ? AUX_Q : (k0 == 1 ? AUX_FS : AUX_UX);
+                if (PB || k0 < 2) cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
+                if (PB && k1 < NAX)
+                    cp_async16(&w.ax[s3][k1][4 * wpart], plane_ptr(ain, k1 == 3 ? AUX_UY : AUX_C, K) + (y * K.pitch + wcol));
+            }
+        } else {
+            float *pp = &w.pop[s3][0][lane + off];
+            stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
+            stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * WW);
+            stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * WW);
+            float *pa = &w.ax[s3][0][lane + off];
+            cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
+            cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
+            if (PB) {
+                cp_async4(pa + AX_UX * WW, plane_ptr(ain, AUX_UX, K) + cell);
+                cp_async4(pa + AX_UY * WW, plane_ptr(ain, AUX_UY, K) + cell);
+                cp_async4(pa + AX_C * WW, plane_ptr(ain, AUX_C, K) + cell);
+            }
+        }
         if (PB) {
-            cp_async4(pa + AX_UX * 32, plane_ptr(ain, AUX_UX, K) + cell);
-            cp_async4(pa + AX_UY * 32, plane_ptr(ain, AUX_UY, K) + cell);
-            cp_async4(pa + AX_C * 32, plane_ptr(ain, AUX_C, K) + cell);
             cp_async4(&w.ps[y & 3][lane].x, plane_ptr(ain, AUX_P, K) + cell);
             cp_async4(&w.ps[y & 3][lane].y, plane_ptr(ain, AUX_S, K) + cell);
         }
     };
     // pulled g of row y, for its phase B one iteration later
     auto stage_g = [&](int y) {
-        if (!PB || !b_lane || y < ys || y >= ye) return;
-        stage9<SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, &w.gp[y & 1][0][lane]);
+        if (!PB || y < ys || y >= ye) return;
+        if (win) {
+            if (wg < 3) {
+                const float *src = plane_ptr(pin, SET_G * 9, K) + wcol;
+                float *dst = &w.gp[y & 1][0][4 * wpart];
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    const int i = 3 * q + wg;  // direction of this group's window
+                    const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
+                    cp_async16(dst + i * WW, plane_ptr(src, i, K) + (y - cyi) * K.pitch);
+                }
+            }
+        } else if (b_lane) {
+            stage9<SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, &w.gp[y & 1][0][lane + off]);
+        }
     };
 
     const int ya0 = PB ? ys - 1 : ys;
@@ -974,15 +1028,15 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
             const float2 lag0 = w.lag[ya & 7][lane + 1];
             const real phi_p = lag0.x, T_p = lag0.y;
-            float *pp = &w.pop[s3][0][lane];
+            float *pp = &w.pop[s3][0][lane + off];
             real dph, dtt;
             lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
             const real delta = sum9s(pp) + dph;
-            abb_fix9<WALLS>(K, pp + 9 * 32, xg, ya, T_p);  // phase B reads the corrected values
-            const real Q_p = w.ax[s3][AX_Q][lane];
-            const real ed = sum9s(pp + 9 * 32) + K.rr * dtt + R(0.5) * Q_p;
-            const real sl = sum9s(pp + 18 * 32);
-            const real fs_p = w.ax[s3][AX_FS][lane];
+            abb_fix9<WALLS>(K, pp + 9 * WW, xg, ya, T_p);  // phase B reads the corrected values
+            const real Q_p = w.ax[s3][AX_Q][lane + off];
+            const real ed = sum9s(pp + 9 * WW) + K.rr * dtt + R(0.5) * Q_p;
+            const real sl = sum9s(pp + 18 * WW);
+            const real fs_p = w.ax[s3][AX_FS][lane + off];
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
             if (MODE == MODE_REDUCE) {
@@ -1006,7 +1060,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
         if (PB && yb >= ys && yb < ye && b_lane) {
-            const RingAcc A{w, lane, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
+            const RingAcc A{w, lane, off, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
                             s3p, yb & 1};
             phase_b<MODE, WALLS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
