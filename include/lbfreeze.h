@@ -77,7 +77,17 @@ typedef struct {
  * fs_modulated_st: 1 multiplies the surface force by (1 - f_s) (Sec. 4.5).
  * phase_change_on: 0 drops the latent heat and keeps f_s = 0.
  * divu_mode: 0 takes div u = mdot (the model value of Eq. NS1) in the
- * phase-field and enthalpy sources; other values are rejected. */
+ * phase-field and enthalpy sources; other values are rejected.
+ * pop_storage: how the 36 population planes are stored.  LB_STORAGE_F32 (0):
+ * FP32 deviations from lagged references.  LB_STORAGE_F16 (1): the same
+ * deviations times 2^8 in IEEE half precision (the solute set shifted by
+ * w_i c_ref as well), which halves the population bytes; the arithmetic stays
+ * FP32 and the lagged fields stay FP32.  Half storage rounds every stored
+ * population to 11 bits, so its results differ from the FP32 ones (tests state
+ * the difference per field); a deviation beyond 2^8 x 65504 becomes infinite and
+ * is reported as LB_ERR_UNSTABLE. */
+#define LB_STORAGE_F32 0
+#define LB_STORAGE_F16 1
 typedef struct {
     double rho_l, rho_s, rho_g;
     double mu_l, mu_s, mu_g;
@@ -90,6 +100,7 @@ typedef struct {
     double gx, gy;
     int fs_modulated_st, phase_change_on;
     int divu_mode;
+    int pop_storage;
 } lb_params;
 
 /* Initial fields, nx*ny floats each, host or device memory (on_device = 0/1).
@@ -157,7 +168,7 @@ lb_status lb_steps_taken(lb_handle *h, long *out);
 
 /* Checkpoint: write / read the complete state (populations, lagged fields,
  * step count, V_0) of the handle to / from a file.  lb_load requires a file
- * written for the same nx, ny; the result continues bit-for-bit as the saved
+ * written for the same nx, ny and population storage; the result continues bit-for-bit as the saved
  * run would have.  Both synchronise the stream. */
 lb_status lb_save(lb_handle *h, const char *path);
 lb_status lb_load(lb_handle *h, const char *path);
@@ -177,7 +188,8 @@ typedef struct lb_batch lb_batch;
 
 /* Create n >= 1 instances: grids[i], params[i], init[i] as for lb_create (the
  * same checks and errors; a failure names the instance in
- * lb_batch_last_error(NULL)).  Synchronises the device. */
+ * lb_batch_last_error(NULL)).  All instances use the same pop_storage
+ * (LB_ERR_INVALID_ARG otherwise).  Synchronises the device. */
 lb_status lb_batch_create(int n, const lb_grid *grids, const lb_params *params, const lb_fields *init,
                           lb_batch **out);
 

@@ -32,6 +32,8 @@ struct lb_handle {
     unsigned long long *counter = nullptr;  // the step kernel's work counters (2)
     long long nitems = 0;                   // work items of one step
     int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
+    bool half = false;           // populations stored in half precision
+    size_t pop_bytes() const { return (half ? 2 : 4) * 36 * (size_t)K.plane; }
     int cur = 0;
     cudaStream_t stream = nullptr;
     double V0 = 0.0;
@@ -113,6 +115,8 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
     if (!(p->D_l > 0) || p->D_s < 0) return "D_l must be > 0 and D_s >= 0 (tau_l > 1/2 in the liquid)";
     if (!(p->k_p > 0)) return "k_p must be > 0";
     if (p->divu_mode != 0) return "divu_mode must be 0";
+    if (p->pop_storage != LB_STORAGE_F32 && p->pop_storage != LB_STORAGE_F16)
+        return "pop_storage must be LB_STORAGE_F32 or LB_STORAGE_F16";
     if (p->phase_change_on && p->T_liq < p->T_sol) return "T_liq < T_sol";
     return "";
 }
@@ -174,19 +178,28 @@ static unsigned reduce_blocks(const Consts &K)
     return n < cap ? n : cap;
 }
 
-template <int MODE>
-static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials = nullptr)
+template <int MODE, class PS>
+static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials)
 {
     if (lbk::STRIP_SMEM > 48 * 1024) {  // rings above the default dynamic shared-memory limit need the opt-in
-        static bool opted = false;      // per instantiation (one per mode)
+        static bool opted = false;      // per instantiation
         if (!opted) {
-            cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)lbk::STRIP_SMEM);
             opted = true;
         }
     }
     const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks(K) : strip_blocks(K);
-    lbk::lb_strip_kernel<MODE><<<grid, dim3(32, LB_SW, 1), lbk::STRIP_SMEM, st>>>(K, B, partials);
+    lbk::lb_strip_kernel<MODE, PS><<<grid, dim3(32, LB_SW, 1), lbk::STRIP_SMEM, st>>>(K, B, partials);
+}
+
+template <int MODE>
+static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, bool half, double *partials = nullptr)
+{
+    if (half)
+        launch_strip_as<MODE, lbk::PopF16>(K, B, st, partials);
+    else
+        launch_strip_as<MODE, lbk::PopF32>(K, B, st, partials);
 }
 
 static int flat_blocks(long long n, int threads)
@@ -216,20 +229,29 @@ static long long fill_record(const lb_handle *h, lbk::StepRec &r, long long item
 
 // One step of ninst lattices (records rec, nitems work items in all) from buffer
 // `parity`: a persistent launch of at most one wave of resident blocks.
-static cudaError_t launch_step(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
-                               unsigned long long *counter, cudaStream_t st)
+template <class PS>
+static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
+                                  unsigned long long *counter, cudaStream_t st)
 {
     if (lbk::STEP_SMEM > 48 * 1024) {
         static bool opted = false;
         if (!opted) {
-            cudaFuncSetAttribute(lbk::lb_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lbk::STEP_SMEM);
+            cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lbk::STEP_SMEM);
             opted = true;
         }
     }
     const long long wave = 152LL * LB_SMINB, need = (nitems + LB_SW - 1) / LB_SW;
     const unsigned grid = (unsigned)(need < wave ? (need < 1 ? 1 : need) : wave);
-    lbk::lb_step_kernel<<<grid, dim3(32, LB_SW, 1), lbk::STEP_SMEM, st>>>(rec, ninst, nitems, parity, counter);
+    lbk::lb_step_kernel<PS><<<grid, dim3(32, LB_SW, 1), lbk::STEP_SMEM, st>>>(rec, ninst, nitems, parity, counter);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_step(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
+                               unsigned long long *counter, cudaStream_t st, bool half)
+{
+    return half ? launch_step_as<lbk::PopF16>(rec, ninst, nitems, parity, counter, st)
+                : launch_step_as<lbk::PopF32>(rec, ninst, nitems, parity, counter, st);
 }
 
 static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
@@ -242,7 +264,7 @@ static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
     B.aout = nullptr;
     B.fields = nullptr;
     B.status = h->status;
-    launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->partials);
+    launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->half, h->partials);
     CK(h, cudaGetLastError());
     lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_parts, h->red_out);
     CK(h, cudaGetLastError());
@@ -269,6 +291,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     lb_handle *h = new lb_handle();
     h->grid = *grid;
     h->params = *params;
+    h->half = params->pop_storage == LB_STORAGE_F16;
     h->K = make_consts(grid, params);
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
@@ -281,7 +304,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
         return e;
     };
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->pops[k], 36 * plane_b);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->pops[k], h->pop_bytes());
     for (int k = 0; k < 2 && e == cudaSuccess; k++) e = alloc((void **)&h->aux[k], lbk::NAUX * plane_b);
     if (e == cudaSuccess) e = alloc((void **)&h->fields, 7 * plane_b);
     if (e == cudaSuccess) e = alloc((void **)&h->partials, sizeof(double) * lbk::NRED * h->red_parts);
@@ -317,11 +340,28 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
             dev[k] = d;
         }
         if (st != LB_OK) break;
-        float *eq = h->pops[1];
+        // equilibria in FP32: in the second population buffer, or for half storage
+        // in a temporary buffer freed once the first buffer holds the state
+        float *eq = h->pops[1], *eq_tmp = nullptr;
+        if (h->half) {
+            cudaError_t ae = cudaMalloc((void **)&eq_tmp, 36 * plane_b);
+            if (ae != cudaSuccess) { st = cuda_fail(h, ae, "cudaMalloc of the initial equilibria"); break; }
+            eq = eq_tmp;
+        }
         lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4], eq,
                                                                            h->aux[0]);
-        lbk::lb_init_unstream_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0], h->pops[0]);
+        if (h->half)
+            lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
+                                                                                                 h->pops[0]);
+        else
+            lbk::lb_init_unstream_kernel<lbk::PopF32><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
+                                                                                                 h->pops[0]);
         cudaError_t ce = cudaGetLastError();
+        if (eq_tmp) {
+            cudaError_t fe = cudaStreamSynchronize(h->stream);
+            cudaFree(eq_tmp);
+            if (ce == cudaSuccess) ce = fe;
+        }
         if (ce != cudaSuccess) { st = cuda_fail(h, ce, "init kernels"); break; }
         h->cur = 0;
         double r[lbk::NRED];
@@ -351,7 +391,7 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
     if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
     if (h->sticky != LB_OK) return h->sticky;
     for (int s = 0; s < n; s++) {
-        cudaError_t e = launch_step(h->rec, 1, h->nitems, h->cur, h->counter, h->stream);
+        cudaError_t e = launch_step(h->rec, 1, h->nitems, h->cur, h->counter, h->stream, h->half);
         if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
         h->cur = 1 - h->cur;
         h->steps++;
@@ -379,7 +419,7 @@ extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs
     B.aout = nullptr;
     B.fields = h->fields;
     B.status = h->status;
-    launch_strip<lbk::MODE_FIELDS>(K, B, h->stream);
+    launch_strip<lbk::MODE_FIELDS>(K, B, h->stream, h->half);
     CK(h, cudaGetLastError());
     float *dst[7] = {phi, T, fs, C, ux, uy, p};
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -426,11 +466,11 @@ extern "C" lb_status lb_save(lb_handle *h, const char *path)
     if (!h || !path) return fail(h, LB_ERR_INVALID_ARG, "null argument");
     if (h->sticky != LB_OK) return h->sticky;
     const Consts &K = h->K;
-    const size_t np = 36 * (size_t)K.plane, na = lbk::NAUX * (size_t)K.plane;
-    float *buf = (float *)malloc(sizeof(float) * (np + na));
+    const size_t pb = h->pop_bytes(), ab = sizeof(float) * lbk::NAUX * (size_t)K.plane;
+    char *buf = (char *)malloc(pb + ab);
     if (!buf) return fail(h, LB_ERR_INVALID_ARG, "host allocation for the checkpoint failed");
-    cudaError_t e = cudaMemcpyAsync(buf, h->pops[h->cur], sizeof(float) * np, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + np, h->aux[h->cur], sizeof(float) * na, cudaMemcpyDeviceToHost, h->stream);
+    cudaError_t e = cudaMemcpyAsync(buf, h->pops[h->cur], pb, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + pb, h->aux[h->cur], ab, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         free(buf);
@@ -444,8 +484,9 @@ extern "C" lb_status lb_save(lb_handle *h, const char *path)
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "LBFRZ01", 8);
-    hd.version = 1; hd.nx = K.nx; hd.ny = K.ny; hd.pitch = K.pitch; hd.steps = h->steps; hd.V0 = h->V0;
-    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf, sizeof(float), np + na, f) == np + na;
+    hd.version = h->half ? 2 : 1;  // 2: half-precision populations
+    hd.nx = K.nx; hd.ny = K.ny; hd.pitch = K.pitch; hd.steps = h->steps; hd.V0 = h->V0;
+    bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf, 1, pb + ab, f) == pb + ab;
     ok = (fclose(f) == 0) && ok;
     free(buf);
     return ok ? LB_OK : fail(h, LB_ERR_INVALID_ARG, std::string("write failed: ") + path);
@@ -460,24 +501,24 @@ extern "C" lb_status lb_load(lb_handle *h, const char *path)
     if (!f) return fail(h, LB_ERR_INVALID_ARG, std::string("cannot open ") + path);
     CkptHeader hd;
     if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBFRZ01", 8) != 0 || hd.nx != K.nx || hd.ny != K.ny ||
-        hd.pitch != K.pitch) {
+        hd.pitch != K.pitch || hd.version != (h->half ? 2 : 1)) {
         fclose(f);
         return fail(h, LB_ERR_INVALID_ARG, "checkpoint does not match this lattice");
     }
-    const size_t np = 36 * (size_t)K.plane, na = lbk::NAUX * (size_t)K.plane;
-    float *buf = (float *)malloc(sizeof(float) * (np + na));
+    const size_t pb = h->pop_bytes(), ab = sizeof(float) * lbk::NAUX * (size_t)K.plane;
+    char *buf = (char *)malloc(pb + ab);
     if (!buf) {
         fclose(f);
         return fail(h, LB_ERR_INVALID_ARG, "host allocation for the checkpoint failed");
     }
-    bool ok = fread(buf, sizeof(float), np + na, f) == np + na;
+    bool ok = fread(buf, 1, pb + ab, f) == pb + ab;
     fclose(f);
     if (!ok) {
         free(buf);
         return fail(h, LB_ERR_INVALID_ARG, "truncated checkpoint");
     }
-    cudaError_t e = cudaMemcpyAsync(h->pops[h->cur], buf, sizeof(float) * np, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h->aux[h->cur], buf + np, sizeof(float) * na, cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = cudaMemcpyAsync(h->pops[h->cur], buf, pb, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->aux[h->cur], buf + pb, ab, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     free(buf);
     if (e != cudaSuccess) return cuda_fail(h, e, "checkpoint upload");
@@ -519,6 +560,7 @@ static std::mutex g_noalloc_mu;
 
 namespace {
 
+template <class PS>
 __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Consts K, const float *__restrict__ pin,
                                                                          const float *__restrict__ ain,
                                                                          double *__restrict__ scratch)
@@ -529,7 +571,8 @@ __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Co
     double acc[lbk::NRED] = {0, 0, 0, 0, 0, 0};
     for (int x = threadIdx.x; x < K.nx; x += blockDim.x) {
         const int cell = y * K.pitch + x;
-        const lbk::CellA c = lbk::cell_a(K, pin, ain, x, y, cell);
+        const lbk::CellA c =
+            lbk::cell_a<PS>(K, reinterpret_cast<const typename PS::T *>(pin), ain, x, y, cell);
         const double phid = (double)c.phi_p + (double)c.L.dphi;
         acc[0] += phid;
         acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
@@ -591,7 +634,12 @@ extern "C" lb_status lb_reduce_noalloc(lb_handle *h, double out[8])
         }
         scratch = g_noalloc_addr[dev];
     }
-    noalloc_rows_kernel<<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur], scratch);
+    if (h->half)
+        noalloc_rows_kernel<lbk::PopF16><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
+                                                                                  scratch);
+    else
+        noalloc_rows_kernel<lbk::PopF32><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
+                                                                                  scratch);
     CK(h, cudaGetLastError());
     noalloc_total_kernel<<<1, 32, 0, h->stream>>>(scratch, K.ny);
     CK(h, cudaGetLastError());
@@ -674,7 +722,7 @@ static lb_status upload_instances(lb_batch *b)
 // One batched step from buffer `parity` on stream st.
 static lb_status launch_batch(lb_batch *b, int parity, cudaStream_t st)
 {
-    BCK(b, launch_step(b->d_inst, (int)b->h.size(), b->nitems, parity, b->d_counter, st));
+    BCK(b, launch_step(b->d_inst, (int)b->h.size(), b->nitems, parity, b->d_counter, st, b->h[0]->half));
     return LB_OK;
 }
 
@@ -692,6 +740,11 @@ extern "C" lb_status lb_batch_create(int n, const lb_grid *grids, const lb_param
             return bfail(nullptr, s, why);
         }
         b->h.push_back(h);
+        if (h->half != b->h[0]->half) {
+            lb_batch_destroy(b);
+            return bfail(nullptr, LB_ERR_INVALID_ARG, "instance " + std::to_string(i) +
+                                                          ": all instances must use the same pop_storage");
+        }
     }
     b->inst.resize(n);
     lb_status s = LB_OK;

@@ -41,6 +41,7 @@
 // halo costs 2 rows per segment and two columns per 30, and the warps of a
 // CTA never synchronise with one another (only __syncwarp).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -61,6 +62,24 @@ __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i
 __host__ __device__ constexpr real wgt(int i) { return i == 0 ? (R(4.0) / R(9.0)) : (i <= 4 ? (R(1.0) / R(9.0)) : (R(1.0) / R(36.0))); }
 
 constexpr int SET_F = 0, SET_G = 1, SET_H = 2, SET_L = 3;
+
+// Storage of the 36 population planes.  PopF32: FP32 deviations (see the top of
+// this file).  PopF16: the same deviations times 2^8 in IEEE half precision, the
+// solute set additionally shifted by w_i c_ref, halving the population bytes; the
+// arithmetic stays FP32.  A deviation beyond 2^8 * 65504 overflows to infinity,
+// which the step reports as non-finite.
+struct PopF32 {
+    typedef float T;
+    static constexpr bool kHalf = false;
+    __device__ static real dec(T v) { return v; }
+    __device__ static T enc(real d) { return d; }
+};
+struct PopF16 {
+    typedef __half T;
+    static constexpr bool kHalf = true;
+    __device__ static real dec(T v) { return __half2float(v) * R(1.0 / 256.0); }
+    __device__ static T enc(real d) { return __float2half_rn(d * R(256.0)); }
+};
 constexpr int AUX_FS = 0, AUX_Q = 1, AUX_UX = 2, AUX_UY = 3, AUX_PHI = 4, AUX_C = 5, AUX_P = 6, AUX_S = 7, AUX_T = 8;
 constexpr int NAUX = 9;
 constexpr int WALL_DIRICHLET = 0;
@@ -123,13 +142,13 @@ __device__ __forceinline__ double rcp(double v) { return 1.0 / v; }
 // Asynchronous 4-byte global -> shared copies (sm_80+ cp.async, cached in L1):
 // the strip sweep stages the next row's inputs with them, so their latency
 // overlaps the current row's arithmetic without holding registers.
-__device__ __forceinline__ void cp_async4(void *smem, const float *gmem)
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 // 16-byte form, cached in L2 only: both addresses 16-byte aligned.
-__device__ __forceinline__ void cp_async16(void *smem, const float *gmem)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -251,8 +270,8 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (wall temperature at the
 // link midpoint) is applied in deviation form relative to w rr T_own.
 // pull_src gives the address read, abb_fix the wall rule applied to its value.
-template <int S, int I, bool W>
-__device__ __forceinline__ const float *pull_src(const Consts &K, const float *__restrict__ pin, int x, int y, int cell)
+template <int S, int I, bool W, class T>
+__device__ __forceinline__ const T *pull_src(const Consts &K, const T *__restrict__ pin, int x, int y, int cell)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
@@ -275,27 +294,48 @@ __device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, r
     return v;
 }
 
-template <int S, int I, bool W>
-__device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
+// Decoded stored value of set S, direction I: the deviation, and for the solute
+// set in half storage the w_I c_ref shift added back.
+template <class PS>
+__device__ __forceinline__ real dec_pop(const Consts &K, int s, int i, typename PS::T v)
+{
+    return (PS::kHalf && s == SET_L) ? PS::dec(v) + wgt(i) * K.c_ref : PS::dec(v);
+}
+
+template <class PS>
+__device__ __forceinline__ typename PS::T enc_pop(const Consts &K, int s, int i, real v)
+{
+    return PS::enc((PS::kHalf && s == SET_L) ? v - wgt(i) * K.c_ref : v);
+}
+
+// Store population (set s, direction i) of cell into the output planes.
+template <class PS>
+__device__ __forceinline__ void put_pop(const Consts &K, float *pout, int s, int i, int cell, real v)
+{
+    plane_ptr(reinterpret_cast<typename PS::T *>(pout), s * 9 + i, K)[cell] = enc_pop<PS>(K, s, i, v);
+}
+
+template <class PS, int S, int I, bool W>
+__device__ __forceinline__ real pull(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
                                      real T_own)
 {
-    return abb_fix<S, I, W>(K, __ldg(pull_src<S, I, W>(K, pin, x, y, cell)), x, y, T_own);
+    return abb_fix<S, I, W>(K, dec_pop<PS>(K, S, I, __ldg(pull_src<S, I, W>(K, pin, x, y, cell))), x, y, T_own);
 }
 
 // W = false: the caller guarantees that no source row lies beyond a wall.
-template <int S, bool W = true>
-__device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell, real v[9],
-                                      real T_own = R(0.0))
+template <class PS, int S, bool W = true>
+__device__ __forceinline__ void pull9(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
+                                      real v[9], real T_own = R(0.0))
 {
-    v[0] = pull<S, 0, W>(K, pin, x, y, cell, T_own);
-    v[1] = pull<S, 1, W>(K, pin, x, y, cell, T_own);
-    v[2] = pull<S, 2, W>(K, pin, x, y, cell, T_own);
-    v[3] = pull<S, 3, W>(K, pin, x, y, cell, T_own);
-    v[4] = pull<S, 4, W>(K, pin, x, y, cell, T_own);
-    v[5] = pull<S, 5, W>(K, pin, x, y, cell, T_own);
-    v[6] = pull<S, 6, W>(K, pin, x, y, cell, T_own);
-    v[7] = pull<S, 7, W>(K, pin, x, y, cell, T_own);
-    v[8] = pull<S, 8, W>(K, pin, x, y, cell, T_own);
+    v[0] = pull<PS, S, 0, W>(K, pin, x, y, cell, T_own);
+    v[1] = pull<PS, S, 1, W>(K, pin, x, y, cell, T_own);
+    v[2] = pull<PS, S, 2, W>(K, pin, x, y, cell, T_own);
+    v[3] = pull<PS, S, 3, W>(K, pin, x, y, cell, T_own);
+    v[4] = pull<PS, S, 4, W>(K, pin, x, y, cell, T_own);
+    v[5] = pull<PS, S, 5, W>(K, pin, x, y, cell, T_own);
+    v[6] = pull<PS, S, 6, W>(K, pin, x, y, cell, T_own);
+    v[7] = pull<PS, S, 7, W>(K, pin, x, y, cell, T_own);
+    v[8] = pull<PS, S, 8, W>(K, pin, x, y, cell, T_own);
 }
 
 // Lagged field (plane A) of the cell that wrote the population pulled into
@@ -358,9 +398,9 @@ struct CellA {
     real ed, chi_p, fs_p, phi_p, T_p;
 };
 
-template <bool W = true>
-__device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict__ pin, const float *__restrict__ ain,
-                                        int x, int y, int cell)
+template <class PS, bool W = true>
+__device__ __forceinline__ CellA cell_a(const Consts &K, const typename PS::T *__restrict__ pin,
+                                        const float *__restrict__ ain, int x, int y, int cell)
 {
     CellA c;
     real v[9];
@@ -368,12 +408,12 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     c.T_p = __ldg(plane_ptr(ain, AUX_T, K) + cell);
     c.fs_p = __ldg(plane_ptr(ain, AUX_FS, K) + cell);
     c.chi_p = clamp01(R(0.5) * (R(1.0) + c.phi_p));
-    pull9<SET_F, W>(K, pin, x, y, cell, v);
+    pull9<PS, SET_F, W>(K, pin, x, y, cell, v);
     const real delta = sum9(v) + aux_dev_sum<AUX_PHI, W>(K, ain, x, y, cell, c.phi_p);
-    pull9<SET_H, W>(K, pin, x, y, cell, v, c.T_p);
+    pull9<PS, SET_H, W>(K, pin, x, y, cell, v, c.T_p);
     const real Q_p = __ldg(plane_ptr(ain, AUX_Q, K) + cell);
     c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T, W>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
-    pull9<SET_L, W>(K, pin, x, y, cell, v);
+    pull9<PS, SET_L, W>(K, pin, x, y, cell, v);
     const real sl = sum9(v);
     c.L = local_fields(K, c.phi_p, delta, c.ed, c.T_p, c.chi_p, c.fs_p, sl);
     return c;
@@ -393,7 +433,7 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1, MODE_REDUCE = 2 };
 // (offsets dy, dx in {-1, 0, 1}, already mirrored at walls) and the cell's
 // pulled f, h, l and g, and its own lagged Q, f_s, u and C.
 // ---------------------------------------------------------------------------------------
-template <int MODE, bool WALLS, class Acc>
+template <int MODE, bool WALLS, class PS, class Acc>
 __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const Acc &A, int x, int y, int cell)
 {
     const real rr = K.rr;
@@ -510,7 +550,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // lagged pressure, so that the momentum and the pressure are sums of small terms
     const real p_p = A.p(0, 0);
     real g[9], dg[9];
-    A.gpops(g);
+    A.gpops(K, g);
     real jx = R(0.0), jy = R(0.0), sg = R(0.0);
 #pragma unroll
     for (int i = 0; i < 9; i++) {
@@ -561,10 +601,10 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     float *__restrict__ pout = B.pout;
     auto store4 = [&](int set, int a, const pf2 vp, const pf2 vm) {
         const float2 op = up2(vp), om2 = up2(vm);
-        plane_ptr(pout, set * 9 + a, K)[cell] = op.x;
-        plane_ptr(pout, set * 9 + a + 1, K)[cell] = op.y;
-        plane_ptr(pout, set * 9 + opp(a), K)[cell] = om2.x;
-        plane_ptr(pout, set * 9 + opp(a + 1), K)[cell] = om2.y;
+        put_pop<PS>(K, pout, set, a, cell, op.x);
+        put_pop<PS>(K, pout, set, a + 1, cell, op.y);
+        put_pop<PS>(K, pout, set, opp(a), cell, om2.x);
+        put_pop<PS>(K, pout, set, opp(a + 1), cell, om2.y);
     };
     // (c_a . v, c_{a+1} . v)
     auto cdot2 = [](int a, real vx, real vy) {
@@ -583,7 +623,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real d = dg[0] + wp * dpp;
             const real deq = wp * p_lo + rho * (wgt(0) * (-R(1.5) * uu));
             const real G0 = wgt(0) * (S - R(3.0) * uF);
-            plane_ptr(pout, SET_G * 9 + 0, K)[cell] = d - (d - deq) * om_g + src_g * G0;
+            put_pop<PS>(K, pout, SET_G, 0, cell, d - (d - deq) * om_g + src_g * G0);
         }
 #pragma unroll
         for (int q = 0; q < 2; q++) {
@@ -616,7 +656,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         {
             const real d = f[0] + wgt(0) * (phi_p - phi_st);
             const real deq = wgt(0) * phi_lo;
-            plane_ptr(pout, SET_F * 9 + 0, K)[cell] = d - (d - deq) * om + src * (wgt(0) * phi * mdot);
+            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wgt(0) * phi * mdot));
         }
         // lagged phi of the cell that wrote the population pulled into direction i (own cell at a wall)
         auto php = [&](int i) {
@@ -650,7 +690,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
         real l[9];
         A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
-        plane_ptr(pout, SET_L * 9 + 0, K)[cell] = l[0] - (l[0] - wgt(0) * C) * om_l;
+        put_pop<PS>(K, pout, SET_L, 0, cell, l[0] - (l[0] - wgt(0) * C) * om_l);
 #pragma unroll
         for (int q = 0; q < 2; q++) {
             const int a = q == 0 ? 1 : 5;
@@ -711,7 +751,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
             const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
             const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
-            plane_ptr(pout, SET_H * 9 + 0, K)[cell] = h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q;
+            put_pop<PS>(K, pout, SET_H, 0, cell, h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q);
         }
     }
 
@@ -808,7 +848,41 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Elements of a staged window slot (160 bytes) in the storage type T.
+template <class T>
+__host__ __device__ constexpr int win_elems()
+{
+    return WW * (int)(sizeof(float) / sizeof(T));
+}
+
+// Decoded staged pulls of set S for the lane whose window index is idx.
+template <class PS, int S>
+__device__ __forceinline__ void load9(const Consts &K, const WarpRing &w, int slot, int idx, real v[9])
+{
+    typedef typename PS::T T;
+    constexpr int E = win_elems<T>();
+    const T *p = reinterpret_cast<const T *>(&w.pop[slot][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][0]) + idx;
+#pragma unroll
+    for (int i = 0; i < 9; i++) v[i] = dec_pop<PS>(K, S, i, p[i * E - cx(i)]);
+}
+
+// The enthalpy wall rule on decoded pulls (W only).
+template <bool W>
+__device__ __forceinline__ void abb_fix9(const Consts &K, real v[9], int x, int y, real T_own)
+{
+    if (!W) return;
+    v[1] = abb_fix<SET_H, 1, W>(K, v[1], x, y, T_own);
+    v[2] = abb_fix<SET_H, 2, W>(K, v[2], x, y, T_own);
+    v[3] = abb_fix<SET_H, 3, W>(K, v[3], x, y, T_own);
+    v[4] = abb_fix<SET_H, 4, W>(K, v[4], x, y, T_own);
+    v[5] = abb_fix<SET_H, 5, W>(K, v[5], x, y, T_own);
+    v[6] = abb_fix<SET_H, 6, W>(K, v[6], x, y, T_own);
+    v[7] = abb_fix<SET_H, 7, W>(K, v[7], x, y, T_own);
+    v[8] = abb_fix<SET_H, 8, W>(K, v[8], x, y, T_own);
+}
+
 // Accessor of phase_b for the strip kernel.
+template <class PS, bool W>
 struct RingAcc {
     const WarpRing &w;
     int lane, off;              // off: window offset of the staged planes
@@ -827,59 +901,53 @@ struct RingAcc {
     __device__ real p(int dy, int dx) const { return psv(dy, dx).x; }
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
+    // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
-    __device__ void pops(const Consts &, const float *__restrict__, int, int, long long, real v[9], real) const
+    __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
     {
-        const float *p = &w.pop[sp][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][lane + off];
-#pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = p[i * WW - cx(i)];
+        load9<PS, S>(K, w, sp, lane + off, v);
+        if (S == SET_H) abb_fix9<W>(K, v, x, y, T_own);
     }
-    __device__ void gpops(real v[9]) const
+    __device__ void gpops(const Consts &K, real v[9]) const
     {
-        const float *p = &w.gp[sgp][0][lane + off];
+        typedef typename PS::T T;
+        constexpr int E = win_elems<T>();
+        const T *p = reinterpret_cast<const T *>(&w.gp[sgp][0][0]) + lane + off;
 #pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = p[i * WW - cx(i)];
+        for (int i = 0; i < 9; i++) v[i] = PS::dec(p[i * E - cx(i)]);
     }
     __device__ real aux(int k) const { return w.ax[sp][k][lane + off]; }
 };
 
-// Stage the 9 pulls of set S at (x, y) one lane at a time into dst[i WW - c_ix]
-// (raw source values; the anti-bounce-back rule is applied when they are read).
-template <int S, bool W>
-__device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
-                                       float *dst)
+// Stage the 9 pulls of set S at (x, y) one lane at a time into dst[i E - c_ix]
+// (E the window slot size; raw stored values, decoded and given the wall rule
+// when read).  FP32 values go by cp.async; half values are loaded and stored.
+template <class PS, int S, bool W>
+__device__ __forceinline__ void stage9(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
+                                       typename PS::T *dst)
 {
-    cp_async4(dst + 0 * WW - cx(0), pull_src<S, 0, W>(K, pin, x, y, cell));
-    cp_async4(dst + 1 * WW - cx(1), pull_src<S, 1, W>(K, pin, x, y, cell));
-    cp_async4(dst + 2 * WW - cx(2), pull_src<S, 2, W>(K, pin, x, y, cell));
-    cp_async4(dst + 3 * WW - cx(3), pull_src<S, 3, W>(K, pin, x, y, cell));
-    cp_async4(dst + 4 * WW - cx(4), pull_src<S, 4, W>(K, pin, x, y, cell));
-    cp_async4(dst + 5 * WW - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
-    cp_async4(dst + 6 * WW - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
-    cp_async4(dst + 7 * WW - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
-    cp_async4(dst + 8 * WW - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
-}
-
-// Apply the enthalpy wall rule to staged pulls in place (W only).
-template <bool W>
-__device__ __forceinline__ void abb_fix9(const Consts &K, float *v, int x, int y, real T_own)
-{
-    if (!W) return;
-    v[1 * WW - cx(1)] = abb_fix<SET_H, 1, W>(K, v[1 * WW - cx(1)], x, y, T_own);
-    v[2 * WW - cx(2)] = abb_fix<SET_H, 2, W>(K, v[2 * WW - cx(2)], x, y, T_own);
-    v[3 * WW - cx(3)] = abb_fix<SET_H, 3, W>(K, v[3 * WW - cx(3)], x, y, T_own);
-    v[4 * WW - cx(4)] = abb_fix<SET_H, 4, W>(K, v[4 * WW - cx(4)], x, y, T_own);
-    v[5 * WW - cx(5)] = abb_fix<SET_H, 5, W>(K, v[5 * WW - cx(5)], x, y, T_own);
-    v[6 * WW - cx(6)] = abb_fix<SET_H, 6, W>(K, v[6 * WW - cx(6)], x, y, T_own);
-    v[7 * WW - cx(7)] = abb_fix<SET_H, 7, W>(K, v[7 * WW - cx(7)], x, y, T_own);
-    v[8 * WW - cx(8)] = abb_fix<SET_H, 8, W>(K, v[8 * WW - cx(8)], x, y, T_own);
-}
-
-// Sum of the 9 staged pulls of a set, v at the set's first window, lane + off.
-__device__ __forceinline__ real sum9s(const float *v)
-{
-    return v[0] + ((v[1 * WW - 1] + v[2 * WW]) + (v[3 * WW + 1] + v[4 * WW])) +
-           ((v[5 * WW - 1] + v[6 * WW + 1]) + (v[7 * WW + 1] + v[8 * WW - 1]));
+    constexpr int E = win_elems<typename PS::T>();
+    if constexpr (!PS::kHalf) {
+        cp_async4(dst + 0 * E - cx(0), pull_src<S, 0, W>(K, pin, x, y, cell));
+        cp_async4(dst + 1 * E - cx(1), pull_src<S, 1, W>(K, pin, x, y, cell));
+        cp_async4(dst + 2 * E - cx(2), pull_src<S, 2, W>(K, pin, x, y, cell));
+        cp_async4(dst + 3 * E - cx(3), pull_src<S, 3, W>(K, pin, x, y, cell));
+        cp_async4(dst + 4 * E - cx(4), pull_src<S, 4, W>(K, pin, x, y, cell));
+        cp_async4(dst + 5 * E - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
+        cp_async4(dst + 6 * E - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
+        cp_async4(dst + 7 * E - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
+        cp_async4(dst + 8 * E - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
+    } else {
+        dst[0 * E - cx(0)] = __ldg(pull_src<S, 0, W>(K, pin, x, y, cell));
+        dst[1 * E - cx(1)] = __ldg(pull_src<S, 1, W>(K, pin, x, y, cell));
+        dst[2 * E - cx(2)] = __ldg(pull_src<S, 2, W>(K, pin, x, y, cell));
+        dst[3 * E - cx(3)] = __ldg(pull_src<S, 3, W>(K, pin, x, y, cell));
+        dst[4 * E - cx(4)] = __ldg(pull_src<S, 4, W>(K, pin, x, y, cell));
+        dst[5 * E - cx(5)] = __ldg(pull_src<S, 5, W>(K, pin, x, y, cell));
+        dst[6 * E - cx(6)] = __ldg(pull_src<S, 6, W>(K, pin, x, y, cell));
+        dst[7 * E - cx(7)] = __ldg(pull_src<S, 7, W>(K, pin, x, y, cell));
+        dst[8 * E - cx(8)] = __ldg(pull_src<S, 8, W>(K, pin, x, y, cell));
+    }
 }
 
 // Lagged phi and T of the cell that wrote the population pulled into direction
@@ -917,28 +985,33 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w,
 
 // Phase A / phase B sweep of one warp over rows [ys, ye) of its strip.  WALLS =
 // false: every row ys - 2 .. ye + 1 lies inside the lattice.
-template <int MODE, bool WALLS>
+template <int MODE, bool WALLS, class PS>
 __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing &w, int lane, int x0, int ys, int ye,
                                            double acc[NRED])
 {
+    typedef typename PS::T T;
     constexpr bool PB = MODE != MODE_REDUCE;  // phase B follows phase A
+    constexpr int E = win_elems<T>();         // window slot size in T
+    constexpr int CH = 16 / (int)sizeof(T);   // elements of a 16-byte chunk
+    constexpr int PLEN = PS::kHalf ? 48 : 40; // staged columns of a population window
     const int ex = x0 - 1 + lane;
     const int xg = ((ex % K.nx) + K.nx) % K.nx;
     const bool b_lane = lane >= 1 && lane <= LB_TX && ex < K.nx;
-    const float *__restrict__ pin = B.pin;
+    const T *__restrict__ pin = reinterpret_cast<const T *>(B.pin);
     const float *__restrict__ ain = B.ain;
     const int xa = (((x0 - 2 + lane) % K.nx) + K.nx) % K.nx;
     const int xb = (((x0 + 30 + (lane & 1)) % K.nx) + K.nx) % K.nx;
-    // Staging form.  Inner segments of strips whose window [x_lo, x_lo + WW) lies
-    // inside the lattice row copy whole windows in 16-byte chunks (lanes in groups
-    // of 10, one window per group; lanes 30, 31 idle); the wall bands and the
-    // strips at the x ends copy one value per lane (pull rules, periodic wrap)
-    // into the same layout.
-    const int x_lo = (x0 - 2) & ~3;
-    const bool win = !WALLS && x0 >= 2 && x_lo + WW <= K.nx;
+    // Staging form.  Inner segments of strips whose windows (from the 16-byte
+    // boundary x_lo <= x0 - 2) lie inside the lattice row copy whole windows in
+    // 16-byte chunks, a group of lanes per window; the wall bands and the strips
+    // at the x ends copy one value per lane (pull rules, periodic wrap) into the
+    // same layout.
+    const int x_lo = (x0 - 2) & ~(CH - 1);
+    const bool win = !WALLS && x0 >= 2 && x_lo + PLEN <= K.nx && x_lo + WW <= K.nx;
     const int off = win ? x0 - 1 - x_lo : 4;
-    const int wg = lane / 10, wpart = lane - 10 * wg;
+    const int wg = lane / 10, wpart = lane - 10 * wg;  // float windows: 10 chunks, 3 windows per copy
     const int wcol = x_lo + 4 * wpart;
+    const int hg = lane / 6, hpart = lane - 6 * hg;    // half windows: 6 chunks, 5 windows per copy
 
     auto stage_lag = [&](int yl) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
@@ -950,29 +1023,50 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             cp_async4(&w.lag[yl & 7][32 + lane].y, plane_ptr(ain, AUX_T, K) + (ro + xb));
         }
     };
+    // own-cell lagged values of row y as float windows: Q, f_s, u_x (first copy), u_y, C (second)
+    auto stage_ax_win = [&](int y, int s3) {
+        if (wg < 3) {
+            const int k0 = wg, k1 = wg + 3;
+            const int a0 = k0 == 0 ? AUX_Q : (k0 == 1 ? AUX_FS : AUX_UX);
+            if (PB || k0 < 2) cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
+            if (PB && k1 < NAX)
+                cp_async16(&w.ax[s3][k1][4 * wpart], plane_ptr(ain, k1 == 3 ? AUX_UY : AUX_C, K) + (y * K.pitch + wcol));
+        }
+    };
     // phase-A inputs of row y, and the own-cell lagged values phase B needs
     auto stage_a = [&](int y, int s3) {  // s3 = y mod 3
         if (WALLS && (y < 0 || y >= K.ny)) return;
         const int cell = y * K.pitch + xg;
+        T *pw = reinterpret_cast<T *>(&w.pop[s3][0][0]);  // window 0 of the slot
         if (win) {
-            if (wg < 3) {
-                // group wg: set f, h or l; one window per direction, rows y - c_iy
-                const float *src = plane_ptr(pin, wg == 0 ? SET_F * 9 : (wg == 1 ? SET_H * 9 : SET_L * 9), K) + wcol;
-                float *dst = &w.pop[s3][9 * wg][4 * wpart];
+            if constexpr (!PS::kHalf) {
+                if (wg < 3) {
+                    // group wg: set f, h or l; one window per direction, rows y - c_iy
+                    const T *src = plane_ptr(pin, wg == 0 ? SET_F * 9 : (wg == 1 ? SET_H * 9 : SET_L * 9), K) + wcol;
+                    T *dst = pw + 9 * wg * E + 4 * wpart;
 #pragma unroll
-                for (int i = 0; i < 9; i++) cp_async16(dst + i * WW, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
-                // own-cell lagged values: windows Q, f_s, u_x (first copy), u_y, C (second)
-                const int k0 = wg, k1 = wg + 3;
-                const int a0 = k0 == 0 ? AUX_Q : (k0 == 1 ? AUX_FS : AUX_UX);
-                if (PB || k0 < 2) cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
-                if (PB && k1 < NAX)
-                    cp_async16(&w.ax[s3][k1][4 * wpart], plane_ptr(ain, k1 == 3 ? AUX_UY : AUX_C, K) + (y * K.pitch + wcol));
+                    for (int i = 0; i < 9; i++) cp_async16(dst + i * E, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
+                }
+            } else {
+                if (hg < 5) {
+#pragma unroll
+                    for (int q = 0; q < 6; q++) {
+                        const int wi = 5 * q + hg;  // window: f 0..8, h 9..17, l 18..26
+                        if (wi < 27) {
+                            const int set = wi / 9, i = wi - 9 * set;
+                            const int plane = (set == 0 ? SET_F * 9 : (set == 1 ? SET_H * 9 : SET_L * 9)) + i;
+                            cp_async16(pw + wi * E + CH * hpart,
+                                       plane_ptr(pin, plane, K) + ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
+                        }
+                    }
+                }
             }
+            stage_ax_win(y, s3);
         } else {
-            float *pp = &w.pop[s3][0][lane + off];
-            stage9<SET_F, WALLS>(K, pin, xg, y, cell, pp);
-            stage9<SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * WW);
-            stage9<SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * WW);
+            T *pp = pw + lane + off;
+            stage9<PS, SET_F, WALLS>(K, pin, xg, y, cell, pp);
+            stage9<PS, SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * E);
+            stage9<PS, SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * E);
             float *pa = &w.ax[s3][0][lane + off];
             cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
             cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
@@ -990,19 +1084,31 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     // pulled g of row y, for its phase B one iteration later
     auto stage_g = [&](int y) {
         if (!PB || y < ys || y >= ye) return;
+        T *gw = reinterpret_cast<T *>(&w.gp[y & 1][0][0]);
         if (win) {
-            if (wg < 3) {
-                const float *src = plane_ptr(pin, SET_G * 9, K) + wcol;
-                float *dst = &w.gp[y & 1][0][4 * wpart];
+            if constexpr (!PS::kHalf) {
+                if (wg < 3) {
+                    const T *src = plane_ptr(pin, SET_G * 9, K) + wcol;
 #pragma unroll
-                for (int q = 0; q < 3; q++) {
-                    const int i = 3 * q + wg;  // direction of this group's window
-                    const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
-                    cp_async16(dst + i * WW, plane_ptr(src, i, K) + (y - cyi) * K.pitch);
+                    for (int q = 0; q < 3; q++) {
+                        const int i = 3 * q + wg;  // direction of this group's window
+                        const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
+                        cp_async16(gw + i * E + 4 * wpart, plane_ptr(src, i, K) + (y - cyi) * K.pitch);
+                    }
+                }
+            } else {
+                if (hg < 5) {
+#pragma unroll
+                    for (int q = 0; q < 2; q++) {
+                        const int i = 5 * q + hg;
+                        if (i < 9)
+                            cp_async16(gw + i * E + CH * hpart,
+                                       plane_ptr(pin, SET_G * 9 + i, K) + ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
+                    }
                 }
             }
         } else if (b_lane) {
-            stage9<SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, &w.gp[y & 1][0][lane + off]);
+            stage9<PS, SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, gw + lane + off);
         }
     };
 
@@ -1028,14 +1134,16 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
             const float2 lag0 = w.lag[ya & 7][lane + 1];
             const real phi_p = lag0.x, T_p = lag0.y;
-            float *pp = &w.pop[s3][0][lane + off];
-            real dph, dtt;
+            real dph, dtt, v[9];
             lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
-            const real delta = sum9s(pp) + dph;
-            abb_fix9<WALLS>(K, pp + 9 * WW, xg, ya, T_p);  // phase B reads the corrected values
+            load9<PS, SET_F>(K, w, s3, lane + off, v);
+            const real delta = sum9(v) + dph;
+            load9<PS, SET_H>(K, w, s3, lane + off, v);
+            abb_fix9<WALLS>(K, v, xg, ya, T_p);
             const real Q_p = w.ax[s3][AX_Q][lane + off];
-            const real ed = sum9s(pp + 9 * WW) + K.rr * dtt + R(0.5) * Q_p;
-            const real sl = sum9s(pp + 18 * WW);
+            const real ed = sum9(v) + K.rr * dtt + R(0.5) * Q_p;
+            load9<PS, SET_L>(K, w, s3, lane + off, v);
+            const real sl = sum9(v);
             const real fs_p = w.ax[s3][AX_FS][lane + off];
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
@@ -1060,9 +1168,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
         if (PB && yb >= ys && yb < ye && b_lane) {
-            const RingAcc A{w, lane, off, {(yb - 1) & 3, yb & 3, (yb + 1) & 3}, {(yb - 1) & 7, yb & 7, (yb + 1) & 7},
-                            s3p, yb & 1};
-            phase_b<MODE, WALLS>(K, B, A, ex, yb, yb * K.pitch + ex);
+            const RingAcc<PS, WALLS> A{w, lane, off, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
+                                       {(yb - 1) & 7, yb & 7, (yb + 1) & 7}, s3p, yb & 1};
+            phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
         __syncwarp();
     }
@@ -1076,7 +1184,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
 #define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, LB_SMINB)
 #endif
 
-template <int MODE>
+template <int MODE, class PS>
 __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B, double *__restrict__ partials)
 {
     extern __shared__ __align__(16) unsigned char lb_smem[];
@@ -1093,9 +1201,9 @@ __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B,
         segment_rows(K.ny, K.segh, seg, ys, ye);
         if (x0 >= K.nx || ys >= ye) continue;  // the whole warp: warps never synchronise with one another
         if (seg < 2)
-            strip_rows<MODE, true>(K, B, w, lane, x0, ys, ye, acc);
+            strip_rows<MODE, true, PS>(K, B, w, lane, x0, ys, ye, acc);
         else
-            strip_rows<MODE, false>(K, B, w, lane, x0, ys, ye, acc);
+            strip_rows<MODE, false, PS>(K, B, w, lane, x0, ys, ye, acc);
         __syncwarp();
     }
     if (MODE == MODE_REDUCE) {
@@ -1130,6 +1238,7 @@ struct StepRec {
 
 constexpr size_t STEP_SMEM = STRIP_SMEM;
 
+template <class PS>
 __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst, int ninst, long long nitems,
                                                 int parity, unsigned long long *__restrict__ counter)
 {
@@ -1166,9 +1275,9 @@ __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst,
         segment_rows(K.ny, K.segh, seg, ys, ye);
         if (ys >= ye) continue;
         if (seg < 2)
-            strip_rows<MODE_STEP, true>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
+            strip_rows<MODE_STEP, true, PS>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
         else
-            strip_rows<MODE_STEP, false>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
+            strip_rows<MODE_STEP, false, PS>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
         __syncwarp();
     }
 }
@@ -1222,6 +1331,7 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
 // Inverse streaming: the stored state is post-collision, so the initial
 // post-streaming populations `eq` are placed where the next pull finds them,
 // f and h as deviations from the references of the cell that holds them.
+template <class PS>
 __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict__ eq, const float *__restrict__ aux,
                                         float *__restrict__ pops)
 {
@@ -1254,7 +1364,7 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
                     if (s == SET_H && i != 0) v += wgt(i) * K.rr * ((real)aux[AUX_T * K.plane + ct] - T_here);
                 }
                 if (s == SET_F) v -= wgt(i) * phi_here;
-                pops[(long long)(s * 9 + i) * K.plane + cell] = v;
+                reinterpret_cast<typename PS::T *>(pops)[(long long)(s * 9 + i) * K.plane + cell] = enc_pop<PS>(K, s, i, v);
             }
         }
     }

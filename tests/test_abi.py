@@ -42,13 +42,15 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbfreeze.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(lb_grid), sizeof(lb_params),'
-                    ' sizeof(lb_fields), offsetof(lb_params, fs_modulated_st), offsetof(lb_params, divu_mode));return 0;}\n')
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lb_grid), sizeof(lb_params),'
+                    ' sizeof(lb_fields), offsetof(lb_params, fs_modulated_st), offsetof(lb_params, divu_mode),'
+                    ' offsetof(lb_params, pop_storage));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)], check=True)
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
     assert vals == [C.sizeof(lbfreeze.lb_grid), C.sizeof(lbfreeze.lb_params), C.sizeof(lbfreeze.lb_fields),
-                    lbfreeze.lb_params.fs_modulated_st.offset, lbfreeze.lb_params.divu_mode.offset]
+                    lbfreeze.lb_params.fs_modulated_st.offset, lbfreeze.lb_params.divu_mode.offset,
+                    lbfreeze.lb_params.pop_storage.offset]
 
 
 def test_error_strings(lib):
@@ -74,7 +76,7 @@ def _create(lib, grid, params, n, phi=True):
     dict(grid=dict(nx=1, ny=1 << 26)),
     dict(params=dict(eps=0.0)), dict(params=dict(rho_g=0.0)), dict(params=dict(mu_l=0.0)),
     dict(params=dict(mobility=-1.0)), dict(params=dict(lam_s=0.0)), dict(params=dict(D_l=0.0)),
-    dict(params=dict(divu_mode=1)), dict(params=dict(sigma0=float("nan"))),
+    dict(params=dict(divu_mode=1)), dict(params=dict(pop_storage=2)), dict(params=dict(sigma0=float("nan"))),
     dict(params=dict(T_sol=1.0, T_liq=0.0)), dict(grid=dict(bc_top=7)), dict(phi=False)])
 def test_invalid_arguments_rejected_without_a_device(lib, bad):
     w = W.stefan_layer(nx=8, ny=8, h0=4)

@@ -1,0 +1,108 @@
+"""Half-precision population storage (lb_params.pop_storage = LB_STORAGE_F16).
+
+The populations are stored as scaled FP16 deviations and the arithmetic stays
+FP32, so the results differ from the oracle by the rounding of every stored
+population to 11 bits.  These tests state that difference: per field after 100
+steps (same scales as the FP32 parity tests), and on the end-of-run quantities
+-- the freezing time of a droplet and the mean front height of the film --
+which must stay within 1e-3 of the oracle like the FP32 path."""
+import numpy as np
+import pytest
+
+from paper_2511_09422_gb300 import lbfreeze
+from paper_2511_09422_gb300 import workloads as W
+
+import test_parity_gpu as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+F16 = 1
+FIELD_TOL = 6e-3  # measured at most 2.1e-3 (pressure, heated channel) after 100 steps
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2511_09422_gb300 import _build
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+    lbfreeze.load()
+
+
+def _half(w):
+    return dict(w, params=dict(w["params"], pop_storage=F16))
+
+
+@pytest.mark.parametrize("name,make,steps", P.CASES[:1] + P.CASES[3:], ids=[c[0] for c in P.CASES[:1] + P.CASES[3:]])
+def test_fp16_fields_against_oracle(oracle_mod, name, make, steps):
+    w = make()
+    got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=_half(w)["params"])
+    errs = P._rel_errors(got, want)
+    assert all(v <= FIELD_TOL for v in errs.values()), (name, errs)
+    assert all(np.isfinite(got[k]).all() for k in P.FIELDS)
+
+
+def test_fp16_freezing_time(oracle_mod):
+    w = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.2)
+    f32 = P._f32(w)
+    s = lbfreeze.Solver(w["grid"], _half(w)["params"], f32)
+    tf_gpu, _ = P._freezing_time(s.step, s.reduce, 5000)
+    s.close()
+    o = oracle_mod.Oracle(w["grid"], w["params"], {k: v.astype(np.float64) for k, v in f32.items()})
+    tf_ora, _ = P._freezing_time(o.step, o.reduce, 5000)
+    assert abs(tf_gpu - tf_ora) <= 1e-3 * tf_ora, (tf_gpu, tf_ora)
+
+
+def test_fp16_front_height_end_of_run(oracle_mod):
+    w = W.stefan_layer(nx=64, ny=256)
+    f32 = P._f32(w)
+    s = lbfreeze.Solver(w["grid"], _half(w)["params"], f32)
+    s.step(w["steps"])
+    red = s.reduce()
+    s.close()
+    o = oracle_mod.Oracle(w["grid"], w["params"], {k: v.astype(np.float64) for k, v in f32.items()})
+    o.step(w["steps"])
+    wred = o.reduce()
+    assert abs(red[3] - wred[3]) <= 1e-3 * wred[3], (red[3] / 64, wred[3] / 64)
+
+
+def test_fp16_checkpoint_resume_bitwise(tmp_path):
+    w = _half(W.parity_droplet(nx=64, ny=48))
+    f32 = P._f32(w)
+    a = lbfreeze.Solver(w["grid"], w["params"], f32)
+    a.step(30)
+    a.save(str(tmp_path / "ck16.bin"))
+    a.step(30)
+    fa = a.fields()
+    b = lbfreeze.Solver(w["grid"], w["params"], f32)
+    b.load_state(str(tmp_path / "ck16.bin"))
+    b.step(30)
+    fb = b.fields()
+    for k in P.FIELDS:
+        assert np.array_equal(fa[k], fb[k]), k
+    c = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=0), f32)
+    with pytest.raises(lbfreeze.LbError):
+        c.load_state(str(tmp_path / "ck16.bin"))  # written with the other storage
+
+
+def test_fp16_batch_matches_single_and_rejects_mixed_storage():
+    ws = [_half(W.parity_droplet(nx=40, ny=33, seed=1)), _half(W.impurity_front(nx=128, ny=100, radius=15.0)),
+          _half(W.sessile_droplet(nx=150, ny=130, radius=40.0, rho_g=0.1, ste=0.3, c0=0.07))]
+    for w in ws:
+        w["fields"] = P._f32(w)
+    b = lbfreeze.Batch(ws)
+    b.step(11)
+    for i, w in enumerate(ws):
+        s = lbfreeze.Solver(w["grid"], w["params"], w["fields"])
+        s.step(11)
+        want = s.fields()
+        s.close()
+        got = b.instance(i).fields()
+        for k in P.FIELDS:
+            assert np.array_equal(got[k], want[k]), (i, k)
+    b.close()
+    mixed = [ws[0], dict(ws[1], params=dict(ws[1]["params"], pop_storage=0))]
+    with pytest.raises(lbfreeze.LbError) as e:
+        lbfreeze.Batch(mixed)
+    assert "pop_storage" in str(e.value)
