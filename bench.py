@@ -161,6 +161,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+BYTES_PER_UPDATE_F16 = 216  # 36 populations read + written as FP16, 9 lagged FP32 fields read + written
+
+
+def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
+    """The same lattice with half-precision population storage: MLUPS, and
+    achieved bandwidth against its own algorithmic bytes (216 B per update)."""
+    s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=1), f32, stream=stream)
+    s.step(args.warmup)
+    stream.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    s.reduce()  # raises if the half-precision run went non-finite
+    s.close()
+    mlups = ws * cells * args.steps / (ms * 1e-3) / 1e6
+    gbs = BYTES_PER_UPDATE_F16 * cells * args.steps / (ms * 1e-3) / 1e9
+    return {"metric": "MLUPS (all coupled fields), FP16 population storage", "value": round(mlups, 2),
+            "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_F16,
+            "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
+            "dtype": "f32 arithmetic, f16 populations"}
+
+
 def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
     """Instance-steps/s of the droplet sweep: the batched persistent launch
     (autotuned segment heights, CUDA graph) against the same instances stepped
@@ -279,6 +311,10 @@ def run_gpu(args):
     e2e_value = ws * cells * args.steps / float(te.item()) / 1e6
 
     # ---- batched form: a sweep of independent droplets in one launch per step -----------
+    fp16 = None
+    if not args.no_fp16:
+        fp16 = _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
+                         _peaks()[0].get("hbm_gbs"))
     batched = None
     if args.batch > 0:
         batched = _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist if ws > 1 else None)
@@ -315,6 +351,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d),
                 "d2h_bytes_per_step": round(d2h)},
         "gpu_launches": args.steps * launches_per_step,
+        "fp16_storage": fp16,
         "batched": batched,
         "clocks": clk.summary(),
         "check": {"sum_phi": red[0], "sum_C": red[2], "front": red[5]},
@@ -333,6 +370,7 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="droplet-sweep instances of the batched leg (0: skip)")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the half-precision population storage leg")
     ap.add_argument("--batch-steps", type=int, default=100)
     args = ap.parse_args()
     if args.impl == "reference":
