@@ -30,9 +30,11 @@
  *
  * Errors: calls return CNO_OK or an error code; cno_error_string describes
  * the last failure of the calling thread.  Kernels give up a wait on the
- * tensor-core pipeline after 4 s and record it in a device status word; the
- * next call that synchronises returns CNO_ERR_DEVICE_WAIT and no later launch
- * does any work until cno_reset_status.
+ * tensor-core pipeline after 4 s and record it in a device status word (one
+ * per network, one per device for the primitives); later launches that see the
+ * word set do no work.  The next network call that synchronises returns
+ * CNO_ERR_DEVICE_WAIT (destroy and recreate the network); for the primitives,
+ * cno_read_status reports and clears the word.
  */
 #ifndef CNO_H
 #define CNO_H
@@ -127,16 +129,26 @@ cno_status cno_last_output(cno_net *net, const float **out);
 cno_status cno_pack_fields(const float *const *fields, int nfield, int nx, int ny, const float *offset,
                            const float *inv_scale, void *x, int cin, void *stream);
 
-/* field_k += scale[k] * out[y][x][k] for k < nfield (out FP32 [ny][nx][out_cs]). */
-cno_status cno_apply_update(float *const *fields, int nfield, int nx, int ny, const float *out, int out_cs,
-                            const float *scale, void *stream);
+/* Training target from two snapshots of the same lattice k steps apart:
+ * target[y][x][f] = (next_f - cur_f) * inv_scale[f] (FP32 [ny][nx][nfield]). */
+cno_status cno_pack_delta(const float *const *cur, const float *const *next, int nfield, int nx, int ny,
+                          const float *inv_scale, float *target, void *stream);
 
-/* Checks of a phase field phi (device, nx*ny) in FP64, summed in a fixed
- * order: out[0] = sum phi, out[1] = sum (1 - phi^2), out[2] = sum |grad phi|
- * (central differences inside, one-sided at the walls y = 0 and ny - 1, periodic
- * in x).  For a flat profile phi = tanh(2 d / W_i), out[1] / out[2] = W_i / 2 per
- * unit interface length.  Synchronises the stream; out is host memory. */
-cno_status cno_phase_checks(const float *phi, int nx, int ny, double out[3], void *stream);
+/* dst_f = src_f + scale[f] * out[y][x][f] for f < nfield (out FP32
+ * [ny][nx][out_cs]); dst may equal src. */
+cno_status cno_apply_update(const float *const *src, float *const *dst, int nfield, int nx, int ny,
+                            const float *out, int out_cs, const float *scale, void *stream);
+
+/* Acceptance checks of a predicted state, FP64 sums in a fixed order over a
+ * lattice with walls at y = 0 and y = ny - 1 and periodic x:
+ *   out[0] = sum phi,  out[1] = sum chi, chi = clamp((1 + phi) / 2, 0, 1),
+ *   out[2] = sum f_s (0 if fs is NULL),
+ *   out[3] = sum (1 - phi^2),  out[4] = sum |grad phi| (central differences,
+ *   one-sided next to the walls).
+ * The mass of the phase-change material is rho_s out[2] + rho_l (out[1] - out[2]);
+ * for a flat profile phi = tanh(2 d / W) the width is W = 2 out[3] / out[4].
+ * Synchronises the stream; out is host memory. */
+cno_status cno_field_checks(const float *phi, const float *fs, int nx, int ny, double out[5], void *stream);
 
 #ifdef __cplusplus
 }

@@ -138,6 +138,21 @@ lb_status lb_step(lb_handle *h, int n);
 lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C, float *ux,
                         float *uy, float *p, int on_device);
 
+/* Replace the current state by the equilibrium state of the given fields
+ * (the inverse of lb_get_fields): populations at the equilibria of (phi, u, p,
+ * C) and of the enthalpy, lagged fields set from the inputs.  Same layout as
+ * lb_get_fields (nx*ny floats each, host or device memory); phi, T, C are
+ * required.  fs: the solid fraction, clamped to [0, chi]; the enthalpy is
+ * then the latent part rho_l L (chi - f_s) plus the sensible part with the
+ * mixture rule T (f_s (rho Cp)_s + (chi - f_s) (rho Cp)_l + (1 - chi)
+ * (rho Cp)_g).  fs = NULL derives f_s from (T, chi) as lb_create does.
+ * ux, uy, p = NULL mean 0.  The step count and V_0 are kept.  This is how a
+ * learned surrogate's prediction of the fields is handed back to the method;
+ * the paper has no counterpart.  With host inputs the call synchronises the
+ * stream. */
+lb_status lb_set_fields(lb_handle *h, const float *phi, const float *T, const float *fs, const float *C,
+                        const float *ux, const float *uy, const float *p, int on_device);
+
 /* Global diagnostics of the current state in FP64, summed in a fixed order:
  *   out[0] sum phi     out[1] sum rho H    out[2] sum C     out[3] sum f_s
  *   out[4] sum chi, chi = clamp((1 + phi)/2, 0, 1)

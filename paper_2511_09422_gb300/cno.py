@@ -29,7 +29,7 @@ _lock = threading.Lock()
 EXPORTS = ("cno_error_string", "cno_read_status", "cno_conv3x3_forward", "cno_conv3x3_dgrad", "cno_conv3x3_wgrad",
            "cno_weights_to_bf16", "cno_create", "cno_destroy", "cno_set_stream", "cno_num_params",
            "cno_set_params", "cno_get_params", "cno_get_grads", "cno_forward", "cno_train_step",
-           "cno_last_output", "cno_pack_fields", "cno_apply_update", "cno_phase_checks")
+           "cno_last_output", "cno_pack_fields", "cno_pack_delta", "cno_apply_update", "cno_field_checks")
 
 
 class CnoError(RuntimeError):
@@ -71,8 +71,9 @@ def load(path: str | None = None):
             "cno_train_step": (i, [vp, vp, vp, i, i, i, f, i, C.POINTER(d)]),
             "cno_last_output": (i, [vp, C.POINTER(vp)]),
             "cno_pack_fields": (i, [vp, i, i, i, vp, vp, vp, i, vp]),
-            "cno_apply_update": (i, [vp, i, i, i, vp, i, vp, vp]),
-            "cno_phase_checks": (i, [vp, i, i, C.POINTER(d), vp]),
+            "cno_pack_delta": (i, [vp, vp, i, i, i, vp, vp, vp]),
+            "cno_apply_update": (i, [vp, vp, i, i, i, vp, i, vp, vp]),
+            "cno_field_checks": (i, [vp, vp, i, i, C.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -231,29 +232,41 @@ class Net:
         return float(loss.value) if want_loss else None
 
 
-def pack_fields(fields, offset, inv_scale, cin=CIN):
-    """Network input (bf16 [1,ny,nx,cin]) from a list of device FP32 fields [ny,nx]."""
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def pack_fields(fields, offset, inv_scale, cin=CIN, out=None):
+    """Network input (bf16 [1,ny,nx,cin], or the given `out` of that shape) from a
+    list of device FP32 fields [ny,nx]."""
     import torch
     ny, nx = fields[0].shape
-    x = torch.empty((1, ny, nx, cin), device=fields[0].device, dtype=torch.bfloat16)
-    ptrs = (C.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
+    x = torch.empty((1, ny, nx, cin), device=fields[0].device, dtype=torch.bfloat16) if out is None else out
     off = (C.c_float * len(fields))(*offset)
     isc = (C.c_float * len(fields))(*inv_scale)
-    _check(load().cno_pack_fields(ptrs, len(fields), nx, ny, off, isc, _ptr(x), cin, _stream()))
+    _check(load().cno_pack_fields(_ptr_array(fields), len(fields), nx, ny, off, isc, _ptr(x), cin, _stream()))
     return x
 
 
-def apply_update(fields, out, scale):
-    """fields[k] += scale[k] * out[..., k] in place (device)."""
-    ny, nx = fields[0].shape
-    ptrs = (C.c_void_p * len(fields))(*[f.data_ptr() for f in fields])
-    sc = (C.c_float * len(fields))(*scale)
-    _check(load().cno_apply_update(ptrs, len(fields), nx, ny, _ptr(out), out.shape[-1], sc, _stream()))
+def pack_delta(cur, nxt, inv_scale, out):
+    """out[y,x,f] = (nxt[f] - cur[f]) * inv_scale[f] (device FP32 [ny,nx,nfield])."""
+    ny, nx = cur[0].shape
+    isc = (C.c_float * len(cur))(*inv_scale)
+    _check(load().cno_pack_delta(_ptr_array(cur), _ptr_array(nxt), len(cur), nx, ny, isc, _ptr(out), _stream()))
+    return out
 
 
-def phase_checks(phi):
-    """(sum phi, sum (1 - phi^2), sum |grad phi|) in FP64 of a device field [ny,nx]."""
+def apply_update(src, dst, out, scale):
+    """dst[f] = src[f] + scale[f] * out[..., f] (device; dst may be src)."""
+    ny, nx = src[0].shape
+    sc = (C.c_float * len(src))(*scale)
+    _check(load().cno_apply_update(_ptr_array(src), _ptr_array(dst), len(src), nx, ny, _ptr(out), out.shape[-1], sc,
+                                   _stream()))
+
+
+def field_checks(phi, fs=None):
+    """(sum phi, sum chi, sum f_s, sum (1 - phi^2), sum |grad phi|) in FP64 of device fields [ny,nx]."""
     ny, nx = phi.shape
-    out = (C.c_double * 3)()
-    _check(load().cno_phase_checks(_ptr(phi), nx, ny, out, _stream()))
+    out = (C.c_double * 5)()
+    _check(load().cno_field_checks(_ptr(phi), _ptr(fs), nx, ny, out, _stream()))
     return tuple(out)

@@ -921,52 +921,65 @@ __global__ void pack_fields_kernel(FieldPtrs fp, int nfield, long long npix, int
     }
 }
 
-__global__ void apply_update_kernel(FieldOut fo, int nfield, long long npix, const float *__restrict__ out,
-                                    int out_cs)
+__global__ void pack_delta_kernel(FieldPtrs cur, FieldPtrs next, int nfield, long long npix, float *__restrict__ t)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
          p += (long long)gridDim.x * blockDim.x) {
         for (int k = 0; k < nfield; k++)
-            fo.f[k][p] += fo.sc[k] * out[p * out_cs + k];
+            t[p * nfield + k] = (next.f[k][p] - cur.f[k][p]) * cur.sc[k];
     }
 }
 
-// per-row sums of phi, 1 - phi^2, |grad phi| (FP64), one block per row
-__global__ void phase_rows_kernel(const float *__restrict__ phi, int nx, int ny, double *__restrict__ rows)
+__global__ void apply_update_kernel(FieldPtrs src, FieldOut dst, int nfield, long long npix,
+                                    const float *__restrict__ out, int out_cs)
 {
-    __shared__ double red[3][256];
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+         p += (long long)gridDim.x * blockDim.x) {
+        for (int k = 0; k < nfield; k++)
+            dst.f[k][p] = src.f[k][p] + dst.sc[k] * out[p * out_cs + k];
+    }
+}
+
+// per-row sums of phi, chi, f_s, 1 - phi^2, |grad phi| (FP64), one block per row
+constexpr int NCHK = 5;
+__global__ void field_rows_kernel(const float *__restrict__ phi, const float *__restrict__ fs, int nx, int ny,
+                                  double *__restrict__ rows)
+{
+    __shared__ double red[NCHK][256];
     const int y = blockIdx.x;
-    double s0 = 0, s1 = 0, s2 = 0;
+    double s[NCHK] = {0, 0, 0, 0, 0};
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-        const double f = phi[(long long)y * nx + x];
+        const long long c = (long long)y * nx + x;
+        const double f = phi[c];
         const double fe = phi[(long long)y * nx + (x + 1) % nx], fw = phi[(long long)y * nx + (x + nx - 1) % nx];
         double gy;
         if (ny == 1)
             gy = 0.0;
         else if (y == 0)
-            gy = phi[(long long)1 * nx + x] - f;
+            gy = phi[c + nx] - f;
         else if (y == ny - 1)
-            gy = f - phi[(long long)(ny - 2) * nx + x];
+            gy = f - phi[c - nx];
         else
-            gy = 0.5 * (phi[(long long)(y + 1) * nx + x] - phi[(long long)(y - 1) * nx + x]);
+            gy = 0.5 * (phi[c + nx] - phi[c - nx]);
         const double gx = 0.5 * (fe - fw);
-        s0 += f;
-        s1 += 1.0 - f * f;
-        s2 += sqrt(gx * gx + gy * gy);
+        s[0] += f;
+        s[1] += fmin(fmax(0.5 * (1.0 + f), 0.0), 1.0);
+        s[2] += fs ? (double)fs[c] : 0.0;
+        s[3] += 1.0 - f * f;
+        s[4] += sqrt(gx * gx + gy * gy);
     }
-    red[0][threadIdx.x] = s0;
-    red[1][threadIdx.x] = s1;
-    red[2][threadIdx.x] = s2;
+    for (int k = 0; k < NCHK; k++)
+        red[k][threadIdx.x] = s[k];
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 3; k++)
-                red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int k = 0; k < NCHK; k++)
+                red[k][threadIdx.x] += red[k][threadIdx.x + st];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; k++)
-            rows[3 * y + k] = red[k][0];
+        for (int k = 0; k < NCHK; k++)
+            rows[NCHK * y + k] = red[k][0];
 }
 }  // namespace
 
@@ -990,39 +1003,68 @@ extern "C" cno_status cno_pack_fields(const float *const *fields, int nfield, in
     return CNO_OK;
 }
 
-extern "C" cno_status cno_apply_update(float *const *fields, int nfield, int nx, int ny, const float *out,
-                                       int out_cs, const float *scale, void *stream)
+static cno_status field_ptrs(const float *const *f, int nfield, const float *sc, FieldPtrs *fp)
 {
-    if (!fields || !out || !scale || nfield < 1 || nfield > MAXF || out_cs < nfield || nx < 1 || ny < 1)
-        return fail(CNO_ERR_INVALID_ARG, "bad update arguments");
-    FieldOut fo;
     for (int k = 0; k < MAXF; k++) {
-        fo.f[k] = k < nfield ? fields[k] : nullptr;
-        fo.sc[k] = k < nfield ? scale[k] : 0.0f;
-        if (k < nfield && !fields[k])
+        fp->f[k] = k < nfield ? f[k] : nullptr;
+        fp->off[k] = 0.0f;
+        fp->sc[k] = (k < nfield && sc) ? sc[k] : 0.0f;
+        if (k < nfield && !f[k])
             return fail(CNO_ERR_INVALID_ARG, "null field");
     }
+    return CNO_OK;
+}
+
+extern "C" cno_status cno_pack_delta(const float *const *cur, const float *const *next, int nfield, int nx, int ny,
+                                     const float *inv_scale, float *target, void *stream)
+{
+    if (!cur || !next || !inv_scale || !target || nfield < 1 || nfield > MAXF || nx < 1 || ny < 1)
+        return fail(CNO_ERR_INVALID_ARG, "bad target arguments");
+    FieldPtrs a, b;
+    CS(field_ptrs(cur, nfield, inv_scale, &a));
+    CS(field_ptrs(next, nfield, inv_scale, &b));
     const long long npix = (long long)nx * ny;
-    apply_update_kernel<<<grid_for(npix, 256), 256, 0, (cudaStream_t)stream>>>(fo, nfield, npix, out, out_cs);
+    pack_delta_kernel<<<grid_for(npix, 256), 256, 0, (cudaStream_t)stream>>>(a, b, nfield, npix, target);
     CK(cudaGetLastError());
     return CNO_OK;
 }
 
-extern "C" cno_status cno_phase_checks(const float *phi, int nx, int ny, double out[3], void *stream)
+extern "C" cno_status cno_apply_update(const float *const *src, float *const *dst, int nfield, int nx, int ny,
+                                       const float *out, int out_cs, const float *scale, void *stream)
+{
+    if (!src || !dst || !out || !scale || nfield < 1 || nfield > MAXF || out_cs < nfield || nx < 1 || ny < 1)
+        return fail(CNO_ERR_INVALID_ARG, "bad update arguments");
+    FieldPtrs a;
+    CS(field_ptrs(src, nfield, nullptr, &a));
+    FieldOut o;
+    for (int k = 0; k < MAXF; k++) {
+        o.f[k] = k < nfield ? dst[k] : nullptr;
+        o.sc[k] = k < nfield ? scale[k] : 0.0f;
+        if (k < nfield && !dst[k])
+            return fail(CNO_ERR_INVALID_ARG, "null field");
+    }
+    const long long npix = (long long)nx * ny;
+    apply_update_kernel<<<grid_for(npix, 256), 256, 0, (cudaStream_t)stream>>>(a, o, nfield, npix, out, out_cs);
+    CK(cudaGetLastError());
+    return CNO_OK;
+}
+
+extern "C" cno_status cno_field_checks(const float *phi, const float *fs, int nx, int ny, double out[5], void *stream)
 {
     if (!phi || !out || nx < 1 || ny < 1)
         return fail(CNO_ERR_INVALID_ARG, "bad check arguments");
     double *rows = nullptr;
-    CK(cudaMallocAsync(&rows, (size_t)ny * 3 * sizeof(double), (cudaStream_t)stream));
-    phase_rows_kernel<<<ny, 256, 0, (cudaStream_t)stream>>>(phi, nx, ny, rows);
+    CK(cudaMallocAsync(&rows, (size_t)ny * NCHK * sizeof(double), (cudaStream_t)stream));
+    field_rows_kernel<<<ny, 256, 0, (cudaStream_t)stream>>>(phi, fs, nx, ny, rows);
     CK(cudaGetLastError());
-    std::vector<double> h((size_t)ny * 3);
+    std::vector<double> h((size_t)ny * NCHK);
     CK(cudaMemcpyAsync(h.data(), rows, h.size() * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CK(cudaFreeAsync(rows, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    out[0] = out[1] = out[2] = 0.0;
+    for (int k = 0; k < NCHK; k++)
+        out[k] = 0.0;
     for (int y = 0; y < ny; y++)
-        for (int k = 0; k < 3; k++)
-            out[k] += h[3 * y + k];
+        for (int k = 0; k < NCHK; k++)
+            out[k] += h[(size_t)NCHK * y + k];
     return CNO_OK;
 }

@@ -348,8 +348,8 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
             if (ae != cudaSuccess) { st = cuda_fail(h, ae, "cudaMalloc of the initial equilibria"); break; }
             eq = eq_tmp;
         }
-        lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4], eq,
-                                                                           h->aux[0]);
+        lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4],
+                                                                           nullptr, nullptr, eq, h->aux[0]);
         if (h->half)
             lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
                                                                                                  h->pops[0]);
@@ -428,6 +428,46 @@ extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs
         CK(h, cudaMemcpy2DAsync(dst[k], sizeof(float) * K.nx, h->fields + (size_t)k * K.plane, sizeof(float) * K.pitch,
                                 sizeof(float) * K.nx, K.ny, kind, h->stream));
     }
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return LB_OK;
+}
+
+extern "C" lb_status lb_set_fields(lb_handle *h, const float *phi, const float *T, const float *fs, const float *C,
+                                   const float *ux, const float *uy, const float *p, int on_device)
+{
+    if (!h) return LB_ERR_INVALID_ARG;
+    if (h->sticky != LB_OK) return h->sticky;
+    if (!phi || !T || !C) return fail(h, LB_ERR_INVALID_ARG, "phi, T and C are required");
+    const Consts &K = h->K;
+    const size_t n = (size_t)K.nx * K.ny;
+    // the inputs go to the 7-plane fields buffer first (dense, as lb_create does), in
+    // the argument order phi, T, C, ux, uy, fs, p
+    const float *src[7] = {phi, T, C, ux, uy, fs, p};
+    const float *dev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int k = 0; k < 7; k++) {
+        if (!src[k]) continue;
+        float *d = h->fields + (size_t)k * K.plane;
+        CK(h, cudaMemcpyAsync(d, src[k], sizeof(float) * n, kind, h->stream));
+        dev[k] = d;
+    }
+    const size_t plane_b = sizeof(float) * (size_t)K.plane;
+    float *eq = h->pops[1 - h->cur], *eq_tmp = nullptr;
+    if (h->half) {
+        CK(h, cudaMallocAsync((void **)&eq_tmp, 36 * plane_b, h->stream));
+        eq = eq_tmp;
+    }
+    lbk::lb_init_eq_kernel<<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3],
+                                                                                 dev[4], dev[5], dev[6], eq,
+                                                                                 h->aux[h->cur]);
+    if (h->half)
+        lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
+            K, eq, h->aux[h->cur], h->pops[h->cur]);
+    else
+        lbk::lb_init_unstream_kernel<lbk::PopF32><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
+            K, eq, h->aux[h->cur], h->pops[h->cur]);
+    CK(h, cudaGetLastError());
+    if (eq_tmp) CK(h, cudaFreeAsync(eq_tmp, h->stream));
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }

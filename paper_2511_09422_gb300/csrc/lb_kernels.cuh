@@ -1289,7 +1289,8 @@ __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst,
 // ---------------------------------------------------------------------------------------
 __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0, const float *__restrict__ T0,
                                   const float *__restrict__ C0, const float *__restrict__ ux0,
-                                  const float *__restrict__ uy0, float *__restrict__ eq, float *__restrict__ aux)
+                                  const float *__restrict__ uy0, const float *__restrict__ fs0,
+                                  const float *__restrict__ p0, float *__restrict__ eq, float *__restrict__ aux)
 {
     const long long n = (long long)K.nx * K.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -1299,7 +1300,15 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
         const real ux = ux0 ? ux0[k] : R(0.0), uy = uy0 ? uy0[k] : R(0.0);
         const real chi = clamp01(R(0.5) * (R(1.0) + phi));
         real fs;
-        const real e_sens = forward_sensible(K, T, chi, fs);
+        real e_sens;
+        if (fs0) {
+            // given solid fraction (clamped to [0, chi]): sensible enthalpy by the
+            // mixture rule of the volumetric heat capacities
+            fs = K.phase_change ? fminf(fmaxf(fs0[k], R(0.0)), chi) : R(0.0);
+            e_sens = T * (fs * K.rcp_s + (chi - fs) * K.rcp_l + (R(1.0) - chi) * K.rcp_g);
+        } else {
+            e_sens = forward_sensible(K, T, chi, fs);
+        }
         const real rho = zeta(phi, fs, K.rho_l, K.rho_s, K.rho_g);
         const real rhocp = zeta(phi, fs, K.rcp_l, K.rcp_s, K.rcp_g);
         const real uu = ux * ux + uy * uy;
@@ -1322,7 +1331,7 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
         aux[AUX_UY * K.plane + cell] = uy;
         aux[AUX_PHI * K.plane + cell] = phi;
         aux[AUX_C * K.plane + cell] = C;
-        aux[AUX_P * K.plane + cell] = 0.0f;
+        aux[AUX_P * K.plane + cell] = p0 ? p0[k] : 0.0f;
         aux[AUX_S * K.plane + cell] = 0.0f;
         aux[AUX_T * K.plane + cell] = T;
     }
@@ -1330,7 +1339,7 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
 
 // Inverse streaming: the stored state is post-collision, so the initial
 // post-streaming populations `eq` are placed where the next pull finds them,
-// f and h as deviations from the references of the cell that holds them.
+// f, g and h as deviations from the references of the cell that holds them.
 template <class PS>
 __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict__ eq, const float *__restrict__ aux,
                                         float *__restrict__ pops)
@@ -1362,6 +1371,8 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
                     const long long ct = (long long)yt * K.pitch + xt;
                     v = eq[(long long)(s * 9 + i) * K.plane + ct];
                     if (s == SET_H && i != 0) v += wgt(i) * K.rr * ((real)aux[AUX_T * K.plane + ct] - T_here);
+                    if (s == SET_G && i != 0)
+                        v += R(3.0) * wgt(i) * ((real)aux[AUX_P * K.plane + ct] - (real)aux[AUX_P * K.plane + cell]);
                 }
                 if (s == SET_F) v -= wgt(i) * phi_here;
                 reinterpret_cast<typename PS::T *>(pops)[(long long)(s * 9 + i) * K.plane + cell] = enc_pop<PS>(K, s, i, v);

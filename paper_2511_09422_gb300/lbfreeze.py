@@ -52,7 +52,7 @@ class lb_fields(C.Structure):
 _lib = None
 _lock = threading.Lock()
 
-EXPORTS = ("lb_create", "lb_set_stream", "lb_step", "lb_get_fields", "lb_reduce", "lb_steps_taken",
+EXPORTS = ("lb_create", "lb_set_stream", "lb_step", "lb_get_fields", "lb_set_fields", "lb_reduce", "lb_steps_taken",
            "lb_save", "lb_load", "lb_destroy", "lb_error_string", "lb_last_error", "lb_device_bytes",
            "lb_batch_create", "lb_batch_set_stream", "lb_batch_step", "lb_batch_use_graph", "lb_batch_tune",
            "lb_batch_instance", "lb_batch_size", "lb_batch_last_error", "lb_batch_destroy")
@@ -80,6 +80,8 @@ def load(path: str | None = None):
         L.lb_step.argtypes = [C.c_void_p, C.c_int]
         L.lb_get_fields.restype = C.c_int
         L.lb_get_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 7 + [C.c_int]
+        L.lb_set_fields.restype = C.c_int
+        L.lb_set_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 7 + [C.c_int]
         L.lb_reduce.restype = C.c_int
         L.lb_reduce.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
         L.lb_steps_taken.restype = C.c_int
@@ -296,6 +298,33 @@ class Solver:
             ptrs = [C.c_void_p(out[k].ctypes.data) if k in out else None for k in FIELD_NAMES]
         self._check(load().lb_get_fields(self._h, *ptrs, 1 if device else 0))
         return out
+
+    def set_fields(self, fields: dict):
+        """Replace the state by the equilibrium of the given fields (keys of
+        FIELD_NAMES; phi, T, C required): all numpy float32 (ny, nx) arrays, or
+        all contiguous float32 CUDA tensors."""
+        order = ("phi", "T", "fs", "C", "ux", "uy", "p")
+        vals = [fields.get(k) for k in order]
+        dev = [_is_cuda_tensor(v) for v in vals if v is not None]
+        if dev and any(dev) != all(dev):
+            raise ValueError("set_fields mixes host and device inputs")
+        device = bool(dev) and all(dev)
+        keep, ptrs = [], []
+        for k, v in zip(order, vals):
+            if v is None:
+                ptrs.append(None)
+                continue
+            if device:
+                if not (str(v.dtype) == "torch.float32" and v.is_contiguous() and v.numel() == self.nx * self.ny):
+                    raise ValueError("set_fields: %s must be contiguous float32 with nx*ny values" % k)
+                ptrs.append(C.c_void_p(v.data_ptr()))
+            else:
+                a = np.ascontiguousarray(v, dtype=np.float32)
+                if a.size != self.nx * self.ny:
+                    raise ValueError("set_fields: %s must have nx*ny values" % k)
+                keep.append(a)
+                ptrs.append(C.c_void_p(a.ctypes.data))
+        self._check(load().lb_set_fields(self._h, *ptrs, 1 if device else 0))
 
     def reduce(self) -> np.ndarray:
         out = (C.c_double * 8)()
