@@ -244,6 +244,54 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
             "speedup": round(v_b / v_s, 3)}
 
 
+def _surrogate_leg(args, torch, peaks):
+    """The learned surrogate: trained here on LB trajectories (256^2
+    droplets and impurity fronts), then LB alone vs LB with surrogate jumps and
+    the enthalpy / mass / width checks on the 4096^2 impurity front, the
+    freezing time of a held-out droplet, and the throughput of the tensor-core
+    forward pass."""
+    from paper_2511_09422_gb300 import cno
+    from paper_2511_09422_gb300 import surrogate as S
+    from paper_2511_09422_gb300 import workloads as W
+    net, norm, info = S.train_default(n_instances=args.sur_lattices, steps=args.sur_steps, iters=args.sur_iters)
+    big = W.impurity_front(nx=args.size, ny=args.size, radius=200.0 * args.size / 4096.0)
+    cmp = S.compare(big, net, norm, steps=500)
+    held = S.training_workloads(args.sur_lattices, 256)[info["holdout"][0]]
+    tf_lb, dt_lb, _ = S.freezing_time(held)
+    tf_s, dt_s, st_s = S.freezing_time(held, net, norm)
+    # forward pass of the network on the large lattice, timed with CUDA events
+    x = torch.zeros((1, args.size, args.size, cno.CIN), dtype=torch.bfloat16, device="cuda")
+    out = torch.empty((1, args.size, args.size, cno.NF), dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        net.forward(x, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        net.forward(x, out=out)
+    e1.record()
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / 5
+    flops = cno.forward_flops(args.size, args.size)
+    tflops = flops / (fwd_ms * 1e-3) / 1e12
+    peak_tf = peaks.get("bf16_tflops")
+    net.close()
+    lb, su = cmp["lb"], cmp["surrogate"]
+    return {
+        "metric": "LB-step equivalents/s on impurity_front %dx%d with surrogate jumps of %d steps (500 steps)"
+                  % (args.size, args.size, S.K_JUMP),
+        "value": round(su["steps_per_s"], 1), "lb_alone": round(lb["steps_per_s"], 1),
+        "speedup": round(su["steps_per_s"] / lb["steps_per_s"], 3), "stepper": su["stats"],
+        "front_rel_diff": cmp["front_rel_diff"], "solid_rel_diff": cmp["solid_rel_diff"],
+        "freezing_time_heldout_droplet": {"lb": round(tf_lb, 1), "surrogate": round(tf_s, 1),
+                                          "rel_error": abs(tf_s - tf_lb) / tf_lb, "lb_s": round(dt_lb, 3),
+                                          "surrogate_s": round(dt_s, 3), "stepper": st_s},
+        "training": info,
+        "forward": {"ms": round(fwd_ms, 3), "tflops": round(tflops, 1), "flops": flops,
+                    "frac_of_bf16_peak": round(tflops / peak_tf, 4) if peak_tf else None,
+                    "dtype": "bf16 operands, f32 accumulate"},
+    }
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -318,6 +366,9 @@ def run_gpu(args):
     batched = None
     if args.batch > 0:
         batched = _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist if ws > 1 else None)
+    sur = None
+    if args.sur_iters > 0 and ws == 1:
+        sur = _surrogate_leg(args, torch, _peaks()[0])
     h2d = sum(v.numel() * 4 for v in pin_in.values()) / args.steps
     d2h = 8 * 8 + sum(v.numel() * 4 for v in pin_out.values()) / args.steps
 
@@ -353,6 +404,7 @@ def run_gpu(args):
         "gpu_launches": args.steps * launches_per_step,
         "fp16_storage": fp16,
         "batched": batched,
+        "surrogate": sur,
         "clocks": clk.summary(),
         "check": {"sum_phi": red[0], "sum_C": red[2], "front": red[5]},
     }
@@ -372,6 +424,9 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="droplet-sweep instances of the batched leg (0: skip)")
     ap.add_argument("--no-fp16", action="store_true", help="skip the half-precision population storage leg")
     ap.add_argument("--batch-steps", type=int, default=100)
+    ap.add_argument("--sur-iters", type=int, default=3000, help="surrogate training iterations (0: skip the leg)")
+    ap.add_argument("--sur-lattices", type=int, default=48, help="LB trajectories the surrogate is trained on")
+    ap.add_argument("--sur-steps", type=int, default=12000, help="LB steps per training trajectory")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -135,20 +135,33 @@ cno_status cno_pack_delta(const float *const *cur, const float *const *next, int
                           const float *inv_scale, float *target, void *stream);
 
 /* dst_f = src_f + scale[f] * out[y][x][f] for f < nfield (out FP32
- * [ny][nx][out_cs]); dst may equal src. */
+ * [ny][nx][out_cs]), then clamped to [lo[f], hi[f]] if lo and hi are given
+ * (host arrays of nfield values); dst may equal src.  A field with
+ * scale[f] = 0 is copied unchanged (and not clamped).  If phi_band > 0,
+ * field 0 (phi) changes only where |src_0| < phi_band: the order parameter
+ * moves only inside the interface band, and is left exactly at its bulk
+ * values elsewhere. */
 cno_status cno_apply_update(const float *const *src, float *const *dst, int nfield, int nx, int ny,
-                            const float *out, int out_cs, const float *scale, void *stream);
+                            const float *out, int out_cs, const float *scale, const float *lo, const float *hi,
+                            float phi_band, void *stream);
 
 /* Acceptance checks of a predicted state, FP64 sums in a fixed order over a
  * lattice with walls at y = 0 and y = ny - 1 and periodic x:
  *   out[0] = sum phi,  out[1] = sum chi, chi = clamp((1 + phi) / 2, 0, 1),
  *   out[2] = sum f_s (0 if fs is NULL),
  *   out[3] = sum (1 - phi^2),  out[4] = sum |grad phi| (central differences,
- *   one-sided next to the walls).
+ *   one-sided next to the walls),
+ *   out[5], out[6] = minimum and maximum of T (0 if T is NULL),
+ *   out[7] = sum rho H, the enthalpy of Sec. 2.3 with the mixture rule of the
+ *   volumetric heat capacities: rho H = T (f_s c_s + (chi - f_s) c_l +
+ *   (1 - chi) c_g) + L_l (chi - f_s), f_s clamped to [0, chi], from
+ *   hcoef = {c_l, c_s, c_g, L_l} = {(rho Cp)_l, (rho Cp)_s, (rho Cp)_g, rho_l L}
+ *   (0 if hcoef, fs or T is NULL).
  * The mass of the phase-change material is rho_s out[2] + rho_l (out[1] - out[2]);
  * for a flat profile phi = tanh(2 d / W) the width is W = 2 out[3] / out[4].
  * Synchronises the stream; out is host memory. */
-cno_status cno_field_checks(const float *phi, const float *fs, int nx, int ny, double out[5], void *stream);
+cno_status cno_field_checks(const float *phi, const float *fs, const float *T, const float *hcoef, int nx, int ny,
+                            double out[8], void *stream);
 
 #ifdef __cplusplus
 }

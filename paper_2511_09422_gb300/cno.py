@@ -72,8 +72,8 @@ def load(path: str | None = None):
             "cno_last_output": (i, [vp, C.POINTER(vp)]),
             "cno_pack_fields": (i, [vp, i, i, i, vp, vp, vp, i, vp]),
             "cno_pack_delta": (i, [vp, vp, i, i, i, vp, vp, vp]),
-            "cno_apply_update": (i, [vp, vp, i, i, i, vp, i, vp, vp]),
-            "cno_field_checks": (i, [vp, vp, i, i, C.POINTER(d), vp]),
+            "cno_apply_update": (i, [vp, vp, i, i, i, vp, i, vp, vp, vp, f, vp]),
+            "cno_field_checks": (i, [vp, vp, vp, vp, i, i, C.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -152,6 +152,14 @@ def layer_shapes(cin=CIN, widths=WIDTHS, cout=COUT):
     c0, c1, c2, c3 = widths
     return [(cin, c0), (c0, c0), (c0, c1), (c1, c1), (c1, c2), (c2, c2), (c2, c3), (c3, c3),
             (c3, c1), (c1, c0), (c0, c0), (c0, cout)]
+
+
+def forward_flops(h, w, n=1, cin=CIN, widths=WIDTHS, cout=COUT):
+    """Multiply-add FLOPs (2 per MAC) of the twelve convolutions of one forward
+    pass over n images of h x w."""
+    levels = [0, 0, 1, 1, 2, 2, 3, 3, 2, 1, 0, 0]
+    return sum(2.0 * 9 * ci * co * n * (h >> lv) * (w >> lv)
+               for (ci, co), lv in zip(layer_shapes(cin, widths, cout), levels))
 
 
 def unflatten(flat, cin=CIN, widths=WIDTHS, cout=COUT):
@@ -256,17 +264,24 @@ def pack_delta(cur, nxt, inv_scale, out):
     return out
 
 
-def apply_update(src, dst, out, scale):
-    """dst[f] = src[f] + scale[f] * out[..., f] (device; dst may be src)."""
+def apply_update(src, dst, out, scale, phi_band=0.0, lo=None, hi=None):
+    """dst[f] = clamp(src[f] + scale[f] * out[..., f], lo[f], hi[f]) (device; dst
+    may be src); with phi_band > 0, field 0 changes only where |src[0]| < phi_band."""
     ny, nx = src[0].shape
-    sc = (C.c_float * len(src))(*scale)
-    _check(load().cno_apply_update(_ptr_array(src), _ptr_array(dst), len(src), nx, ny, _ptr(out), out.shape[-1], sc,
-                                   _stream()))
+    n = len(src)
+    sc = (C.c_float * n)(*scale)
+    lo_a = None if lo is None else (C.c_float * n)(*lo)
+    hi_a = None if hi is None else (C.c_float * n)(*hi)
+    _check(load().cno_apply_update(_ptr_array(src), _ptr_array(dst), n, nx, ny, _ptr(out), out.shape[-1], sc, lo_a,
+                                   hi_a, float(phi_band), _stream()))
 
 
-def field_checks(phi, fs=None):
-    """(sum phi, sum chi, sum f_s, sum (1 - phi^2), sum |grad phi|) in FP64 of device fields [ny,nx]."""
+def field_checks(phi, fs=None, T=None, hcoef=None):
+    """(sum phi, sum chi, sum f_s, sum (1 - phi^2), sum |grad phi|, min T, max T,
+    sum rho H) in FP64 of device fields [ny,nx]; hcoef = ((rho Cp)_l, (rho Cp)_s,
+    (rho Cp)_g, rho_l L) for the enthalpy sum."""
     ny, nx = phi.shape
-    out = (C.c_double * 5)()
-    _check(load().cno_field_checks(_ptr(phi), _ptr(fs), nx, ny, out, _stream()))
+    out = (C.c_double * 8)()
+    hc = None if hcoef is None else (C.c_float * 4)(*hcoef)
+    _check(load().cno_field_checks(_ptr(phi), _ptr(fs), _ptr(T), hc, nx, ny, out, _stream()))
     return tuple(out)

@@ -266,8 +266,9 @@ static unsigned grid_for(long long n, int block)
 }
 
 // Tiling of a weight gradient: 64-pixel K blocks (wt x ht pixels of one
-// image), 9 taps x output-channel tiles x input-channel tiles, and enough
-// pixel ranges ("splits") for two CTAs per SM with at least 8 K blocks each.
+// image), 9 taps x output-channel tiles x input-channel tiles, and as many
+// pixel ranges ("splits") as fill one wave of two CTAs per SM, with at least
+// 8 K blocks each.
 static void wgrad_plan(int n, int h, int w, int cin, int cout, cnok::WgradArgs *a, int *bn)
 {
     *bn = pick_bn(cin);
@@ -283,11 +284,19 @@ static void wgrad_plan(int n, int h, int w, int cin, int cout, cnok::WgradArgs *
     a->kb_total = n * a->tiles_w * a->tiles_h;
     a->mtiles = (cout + 127) / 128;
     a->ntiles = cin / *bn;
+    // one wave: at most two CTAs per SM in total
     const int base = 9 * a->mtiles * a->ntiles;
-    int splits = (2 * num_sms() + base - 1) / base;
+    int splits = (2 * num_sms()) / base;
     splits = std::max(1, std::min(splits, a->kb_total / 8));
     a->kb_per_split = (a->kb_total + splits - 1) / splits;
     a->splits = (a->kb_total + a->kb_per_split - 1) / a->kb_per_split;
+}
+
+// Blocks of the bias-gradient first pass: two per SM, at least 256 pixels each.
+static int bias_blocks(int n, int h, int w)
+{
+    const long long npix = (long long)n * h * w;
+    return (int)std::max(1LL, std::min((long long)2 * num_sms(), (npix + 255) / 256));
 }
 
 // FP32 scratch of a weight gradient: the per-range partials of dW, reused for
@@ -297,9 +306,7 @@ static size_t wgrad_scratch_floats(int n, int h, int w, int cin, int cout)
     cnok::WgradArgs a;
     int bn;
     wgrad_plan(n, h, w, cin, cout, &a, &bn);
-    const long long npix = (long long)n * h * w;
-    const long long blocks = (npix + 1023) / 1024;
-    return (size_t)std::max((long long)a.splits * cout * 9 * cin, blocks * cout);
+    return (size_t)std::max((long long)a.splits * cout * 9 * cin, (long long)bias_blocks(n, h, w) * cout);
 }
 
 // Weight gradient into dw (FP32 [cout][9][cin]) and optionally db; `partial`
@@ -334,11 +341,11 @@ static cno_status wgrad_launch(const void *dz, const void *x, int n, int h, int 
         // bias gradient: per-block channel sums, then the blocks in order (the
         // same stream orders this after the weight sum above)
         const long long npix = (long long)n * h * w;
-        const int ppb = 1024;
-        const long long blocks = (npix + ppb - 1) / ppb;
-        cnok::channel_sum_kernel<<<(unsigned)blocks, 64, 0, st>>>((const bf16 *)dz, npix, cout, ppb, partial);
+        const int blocks = bias_blocks(n, h, w);
+        const long long ppb = (npix + blocks - 1) / blocks;
+        cnok::channel_sum_kernel<<<blocks, 256, 0, st>>>((const bf16 *)dz, npix, cout, ppb, partial);
         CK(cudaGetLastError());
-        cnok::sum_partials_kernel<<<grid_for(cout, 256), 256, 0, st>>>(partial, (int)blocks, cout, db);
+        cnok::sum_partials_kernel<<<grid_for(cout, 256), 256, 0, st>>>(partial, blocks, cout, db);
         CK(cudaGetLastError());
     }
     return CNO_OK;
@@ -902,7 +909,7 @@ struct FieldPtrs {
 };
 struct FieldOut {
     float *f[MAXF];
-    float sc[MAXF];
+    float sc[MAXF], lo[MAXF], hi[MAXF];
 };
 
 __global__ void pack_fields_kernel(FieldPtrs fp, int nfield, long long npix, int cin, bf16 *__restrict__ x)
@@ -931,23 +938,31 @@ __global__ void pack_delta_kernel(FieldPtrs cur, FieldPtrs next, int nfield, lon
 }
 
 __global__ void apply_update_kernel(FieldPtrs src, FieldOut dst, int nfield, long long npix,
-                                    const float *__restrict__ out, int out_cs)
+                                    const float *__restrict__ out, int out_cs, float phi_band)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
          p += (long long)gridDim.x * blockDim.x) {
-        for (int k = 0; k < nfield; k++)
-            dst.f[k][p] = src.f[k][p] + dst.sc[k] * out[p * out_cs + k];
+        for (int k = 0; k < nfield; k++) {
+            const float v = src.f[k][p];
+            const bool frozen = dst.sc[k] == 0.0f || (k == 0 && phi_band > 0.0f && fabsf(v) >= phi_band);
+            dst.f[k][p] = frozen ? v : fminf(fmaxf(v + dst.sc[k] * out[p * out_cs + k], dst.lo[k]), dst.hi[k]);
+        }
     }
 }
 
-// per-row sums of phi, chi, f_s, 1 - phi^2, |grad phi| (FP64), one block per row
-constexpr int NCHK = 5;
-__global__ void field_rows_kernel(const float *__restrict__ phi, const float *__restrict__ fs, int nx, int ny,
-                                  double *__restrict__ rows)
+// per-row sums of phi, chi, f_s, 1 - phi^2, |grad phi|, the row's minimum and
+// maximum of T, and the sum of rho H (FP64), one block per row
+constexpr int NCHK = 8;
+struct HCoef {
+    double cl, cs, cg, lat;
+    int on;
+};
+__global__ void field_rows_kernel(const float *__restrict__ phi, const float *__restrict__ fs,
+                                  const float *__restrict__ T, HCoef hc, int nx, int ny, double *__restrict__ rows)
 {
     __shared__ double red[NCHK][256];
     const int y = blockIdx.x;
-    double s[NCHK] = {0, 0, 0, 0, 0};
+    double s[NCHK] = {0, 0, 0, 0, 0, INFINITY, -INFINITY, 0};
     for (int x = threadIdx.x; x < nx; x += blockDim.x) {
         const long long c = (long long)y * nx + x;
         const double f = phi[c];
@@ -967,14 +982,26 @@ __global__ void field_rows_kernel(const float *__restrict__ phi, const float *__
         s[2] += fs ? (double)fs[c] : 0.0;
         s[3] += 1.0 - f * f;
         s[4] += sqrt(gx * gx + gy * gy);
+        const double t = T ? (double)T[c] : 0.0;
+        s[5] = fmin(s[5], t);
+        s[6] = fmax(s[6], t);
+        if (hc.on) {
+            const double chi = fmin(fmax(0.5 * (1.0 + f), 0.0), 1.0);
+            const double sol = fmin(fmax((double)fs[c], 0.0), chi);
+            s[7] += t * (sol * hc.cs + (chi - sol) * hc.cl + (1.0 - chi) * hc.cg) + hc.lat * (chi - sol);
+        }
     }
     for (int k = 0; k < NCHK; k++)
         red[k][threadIdx.x] = s[k];
     __syncthreads();
     for (int st = blockDim.x / 2; st > 0; st >>= 1) {
-        if (threadIdx.x < st)
-            for (int k = 0; k < NCHK; k++)
+        if (threadIdx.x < st) {
+            for (int k = 0; k < 5; k++)
                 red[k][threadIdx.x] += red[k][threadIdx.x + st];
+            red[5][threadIdx.x] = fmin(red[5][threadIdx.x], red[5][threadIdx.x + st]);
+            red[6][threadIdx.x] = fmax(red[6][threadIdx.x], red[6][threadIdx.x + st]);
+            red[7][threadIdx.x] += red[7][threadIdx.x + st];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0)
@@ -1030,7 +1057,8 @@ extern "C" cno_status cno_pack_delta(const float *const *cur, const float *const
 }
 
 extern "C" cno_status cno_apply_update(const float *const *src, float *const *dst, int nfield, int nx, int ny,
-                                       const float *out, int out_cs, const float *scale, void *stream)
+                                       const float *out, int out_cs, const float *scale, const float *lo,
+                                       const float *hi, float phi_band, void *stream)
 {
     if (!src || !dst || !out || !scale || nfield < 1 || nfield > MAXF || out_cs < nfield || nx < 1 || ny < 1)
         return fail(CNO_ERR_INVALID_ARG, "bad update arguments");
@@ -1040,31 +1068,47 @@ extern "C" cno_status cno_apply_update(const float *const *src, float *const *ds
     for (int k = 0; k < MAXF; k++) {
         o.f[k] = k < nfield ? dst[k] : nullptr;
         o.sc[k] = k < nfield ? scale[k] : 0.0f;
+        o.lo[k] = (k < nfield && lo) ? lo[k] : -INFINITY;
+        o.hi[k] = (k < nfield && hi) ? hi[k] : INFINITY;
         if (k < nfield && !dst[k])
             return fail(CNO_ERR_INVALID_ARG, "null field");
     }
     const long long npix = (long long)nx * ny;
-    apply_update_kernel<<<grid_for(npix, 256), 256, 0, (cudaStream_t)stream>>>(a, o, nfield, npix, out, out_cs);
+    apply_update_kernel<<<grid_for(npix, 256), 256, 0, (cudaStream_t)stream>>>(a, o, nfield, npix, out, out_cs,
+                                                                                 phi_band);
     CK(cudaGetLastError());
     return CNO_OK;
 }
 
-extern "C" cno_status cno_field_checks(const float *phi, const float *fs, int nx, int ny, double out[5], void *stream)
+extern "C" cno_status cno_field_checks(const float *phi, const float *fs, const float *T, const float *hcoef,
+                                       int nx, int ny, double out[8], void *stream)
 {
     if (!phi || !out || nx < 1 || ny < 1)
         return fail(CNO_ERR_INVALID_ARG, "bad check arguments");
     double *rows = nullptr;
     CK(cudaMallocAsync(&rows, (size_t)ny * NCHK * sizeof(double), (cudaStream_t)stream));
-    field_rows_kernel<<<ny, 256, 0, (cudaStream_t)stream>>>(phi, fs, nx, ny, rows);
+    HCoef hc = {0, 0, 0, 0, 0};
+    if (hcoef && fs && T)
+        hc = {hcoef[0], hcoef[1], hcoef[2], hcoef[3], 1};
+    field_rows_kernel<<<ny, 256, 0, (cudaStream_t)stream>>>(phi, fs, T, hc, nx, ny, rows);
     CK(cudaGetLastError());
     std::vector<double> h((size_t)ny * NCHK);
     CK(cudaMemcpyAsync(h.data(), rows, h.size() * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CK(cudaFreeAsync(rows, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    for (int k = 0; k < NCHK; k++)
+    for (int k = 0; k < 5; k++)
         out[k] = 0.0;
-    for (int y = 0; y < ny; y++)
-        for (int k = 0; k < NCHK; k++)
+    out[5] = INFINITY;
+    out[6] = -INFINITY;
+    out[7] = 0.0;
+    for (int y = 0; y < ny; y++) {
+        for (int k = 0; k < 5; k++)
             out[k] += h[(size_t)NCHK * y + k];
+        out[5] = std::min(out[5], h[(size_t)NCHK * y + 5]);
+        out[6] = std::max(out[6], h[(size_t)NCHK * y + 6]);
+        out[7] += h[(size_t)NCHK * y + 7];
+    }
+    if (!T)
+        out[5] = out[6] = 0.0;
     return CNO_OK;
 }

@@ -554,37 +554,6 @@ __global__ void __launch_bounds__(192, 1)
     }
 }
 
-// dW[i] = sum over splits s (in order) of partial[s][i]
-__global__ void sum_partials_kernel(const float *__restrict__ partial, int splits, long long count,
-                                    float *__restrict__ out)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int k = 0; k < splits; k++)
-            s += partial[k * count + i];
-        out[i] = s;
-    }
-}
-
-// Bias gradient: per-block channel sums of dz (npix x c, bf16) into
-// partial[block][c]; then the blocks are added in order.
-__global__ void channel_sum_kernel(const bf16 *__restrict__ dz, long long npix, int c, int pix_per_block,
-                                   float *__restrict__ partial)
-{
-    const long long p0 = (long long)blockIdx.x * pix_per_block;
-    const long long p1 = min(npix, p0 + pix_per_block);
-    for (int ch = threadIdx.x; ch < c; ch += blockDim.x) {
-        float s = 0.0f;
-        for (long long p = p0; p < p1; p++)
-            s += __bfloat162float(dz[p * c + ch]);
-        partial[(long long)blockIdx.x * c + ch] = s;
-    }
-}
-
-// --------------------------------------------------------------------------
-// Elementwise kernels on NHWC bf16 tensors, 8 channels (16 bytes) per thread.
-// --------------------------------------------------------------------------
 __device__ __forceinline__ void unpack8(uint4 u, float (&f)[8])
 {
     const __nv_bfloat162 *p = (const __nv_bfloat162 *)&u;
@@ -606,6 +575,60 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8])
     return u;
 }
 
+// dW[i] = sum over splits s (in order) of partial[s][i]
+__global__ void sum_partials_kernel(const float *__restrict__ partial, int splits, long long count,
+                                    float *__restrict__ out)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < splits; k++)
+            s += partial[k * count + i];
+        out[i] = s;
+    }
+}
+
+// Bias gradient, first pass: block b adds dz (npix x c, bf16) over its pixel
+// range [b * ppb, (b + 1) * ppb) per channel into partial[b][c].  Thread t reads
+// 8 channels (16 bytes) of pixel p0 + t / (c / 8) + k * (256 / (c / 8)), so a
+// warp's loads are contiguous; the threads of one channel group are then added
+// in shared memory in a fixed order.
+__global__ void __launch_bounds__(256) channel_sum_kernel(const bf16 *__restrict__ dz, long long npix, int c,
+                                                          long long ppb, float *__restrict__ partial)
+{
+    __shared__ float red[256][9];
+    const int groups = c / 8;                 // 16-byte channel groups (c <= 2048)
+    const int lanes_per_pix = groups;
+    const int pix_step = 256 / lanes_per_pix; // pixels per sweep of the block (>= 1)
+    const int g = threadIdx.x % lanes_per_pix, r = threadIdx.x / lanes_per_pix;
+    const long long p0 = (long long)blockIdx.x * ppb;
+    const long long p1 = min(npix, p0 + ppb);
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (r < pix_step) {
+        for (long long p = p0 + r; p < p1; p += pix_step) {
+            float f[8];
+            unpack8(*(const uint4 *)(dz + p * c + 8 * g), f);
+#pragma unroll
+            for (int e = 0; e < 8; e++)
+                acc[e] += f[e];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; e++)
+        red[threadIdx.x][e] = acc[e];
+    __syncthreads();
+    for (int ch = threadIdx.x; ch < c; ch += 256) {
+        const int gg = ch / 8, e = ch % 8;
+        float sum = 0.0f;
+        for (int rr = 0; rr < pix_step; rr++)
+            sum += red[rr * lanes_per_pix + gg][e];
+        partial[(long long)blockIdx.x * c + ch] = sum;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Elementwise kernels on NHWC bf16 tensors, 8 channels (16 bytes) per thread.
+// --------------------------------------------------------------------------
 // y[n][h][w] = mean of x[n][2h..2h+1][2w..2w+1]; x is n x 2ho x 2wo
 __global__ void pool2_kernel(const bf16 *__restrict__ x, int n, int ho, int wo, int c, bf16 *__restrict__ y)
 {

@@ -81,6 +81,8 @@ def test_pack_delta_update_kernels_match_numpy():
     out = torch.as_tensor(rng.standard_normal((1, ny, nx, 7)).astype(np.float32)).cuda()
     dst = [torch.empty_like(c) for c in cur]
     cno.apply_update(cur, dst, out, isc)
+    band = [torch.empty_like(c) for c in cur]
+    cno.apply_update(cur, band, out, isc, phi_band=0.5)
     torch.cuda.synchronize()
     c = np.stack([a.cpu().numpy() for a in cur], -1)
     n = np.stack([a.cpu().numpy() for a in nxt], -1)
@@ -92,6 +94,25 @@ def test_pack_delta_update_kernels_match_numpy():
     want_u = c.astype(np.float64) + isc.astype(np.float64) * out[0].cpu().numpy().astype(np.float64)
     got_u = np.stack([a.cpu().numpy() for a in dst], -1)
     assert np.all(np.abs(got_u - want_u) <= 2.0 ** -23 * np.abs(want_u) + 1e-30)
+    got_b = np.stack([a.cpu().numpy() for a in band], -1)
+    outside = np.abs(c[..., 0]) >= 0.5
+    assert outside.any() and (~outside).any()
+    assert np.array_equal(got_b[..., 0][outside], c[..., 0][outside])
+    assert np.array_equal(got_b[..., 0][~outside], got_u[..., 0][~outside])
+    assert np.array_equal(got_b[..., 1:], got_u[..., 1:])
+    zero = [torch.empty_like(c) for c in cur]
+    sc0 = isc.copy()
+    sc0[4:] = 0.0
+    cno.apply_update(cur, zero, out, sc0)
+    got_z = np.stack([a.cpu().numpy() for a in zero], -1)
+    assert np.array_equal(got_z[..., 4:], c[..., 4:])          # scale 0: copied
+    assert np.array_equal(got_z[..., :4], got_u[..., :4])
+    clamped = [torch.empty_like(c) for c in cur]
+    lo = [-0.5] * 7
+    hi = [0.25] * 7
+    cno.apply_update(cur, clamped, out, isc, lo=lo, hi=hi)
+    got_c = np.stack([a.cpu().numpy() for a in clamped], -1)
+    assert np.array_equal(got_c, np.clip(got_u, -0.5, 0.25).astype(np.float32))
 
 
 def test_field_checks_match_numpy_and_the_tanh_width():
@@ -100,7 +121,10 @@ def test_field_checks_match_numpy_and_the_tanh_width():
     y = np.arange(ny, dtype=np.float64)[:, None] * np.ones((1, nx))
     phi = np.tanh(2.0 * (40.3 - y) / W.INTERFACE_WIDTH).astype(np.float32)  # flat interface, W = 4
     fs = np.clip(0.5 * (1 + phi), 0, 1).astype(np.float32) * 0.25
-    s = cno.field_checks(torch.as_tensor(phi).cuda(), torch.as_tensor(fs).cuda())
+    Tf = (np.arange(ny * nx, dtype=np.float32).reshape(ny, nx) * 1e-3 - 1.0).astype(np.float32)
+    s = cno.field_checks(torch.as_tensor(phi).cuda(), torch.as_tensor(fs).cuda(), torch.as_tensor(Tf).cuda())
+    assert s[5] == float(Tf.min()) and s[6] == float(Tf.max())
+    s = s[:5]
     p = phi.astype(np.float64)
     gy = np.empty_like(p)
     gy[1:-1] = 0.5 * (p[2:] - p[:-2])
@@ -112,6 +136,22 @@ def test_field_checks_match_numpy_and_the_tanh_width():
     assert np.allclose(s, want, rtol=1e-12, atol=1e-9)
     width = 2.0 * s[3] / s[4]
     assert abs(width - W.INTERFACE_WIDTH) <= 0.03 * W.INTERFACE_WIDTH, width
+
+
+def test_enthalpy_sum_matches_the_lb_reduction():
+    """sum rho H of the check kernel (mixture rule, latent part rho_l L (chi - f_s))
+    on the fields of an LB state equals the LB's own sum of the enthalpy moment."""
+    from paper_2511_09422_gb300 import cno, lbfreeze
+    w = W.parity_droplet(nx=128, ny=96)
+    p = w["params"]
+    s = lbfreeze.Solver(w["grid"], p, _f32(w))
+    s.step(400)
+    F = s.fields(device=True)
+    r = s.reduce()
+    hc = (p["rho_l"] * p["cp_l"], p["rho_s"] * p["cp_s"], p["rho_g"] * p["cp_g"], p["rho_l"] * p["latent"])
+    c = cno.field_checks(F["phi"], F["fs"], F["T"], hc)
+    assert abs(c[7] - r[1]) <= 1e-5 * abs(r[1]), (c[7], r[1])
+    s.close()
 
 
 def _tiny_model(seed=0):
@@ -135,7 +175,7 @@ def test_rejected_jumps_leave_the_lb_result_unchanged():
     for k in FIELDS:
         assert np.array_equal(fa[k], fb[k]), k
     s = st.stats()
-    assert s["accepted"] == 0 and s["rejected"] >= 1 and s["jumps"] == 6
+    assert s["accepted"] == 0 and s["rejected"] >= 1 and s["chunks"] == 6 and s["lb_chunks"] == 6
     assert a.steps == 130
     net.close()
 
@@ -145,7 +185,9 @@ def test_accepted_jump_installs_the_prediction():
     w = W.parity_droplet(nx=128, ny=64)
     net, norm = _tiny_model(seed=1)
     s = lbfreeze.Solver(w["grid"], w["params"], _f32(w))
-    st = surrogate.SurrogateStepper(s, net, norm, w["params"], k=20, mass_tol=1e9, width_tol=1e9)
+    st = surrogate.SurrogateStepper(s, net, norm, w["params"], k=20, mass_tol=1e9, width_tol=1e9, h_tol=1e30,
+                                    slow_only=False)
+    st._lb_chunk(measure=True)   # a fresh enthalpy rate, as before any attempt
     assert st.try_jump()
     got = s.fields(device=True)
     for k in ("phi", "C"):
