@@ -53,13 +53,22 @@ typedef enum {
 /* Lattice and walls (problem statement, Sec. 2, Fig. 1; boundary
  * treatment of Sec. 4.5).  The bottom-wall temperature may vary along x as
  * T_bottom + T_bottom_amp * cos(2 pi T_bottom_modes x / nx) (the heated
- * channel of Sec. 4.1), with cell centres at integer x. */
+ * channel of Sec. 4.1), with cell centres at integer x.
+ * cos_theta_bottom, cos_theta_top: wettability of each wall (Sec. 3.4), the
+ * cosine of the contact angle measured inside the phi = 1 phase, in [-1, 1];
+ * 0 (the zero-initialised value) is 90 degrees.  The wall condition is the
+ * normal derivative of the equilibrium profile at that angle,
+ * n_w . grad phi = -cos(theta) (1 - phi^2) / (sqrt 2 eps), imposed on the
+ * ghost of phi beyond the half-way wall: phi_ghost = phi_adjacent +
+ * cos(theta) (1 - phi_adjacent^2) / (sqrt 2 eps); the density gradient
+ * follows by the linear property rule. */
 typedef struct {
     int nx, ny;             /* 1 <= nx, ny; nx*ny <= LB_MAX_CELLS */
     int bc_bottom, bc_top;  /* LB_WALL_DIRICHLET_T or LB_WALL_ADIABATIC */
     double T_bottom, T_top;
     double T_bottom_amp;
     int T_bottom_modes;
+    double cos_theta_bottom, cos_theta_top;
 } lb_grid;
 
 #define LB_MAX_CELLS (1L << 28)

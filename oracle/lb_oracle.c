@@ -232,8 +232,8 @@ static double T_wall_bottom(const orc_grid *g, double x)
  * linear extrapolation through the wall value: 2 v_w - v_adjacent for a field
  * with a prescribed wall value (the temperature at a Dirichlet wall; the
  * velocity, v_w = 0 at a no-slip wall), and a mirror v_adjacent for a field
- * with zero normal gradient (everything else; for phi this is the
- * 90-degree contact angle). */
+ * with zero normal gradient (everything else; for phi and rho this is the
+ * 90-degree contact angle, other angles are in nb_st below). */
 #define GHOST_MIRROR 0
 #define GHOST_TEMPERATURE 1
 #define GHOST_VELOCITY 2
@@ -258,6 +258,36 @@ static double nb(const orc_grid *g, const double *v, int x, int y, int dx, int d
     return v[(long)yy * g->nx + xx];
 }
 
+/* Wetting (contact angle theta at a wall, Sec. 3.4; the paper cites the
+ * treatment without printing it).  For the equilibrium profile
+ * phi = tanh(2 d / W) = tanh(d / (sqrt 2 eps)) meeting the wall at angle
+ * theta (measured inside the phi = 1 phase), the derivative along the wall
+ * normal n_w pointing into the fluid is
+ *     n_w . grad phi = -cos(theta) (1 - phi^2) / (sqrt 2 eps).
+ * The ghost of phi beyond the half-way wall follows from that derivative
+ * across the half cell on each side of the wall, with phi at the wall taken
+ * as the adjacent value a:  phi_ghost = a + cos(theta) (1 - a^2) / (sqrt 2 eps)
+ * (cos theta = 0 is the mirror, 90 degrees).  The density ghost follows
+ * from the phi ghost by the linear rule: rho_ghost = rho_a + (rho_l - rho_g)/2
+ * (phi_ghost - a).  Other fields keep the ghosts of nb(). */
+#define GHOST_PHI 3
+#define GHOST_RHO 4
+static double nb_st(const orc_state *st, const double *v, int x, int y, int dx, int dy, int kind)
+{
+    const orc_grid *g = &st->g;
+    int yy = y + dy;
+    if ((kind != GHOST_PHI && kind != GHOST_RHO) || (yy >= 0 && yy < g->ny))
+        return nb(g, v, x, y, dx, dy, kind == GHOST_PHI || kind == GHOST_RHO ? GHOST_MIRROR : kind);
+    int xx = ((x + dx) % g->nx + g->nx) % g->nx;
+    int ya = yy < 0 ? 0 : g->ny - 1;
+    double ct = yy < 0 ? g->cos_theta_bottom : g->cos_theta_top;
+    double phi_a = st->phi[(long)ya * g->nx + xx];
+    double dphi = ct * (1.0 - phi_a * phi_a) / (sqrt(2.0) * st->p.eps);
+    double a = v[(long)ya * g->nx + xx];
+    if (kind == GHOST_PHI) return a + dphi;
+    return a + 0.5 * (st->p.rho_l - st->p.rho_g) * dphi;
+}
+
 /* Second-order isotropic schemes (end of Sec. 3.4), dx = dt = 1:
  *   grad z = sum_{i != 0} w_i c_i z(x + c_i) / cs2
  *   lap  z = sum_{i != 0} 2 w_i [z(x + c_i) - z(x)] / cs2                  */
@@ -268,6 +298,23 @@ static void stencil(const orc_grid *g, const double *v, int x, int y, int kind,
     double sx = 0, sy = 0, sl = 0;
     for (int i = 1; i < 9; i++) {
         double zi = nb(g, v, x, y, CX[i], CY[i], kind);
+        sx += WT[i] * CX[i] * zi;
+        sy += WT[i] * CY[i] * zi;
+        sl += 2.0 * WT[i] * (zi - z0);
+    }
+    *gx = sx / CS2;
+    *gy = sy / CS2;
+    if (lap) *lap = sl / CS2;
+}
+
+/* The same schemes with the wetting ghosts of nb_st(). */
+static void stencil_st(const orc_state *st, const double *v, int x, int y, int kind,
+                       double *gx, double *gy, double *lap)
+{
+    double z0 = v[(long)y * st->g.nx + x];
+    double sx = 0, sy = 0, sl = 0;
+    for (int i = 1; i < 9; i++) {
+        double zi = nb_st(st, v, x, y, CX[i], CY[i], kind);
         sx += WT[i] * CX[i] * zi;
         sy += WT[i] * CY[i] * zi;
         sl += 2.0 * WT[i] * (zi - z0);
@@ -435,11 +482,11 @@ static void cell_dynamics(const orc_state *st, int x, int y, cell_out *o)
 
     /* stencils of the current fields and of the lagged p, S */
     double gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, grx, gry, gPx, gPy, gSx, gSy;
-    stencil(g, st->phi, x, y, GHOST_MIRROR, &gpx, &gpy, &lphi);
+    stencil_st(st, st->phi, x, y, GHOST_PHI, &gpx, &gpy, &lphi);
     stencil(g, st->T, x, y, GHOST_TEMPERATURE, &gTx, &gTy, NULL);
     stencil(g, st->C, x, y, GHOST_MIRROR, &gCx, &gCy, NULL);
     stencil(g, st->fs, x, y, GHOST_MIRROR, &gfx, &gfy, NULL);
-    stencil(g, st->rho, x, y, GHOST_MIRROR, &grx, &gry, NULL);
+    stencil_st(st, st->rho, x, y, GHOST_RHO, &grx, &gry, NULL);
     stencil(g, st->p_prev, x, y, GHOST_MIRROR, &gPx, &gPy, NULL);
     stencil(g, st->S_prev, x, y, GHOST_MIRROR, &gSx, &gSy, NULL);
 

@@ -19,6 +19,7 @@ typedef struct {
     double T_bottom, T_top;
     double T_bottom_amp;   /* bottom wall T_bottom + amp cos(2 pi modes x / nx) */
     int T_bottom_modes;
+    double cos_theta_bottom, cos_theta_top; /* wetting: cosine of the contact angle (0: 90 degrees) */
 } orc_grid;
 
 typedef struct {

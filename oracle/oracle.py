@@ -16,7 +16,7 @@ _lib = None
 
 GRID_FIELDS = [("nx", C.c_int), ("ny", C.c_int), ("bc_bottom", C.c_int), ("bc_top", C.c_int),
                ("T_bottom", C.c_double), ("T_top", C.c_double), ("T_bottom_amp", C.c_double),
-               ("T_bottom_modes", C.c_int)]
+               ("T_bottom_modes", C.c_int), ("cos_theta_bottom", C.c_double), ("cos_theta_top", C.c_double)]
 PARAM_FIELDS = [(k, C.c_double) for k in (
     "rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lam_l", "lam_s", "lam_g",
     "cp_l", "cp_s", "cp_g", "latent", "T_sol", "T_liq", "k_p", "D_l", "D_s", "eps", "mobility",

@@ -105,6 +105,8 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
     if ((long)((g->nx + 31) / 32 * 32) * (long)g->ny >= (1L << 31))
         return "padded plane (nx rounded up to 32, times ny) of 2^31 floats or more";
     if (g->bc_bottom < 0 || g->bc_bottom > 1 || g->bc_top < 0 || g->bc_top > 1) return "unknown wall type";
+    if (!(std::fabs(g->cos_theta_bottom) <= 1.0) || !(std::fabs(g->cos_theta_top) <= 1.0))
+        return "cos_theta_bottom and cos_theta_top must lie in [-1, 1]";
     if (!finite_all(p)) return "non-finite parameter";
     if (!(p->eps > 0)) return "eps must be > 0";
     if (!(p->rho_l > 0 && p->rho_s > 0 && p->rho_g > 0)) return "densities must be > 0";
@@ -135,6 +137,8 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.T_top = (real)g->T_top;
     K.T_bottom_amp = (real)g->T_bottom_amp;
     K.wall_k = (real)(2.0 * g->T_bottom_modes / g->nx);
+    K.wet_b = (real)(g->cos_theta_bottom / (std::sqrt(2.0) * p->eps));
+    K.wet_t = (real)(g->cos_theta_top / (std::sqrt(2.0) * p->eps));
     K.rho_l = (real)p->rho_l; K.rho_s = (real)p->rho_s; K.rho_g = (real)p->rho_g;
     K.mu_l = (real)p->mu_l; K.mu_s = (real)p->mu_s; K.mu_g = (real)p->mu_g;
     K.lam_l = (real)p->lam_l; K.lam_s = (real)p->lam_s; K.lam_g = (real)p->lam_g;

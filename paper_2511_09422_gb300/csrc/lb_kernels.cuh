@@ -90,6 +90,7 @@ struct Consts {
     long long plane;          // floats per plane (pitch * ny)
     int bc_bottom, bc_top;
     real T_bottom, T_top, T_bottom_amp, wall_k;  // wall_k = 2 * modes / nx (argument of cospi)
+    real wet_b, wet_t;          // cos(theta) / (sqrt 2 eps) of the bottom and top walls (0: 90 degrees)
     real rho_l, rho_s, rho_g, mu_l, mu_s, mu_g, lam_l, lam_s, lam_g;
     real rcp_l, rcp_s, rcp_g;   // volumetric heat capacities rho*Cp
     real latent_l;              // rho_l * L
@@ -460,7 +461,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // isotropic gradient and Laplacian over the 8 neighbours (order 1..8), from
     // differences z_i - z_0: grad z = 3 sum w_i c_i (z_i - z_0), lap z = 6 sum w_i (z_i - z_0).
     // phi and T differences are split into lagged-value and change parts.  Wall rows
-    // are ghosts: mirror, or 2 T_w - T_adjacent for the temperature at a Dirichlet wall.
+    // are ghosts: mirror, the wetting ghost for phi, or 2 T_w - T_adjacent for the
+    // temperature at a Dirichlet wall.
     real gpx, gpy, lphi, gTx, gTy, gCx, gCy, gfx, gfy, gPx, gPy, gSx, gSy;
     {
         // the six fields run as three packed pairs: (phi, T), (C, f_s), (p, S)
@@ -478,7 +480,13 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             if (!WALLS) {
                 z01 = add2(sub2(pk2(lg), lag0), sub2(pk2(dd), dd0));
             } else {
-                const real zph = (lg.x - phi_p) + (dd.x - dphi);
+                real zph = (lg.x - phi_p) + (dd.x - dphi);
+                if ((at_bottom && cy(i) == -1) || (at_top && cy(i) == 1)) {
+                    // wetting ghost: phi_adj + cos(theta) (1 - phi_adj^2) / (sqrt 2 eps)
+                    const real wet = cy(i) == -1 ? K.wet_b : K.wet_t;
+                    const real pa = lg.x + dd.x;
+                    zph += wet * (R(1.0) - pa * pa);
+                }
                 real zT = (lg.y - T_p) + (dd.y - dT);
                 if ((dir_b && cy(i) == -1) || (dir_t && cy(i) == 1)) {
                     const real Tw = cy(i) == -1 ? wall_T_bottom(K, (real)wrapx(x + cx(i), K.nx)) : K.T_top;

@@ -29,7 +29,7 @@ class LbError(RuntimeError):
 class lb_grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("bc_bottom", C.c_int), ("bc_top", C.c_int),
                 ("T_bottom", C.c_double), ("T_top", C.c_double), ("T_bottom_amp", C.c_double),
-                ("T_bottom_modes", C.c_int)]
+                ("T_bottom_modes", C.c_int), ("cos_theta_bottom", C.c_double), ("cos_theta_top", C.c_double)]
 
 
 _PARAM_DOUBLES = ("rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lam_l", "lam_s", "lam_g",

@@ -59,10 +59,15 @@ def gas_properties(p: dict, rho_g: float, nu: float = 0.1, lam_ratio: float = 0.
 
 
 def grid(nx, ny, bc_bottom=WALL_DIRICHLET_T, bc_top=WALL_ADIABATIC, T_bottom=0.0, T_top=0.0,
-         T_bottom_amp=0.0, T_bottom_modes=1) -> dict:
+         T_bottom_amp=0.0, T_bottom_modes=1, theta_bottom=90.0, theta_top=90.0) -> dict:
+    """Lattice and walls; theta_* are the contact angles in degrees (inside the
+    phi = 1 phase), passed on as their cosines (exactly 0 at 90 degrees)."""
+    def cosd(t):
+        return 0.0 if float(t) == 90.0 else math.cos(math.radians(float(t)))
     return dict(nx=int(nx), ny=int(ny), bc_bottom=int(bc_bottom), bc_top=int(bc_top),
                 T_bottom=float(T_bottom), T_top=float(T_top), T_bottom_amp=float(T_bottom_amp),
-                T_bottom_modes=int(T_bottom_modes))
+                T_bottom_modes=int(T_bottom_modes), cos_theta_bottom=cosd(theta_bottom),
+                cos_theta_top=cosd(theta_top))
 
 
 def tanh_profile(d: np.ndarray, width: float = INTERFACE_WIDTH) -> np.ndarray:
@@ -136,17 +141,21 @@ def thermocapillary_channel(nx=512, ny=256, h=None, T_h=20.0, T_c=10.0, T_0=4.0,
 
 def sessile_droplet(nx=512, ny=512, radius=100.0, rho_ratio=0.9, rho_g=0.001, ste=0.1, c0=0.05,
                     ma_T=10.0, ma_C=10.0, k_p=0.5, D_l=0.05, D_s=0.005, sigma0=0.01,
-                    T_wall=-1.0, lam=0.3, nu=0.1, steps=None, perturb=0.0, seed=0) -> dict:
-    """Binary droplet freezing on a cold substrate (Sec. 4.4): a half-disc of
-    radius R centred on the bottom wall (90-degree contact angle), solute C0 in
-    the droplet, T_0 = T_m = 0, bottom wall Dirichlet T_wall, top adiabatic.
+                    T_wall=-1.0, lam=0.3, nu=0.1, steps=None, perturb=0.0, seed=0, theta=90.0) -> dict:
+    """Binary droplet freezing on a cold substrate (Sec. 4.4): a circular cap of
+    radius R on the bottom wall with contact angle theta (degrees; 90 is the
+    half-disc centred on the wall, the only angle of the paper's Sec. 4.4 case),
+    solute C0 in the droplet, T_0 = T_m = 0, bottom wall Dirichlet T_wall with
+    that wettability, top adiabatic.
     Thermal Marangoni: |sigma_T| from Ma_T = |sigma_T| (T_m - T_w) R / (mu_l alpha_l);
     solutal: |sigma_c| from Ma_C = |sigma_c| C0 R / (mu_l D_l); sigma falls with T
     and with C (Sec. 4.4).  ``perturb`` adds seeded uniform noise of that
     amplitude to T everywhere (upwards, so that no cell starts below T_m) and
     to C inside the droplet."""
     x, y = _coords(nx, ny)
-    xc, yc = nx / 2.0, -0.5
+    # the wall is at y = -1/2; the centre of a cap with contact angle theta lies
+    # R cos(theta) below it
+    xc, yc = nx / 2.0, -0.5 - (0.0 if theta == 90.0 else radius * math.cos(math.radians(theta)))
     d = radius - np.sqrt((x - xc) ** 2 + (y - yc) ** 2)
     phi = tanh_profile(d)
     T = np.zeros_like(phi)
@@ -162,10 +171,10 @@ def sessile_droplet(nx=512, ny=512, radius=100.0, rho_ratio=0.9, rho_g=0.001, st
     alpha_l = p["lam_l"] / (p["rho_l"] * p["cp_l"])
     p["sigma_T"] = -ma_T * p["mu_l"] * alpha_l / ((0.0 - T_wall) * radius) if ma_T else 0.0
     p["sigma_c"] = -ma_C * p["mu_l"] * D_l / (c0 * radius) if (ma_C and c0) else 0.0
-    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_ADIABATIC, T_bottom=T_wall)
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_ADIABATIC, T_bottom=T_wall, theta_bottom=theta)
     return dict(name="sessile_droplet_%dx%d" % (nx, ny), grid=g, params=p,
                 fields=_fields(phi, T, C), steps=steps,
-                meta=dict(radius=radius, ste=ste, c0=c0, ma_T=ma_T, ma_C=ma_C))
+                meta=dict(radius=radius, ste=ste, c0=c0, ma_T=ma_T, ma_C=ma_C, theta=theta))
 
 
 def parity_droplet(nx=128, ny=128, rho_g=0.1, seed=0, steps=100) -> dict:
@@ -222,14 +231,31 @@ def static_droplet(nx=96, ny=96, radius=20.0, sigma=0.01, rho_g=1.0, steps=4000)
                 fields=_fields(phi, T, C), steps=steps, meta=dict(radius=radius, sigma=sigma))
 
 
-def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, steps=1000) -> list:
+def wetting_droplet(nx=80, ny=40, radius=16.0, theta_wall=60.0, theta0=90.0, sigma=0.01, steps=6000) -> dict:
+    """A droplet relaxing on a wall of contact angle theta_wall from a circular
+    cap of angle theta0: equal densities, no phase change, no solute, uniform
+    temperature, adiabatic walls; its equilibrium is a circular cap of angle
+    theta_wall (no gravity)."""
+    x, y = _coords(nx, ny)
+    yc = -0.5 - (0.0 if theta0 == 90.0 else radius * math.cos(math.radians(theta0)))
+    d = radius - np.sqrt((x - nx / 2.0) ** 2 + (y - yc) ** 2)
+    phi = tanh_profile(d)
+    z = np.zeros_like(phi)
+    p = base_params(sigma0=sigma, phase_change_on=0, latent=0.0)
+    p = gas_properties(p, 1.0, lam_ratio=1.0)
+    g = grid(nx, ny, WALL_ADIABATIC, WALL_ADIABATIC, theta_bottom=theta_wall)
+    return dict(name="wetting_droplet_%dx%d_%g" % (nx, ny, theta_wall), grid=g, params=p, fields=_fields(phi, z, z),
+                steps=steps, meta=dict(radius=radius, theta_wall=theta_wall, theta0=theta0))
+
+
+def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, steps=1000,
+                  theta_range=(60.0, 120.0)) -> list:
     """A parameter sweep of independent freezing sessile droplets (the batched
     workload): square lattices with side uniform in [side_min, side_max],
     radius uniform in [0.2, 0.35] of the side, Stefan number uniform in
     [0.05, 0.5], Ma_T = Ma_C uniform in [0, 50], initial solute uniform in
-    [0, 0.1], all drawn from numpy's default_rng(seed).  Contact angle 90
-    degrees for all (the only wetting condition implemented), gas density
-    ratio 0.1."""
+    [0, 0.1], contact angle uniform in theta_range (degrees; None keeps 90),
+    all drawn from numpy's default_rng(seed); gas density ratio 0.1."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -238,7 +264,9 @@ def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, s
         ste = float(rng.uniform(0.05, 0.5))
         ma = float(rng.uniform(0.0, 50.0))
         c0 = float(rng.uniform(0.0, 0.1))
-        w = sessile_droplet(nx=side, ny=side, radius=radius, rho_g=rho_g, ste=ste, c0=c0, ma_T=ma, ma_C=ma)
+        theta = 90.0 if theta_range is None else float(rng.uniform(*theta_range))
+        w = sessile_droplet(nx=side, ny=side, radius=radius, rho_g=rho_g, ste=ste, c0=c0, ma_T=ma, ma_C=ma,
+                            theta=theta)
         w["name"] = "sweep_%03d_%d" % (i, side)
         w["steps"] = steps
         w["meta"].update(side=side)
@@ -246,7 +274,36 @@ def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, s
     return out
 
 
+def thermocapillary_migration(radius=20.0, T_c=0.0, T_h=32.0, sigma0=2.5e-3, sigma_T=-1e-4, mu=0.2, lam=0.2,
+                              steps=None) -> dict:
+    """Droplet migration driven by a surface-tension gradient (Sec. 4.1, first
+    benchmark): a droplet of radius R at the centre of an 8R x 16R box, equal
+    density, heat capacity, viscosity and conductivity in both phases, walls at
+    T_c (bottom) and T_h (top) with the linear profile between them,
+    sigma = sigma0 + sigma_T (T - T_c), no phase change and no solute.  The
+    steady migration velocity of Young, Goldstein and Block for these values is
+    U_YGB = 2 U / ((2 + 3 mu_l/mu_h)(2 + alpha_l/alpha_h)) with
+    U = -sigma_T grad T R / mu_h (R = 20: 1.333e-4)."""
+    nx, ny = int(round(8 * radius)), int(round(16 * radius))
+    x, y = _coords(nx, ny)
+    d = radius - np.sqrt((x - (nx - 1) / 2.0) ** 2 + (y - (ny - 1) / 2.0) ** 2)
+    phi = tanh_profile(d)
+    # linear profile between the walls at y = -1/2 (T_c) and y = ny - 1/2 (T_h)
+    T = T_c + (T_h - T_c) * (y + 0.5) / ny
+    C = np.zeros_like(phi)
+    p = base_params(mu_l=mu, mu_s=mu, mu_g=mu, lam_l=lam, lam_s=lam, lam_g=lam, sigma0=sigma0, sigma_T=sigma_T,
+                    T_ref=T_c, phase_change_on=0, latent=0.0)
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_DIRICHLET_T, T_bottom=T_c, T_top=T_h)
+    grad_T = (T_h - T_c) / ny
+    U = -sigma_T * grad_T * radius / mu
+    u_ygb = 2.0 * U / ((2.0 + 3.0) * (2.0 + 1.0))
+    return dict(name="thermocapillary_migration_%dx%d" % (nx, ny), grid=g, params=p, fields=_fields(phi, T, C),
+                steps=steps, meta=dict(radius=radius, grad_T=grad_T, U=U, U_YGB=u_ygb))
+
+
 WORKLOADS = {
+    "thermocapillary_migration": thermocapillary_migration,
+    "wetting_droplet": wetting_droplet,
     "stefan_layer": stefan_layer,
     "thermocapillary_channel": thermocapillary_channel,
     "sessile_droplet": sessile_droplet,

@@ -118,3 +118,33 @@ def ygb_velocity(sigma_T, gradT, R, mu_h, mu_l, alpha_l, alpha_h):
     """Young-Goldstein-Block migration speed (Sec. 4.1)."""
     U = -sigma_T * gradT * R / mu_h
     return 2.0 * U / ((2.0 + 3.0 * mu_l / mu_h) * (2.0 + alpha_l / alpha_h))
+
+
+def contact_angle_bottom(phi):
+    """Contact angle (degrees, inside the phi > 0 phase) of a droplet sitting on
+    the bottom wall (at y = -1/2), from a least-squares circle through the
+    phi = 0 contour: for a circular cap of radius R centred at height y_c,
+    cos(theta) = (-1/2 - y_c) / R.  Contour points are the linear-interpolation
+    crossings along rows (both sides) and along columns (top side)."""
+    import numpy as _np
+    ny, nx = phi.shape
+    pts = []
+    for y in range(ny):
+        row = phi[y]
+        for x in range(nx - 1):
+            a, b = row[x], row[x + 1]
+            if (a > 0) != (b > 0):
+                pts.append((x + a / (a - b), y))
+    for x in range(nx):
+        col = phi[:, x]
+        for y in range(ny - 1):
+            a, b = col[y], col[y + 1]
+            if (a > 0) != (b > 0):
+                pts.append((x, y + a / (a - b)))
+    P = _np.array(pts, dtype=_np.float64)
+    A = _np.column_stack([P[:, 0], P[:, 1], _np.ones(len(P))])
+    rhs = -(P[:, 0] ** 2 + P[:, 1] ** 2)
+    (D, E, F), *_ = _np.linalg.lstsq(A, rhs, rcond=None)
+    xc, yc = -D / 2.0, -E / 2.0
+    R = math.sqrt(xc * xc + yc * yc - F)
+    return math.degrees(math.acos(max(-1.0, min(1.0, (-0.5 - yc) / R)))), R, (xc, yc)

@@ -1,0 +1,59 @@
+"""Pins of the oracle's wetting condition (contact angle at a wall) against
+geometry: a two-dimensional droplet without gravity relaxes to a circular cap,
+and the cap's contact angle is fixed by the circle alone (cos theta = distance
+from the wall to the centre over the radius).  Starting from the half-disc
+(90 degrees), the oracle's droplet must settle at the wall's angle; a 90-degree
+wall must leave the half-disc where it is; and the ghost rule's sign and
+coefficient match the derivative of the tanh profile at the contact line."""
+import math
+
+import numpy as np
+import pytest
+
+import analytic
+import oracle
+from paper_2511_09422_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    oracle.build_oracle()
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_droplet_relaxes_to_the_wall_contact_angle(theta):
+    w = W.wetting_droplet(theta_wall=theta)
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.step(9000)
+    got, radius, _ = analytic.contact_angle_bottom(o.fields()["phi"])
+    assert abs(got - theta) <= 2.0, (theta, got)
+    # mass of the droplet is conserved while it spreads or beads up
+    assert abs(o.reduce()[0] - float(np.sum(w["fields"]["phi"]))) <= 1e-9 * w["fields"]["phi"].size
+
+
+def test_ninety_degree_wall_keeps_the_half_disc():
+    w = W.wetting_droplet(theta_wall=90.0)
+    assert w["grid"]["cos_theta_bottom"] == 0.0
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.step(3000)
+    got, _, _ = analytic.contact_angle_bottom(o.fields()["phi"])
+    assert abs(got - 90.0) <= 0.2, got
+
+
+def test_ghost_rule_matches_the_tanh_profile_at_the_wall():
+    """phi = tanh(d / (sqrt 2 eps)) for a straight interface through the contact
+    point at angle theta (inside phi > 0): its normal derivative at the wall
+    equals -cos(theta) (1 - phi^2) / (sqrt 2 eps), the rule the ghost encodes."""
+    eps = W.EPS
+    for theta in (30.0, 60.0, 120.0, 150.0):
+        th = math.radians(theta)
+        m = (math.sin(th), -math.cos(th))  # unit normal into the phi > 0 wedge
+
+        def phi(x, y):
+            return math.tanh((x * m[0] + y * m[1]) / (math.sqrt(2.0) * eps))
+
+        for x in (-2.0, -0.7, 0.0, 0.9, 2.5):
+            h = 1e-5
+            dn = (phi(x, h) - phi(x, -h)) / (2 * h)  # wall normal +y, wall at y = 0
+            p = phi(x, 0.0)
+            assert abs(dn - (-math.cos(th) * (1 - p * p) / (math.sqrt(2.0) * eps))) <= 1e-8
