@@ -292,6 +292,39 @@ def _surrogate_leg(args, torch, peaks):
     }
 
 
+def run_forward_only(args):
+    """The surrogate's forward pass alone: 12 tensor-core convolutions and the
+    pooling / upsampling kernels on one size x size image."""
+    import numpy as np
+    import torch
+
+    from paper_2511_09422_gb300 import cno
+    from paper_2511_09422_gb300 import surrogate as S
+    net = cno.Net()
+    net.set_params(S.init_params(0))
+    rng = np.random.default_rng(0)
+    x = torch.as_tensor(rng.standard_normal((1, args.size, args.size, cno.CIN)).astype(np.float32)).cuda()
+    x = x.to(torch.bfloat16)
+    out = torch.empty((1, args.size, args.size, cno.NF), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(x, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        net.forward(x, out=out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = cno.forward_flops(args.size, args.size)
+    peak = _peaks()[0].get("bf16_tflops")
+    print(json.dumps({"metric": "surrogate forward TFLOP/s", "value": round(flops / (ms * 1e-3) / 1e12, 1),
+                      "unit": "TFLOP/s", "ms": round(ms, 4), "size": args.size, "flops": flops,
+                      "frac_of_bf16_peak": round(flops / (ms * 1e-3) / 1e12 / peak, 4) if peak else None,
+                      "status": cno.read_status()}))
+    net.close()
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -427,9 +460,14 @@ def main():
     ap.add_argument("--sur-iters", type=int, default=3000, help="surrogate training iterations (0: skip the leg)")
     ap.add_argument("--sur-lattices", type=int, default=48, help="LB trajectories the surrogate is trained on")
     ap.add_argument("--sur-steps", type=int, default=12000, help="LB steps per training trajectory")
+    ap.add_argument("--sur-forward-only", action="store_true",
+                    help="time only the surrogate network's forward pass on a size x size lattice (He-normal "
+                         "weights, random input) and print one JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sur_forward_only:
+        run_forward_only(args)
     else:
         run_gpu(args)
 
