@@ -185,7 +185,9 @@ static cno_status launch_fprop_bn(const CUtensorMap &mx, const CUtensorMap &mw, 
         CK(cudaFuncSetAttribute(cnok::conv_fprop_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
         attr = true;
     }
-    dim3 grid(tiles, a.cout / BN);
+    // persistent: at most the CTAs that fit on the SMs at once
+    const int ctas = std::min(tiles, S::CTAS_PER_SM * num_sms());
+    dim3 grid(ctas, a.cout / BN);
     cnok::conv_fprop_kernel<BN><<<grid, 192, S::SMEM, st>>>(mx, mw, a);
     CK(cudaGetLastError());
     return CNO_OK;
@@ -224,6 +226,7 @@ static cno_status conv_launch(const void *in, int n, int h, int w, int cin, cons
     a.tiles_h = (h + ht - 1) / ht;
     a.cblocks = cin / 64;
     a.kblocks = 9 * a.cblocks;
+    a.tiles = (int)std::min<long long>((long long)n * a.tiles_w * a.tiles_h, 0x7fffffffLL);
     a.epi = epi;
     a.bias = bias;
     a.slope_src = (const bf16 *)slope_src;

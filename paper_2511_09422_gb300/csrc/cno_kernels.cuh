@@ -197,18 +197,21 @@ __device__ __forceinline__ float lrelu_slope(float y) { return y > 0.0f ? 1.0f :
 // --------------------------------------------------------------------------
 // Convolution forward and data gradient: D[pixel][o] = sum_k A[pixel][k] B[o][k]
 // with k = (tap, input channel), A gathered by TMA from the shifted input
-// (zero fill outside the image), B the weight matrix.  One CTA computes a tile
-// of 128 pixels (wt x ht of one image) by BN output channels.
+// (zero fill outside the image), B the weight matrix.  A tile is 128 pixels
+// (wt x ht of one image) by BN output channels.
 //
-// Warp roles (6 warps): warp 0 lane 0 issues the TMA loads, warp 1 owns the
-// tensor memory and its lane 0 issues the MMAs, warps 2-5 run the epilogue,
-// warp w reading tensor-memory lanes 32 (w % 4) ... 32 (w % 4) + 31.
+// Persistent: each CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// Warp roles (6 warps): warp 0 lane 0 issues the TMA loads into a ring of
+// stages, warp 1 owns the tensor memory and its lane 0 issues the MMAs, warps
+// 2-5 run the epilogue, warp w reading tensor-memory lanes 32 (w % 4) ...
+// 32 (w % 4) + 31.  Two accumulators in tensor memory alternate between tiles,
+// so the epilogue of one tile overlaps the main loop of the next.
 // --------------------------------------------------------------------------
 enum { EPI_BIAS = 0, EPI_BIAS_LRELU = 1, EPI_SLOPE = 2, EPI_PLAIN = 3 };
 
 struct ConvArgs {
     int n, h, w, cin, cout;
-    int wt, ht, tiles_w, tiles_h;
+    int wt, ht, tiles_w, tiles_h, tiles;
     int kblocks, cblocks;
     int epi;
     const float *bias;          // EPI_BIAS*
@@ -223,10 +226,19 @@ struct ConvShape {
     static constexpr int A_BYTES = BM * ROW_BYTES;
     static constexpr int B_BYTES = BN * ROW_BYTES;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int STAGES = (96 * 1024 / STAGE) < 2 ? 2 : (96 * 1024 / STAGE);
-    static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    // BN <= 128: two CTAs per SM, about 96 KB of stages each; BN = 256: one CTA
+    // per SM (its two accumulators fill the 512 tensor-memory columns), 4 stages
+    static constexpr int CTAS_PER_SM = BN >= 256 ? 1 : 2;
+    static constexpr int STAGES = BN >= 256 ? 4 : ((96 * 1024 / STAGE) < 2 ? 2 : (96 * 1024 / STAGE));
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + BAR_BYTES + BN * 4 /* bias */;
+    static constexpr int TMEM_COLS = 2 * BN;  // two FP32 accumulators
 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 template <int BN>
 __global__ void __launch_bounds__(192, 1)
@@ -238,31 +250,34 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + S::STAGES * S::STAGE);
     uint64_t *empty = full + S::STAGES;
-    uint64_t *done = empty + S::STAGES;
-    uint32_t *tmem_holder = (uint32_t *)(done + 1);
+    uint64_t *acc_full = empty + S::STAGES;  // [2]: the MMAs of a tile are done
+    uint64_t *acc_empty = acc_full + 2;      // [2]: the epilogue has read the accumulator
+    uint32_t *tmem_holder = (uint32_t *)(acc_empty + 2);
     volatile int *abort_flag = (volatile int *)(tmem_holder + 1);
+    float *sbias = (float *)(smem + S::STAGES * S::STAGE + S::BAR_BYTES);
 
     if (*(volatile unsigned *)a.status != 0u)
         return;  // an earlier launch failed: leave the output untouched
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int tile = blockIdx.x;
-    const int tw = tile % a.tiles_w;
-    tile /= a.tiles_w;
-    const int th = tile % a.tiles_h;
-    const int img = tile / a.tiles_h;
-    const int w0 = tw * a.wt, h0 = th * a.ht;
     const int n0 = blockIdx.y * BN;
+    const bool has_bias = a.epi == EPI_BIAS || a.epi == EPI_BIAS_LRELU;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S::STAGES; s++) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+        }
         *abort_flag = 0;
         fence_barrier_init();
     }
+    if (warp >= 2 && has_bias)
+        for (int c = threadIdx.x - 64; c < BN; c += 128)
+            sbias[c] = a.bias[n0 + c];
     if (warp == 1)
         tmem_alloc(tmem_holder, S::TMEM_COLS);
     tc_fence_before();
@@ -271,69 +286,104 @@ __global__ void __launch_bounds__(192, 1)
     const uint32_t tmem = *tmem_holder;
 
     if (warp == 0 && lane == 0) {
-        for (int kb = 0; kb < a.kblocks && !*abort_flag; kb++) {
-            const int s = kb % S::STAGES, it = kb / S::STAGES;
-            if (kb >= S::STAGES && !mbar_wait(&empty[s], (it - 1) & 1, a.status)) {
-                atomicOr(a.status, ST_TIMEOUT_PRODUCER);
-                *abort_flag = 1;
-                break;
+        // producer: the stage ring runs on across tiles
+        uint32_t kc = 0;
+        for (int tile = blockIdx.x; tile < a.tiles && !*abort_flag; tile += gridDim.x) {
+            int t = tile;
+            const int tw = t % a.tiles_w;
+            t /= a.tiles_w;
+            const int th = t % a.tiles_h;
+            const int img = t / a.tiles_h;
+            const int w0 = tw * a.wt, h0 = th * a.ht;
+            for (int kb = 0; kb < a.kblocks; kb++, kc++) {
+                const int s = kc % S::STAGES;
+                const uint32_t use = kc / S::STAGES;
+                if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1, a.status)) {
+                    atomicOr(a.status, ST_TIMEOUT_PRODUCER);
+                    *abort_flag = 1;
+                    break;
+                }
+                const int tap = kb / a.cblocks, cb = kb - tap * a.cblocks;
+                const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+                uint8_t *sa = smem + s * S::STAGE;
+                mbar_expect_tx(&full[s], S::STAGE);
+                tma_load_4d(sa, &map_x, &full[s], cb * KB, w0 + dx, h0 + dy, img);
+                tma_load_2d(sa + S::A_BYTES, &map_w, &full[s], kb * KB, n0);
             }
-            const int tap = kb / a.cblocks, cb = kb - tap * a.cblocks;
-            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-            uint8_t *sa = smem + s * S::STAGE;
-            mbar_expect_tx(&full[s], S::STAGE);
-            tma_load_4d(sa, &map_x, &full[s], cb * KB, w0 + dx, h0 + dy, img);
-            tma_load_2d(sa + S::A_BYTES, &map_w, &full[s], kb * KB, n0);
         }
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = idesc_bf16(BM, BN, 0, 0);
-        bool ok = true;
-        for (int kb = 0; kb < a.kblocks; kb++) {
-            const int s = kb % S::STAGES, it = kb / S::STAGES;
-            if (*abort_flag || !mbar_wait(&full[s], it & 1, a.status)) {
+        uint32_t kc = 0;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, it++) {
+            const int acc = it & 1, use = it >> 1;
+            if (*abort_flag || (use > 0 && !mbar_wait(&acc_empty[acc], (use - 1) & 1, a.status))) {
                 atomicOr(a.status, ST_TIMEOUT_MMA);
                 *abort_flag = 1;
-                ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * S::STAGE);
-            const uint32_t sb = sa + S::A_BYTES;
+            const uint32_t dt = tmem + (uint32_t)(acc * BN);
+            bool ok = true;
+            for (int kb = 0; kb < a.kblocks; kb++, kc++) {
+                const int s = kc % S::STAGES;
+                if (*abort_flag || !mbar_wait(&full[s], (kc / S::STAGES) & 1, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + s * S::STAGE);
+                const uint32_t sb = sa + S::A_BYTES;
 #pragma unroll
-            for (int k = 0; k < KB / 16; k++) {
-                // K-major, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B
-                // apart; the k-th 16-element slice starts 32 B further in.
-                const uint64_t ad = sw128_desc(sa + 32 * k, 16, 1024);
-                const uint64_t bd = sw128_desc(sb + 32 * k, 16, 1024);
-                umma_bf16(tmem, ad, bd, idesc, (kb | k) != 0);
+                for (int k = 0; k < KB / 16; k++) {
+                    // K-major, 128-byte swizzle: rows 128 B apart, 8-row groups 1024 B
+                    // apart; the k-th 16-element slice starts 32 B further in.
+                    const uint64_t ad = sw128_desc(sa + 32 * k, 16, 1024);
+                    const uint64_t bd = sw128_desc(sb + 32 * k, 16, 1024);
+                    umma_bf16(dt, ad, bd, idesc, (kb | k) != 0);
+                }
+                umma_commit(&empty[s]);
             }
-            umma_commit(&empty[s]);
+            if (!ok) {
+                atomicOr(a.status, ST_TIMEOUT_MMA);
+                *abort_flag = 1;
+                break;
+            }
+            umma_commit(&acc_full[acc]);
         }
-        if (ok)
-            umma_commit(done);
     } else if (warp >= 2) {
         const int q = warp & 3;
         const int r = 32 * q + lane;
-        const int px = w0 + r % a.wt, py = h0 + r / a.wt;
-        const bool valid = px < a.w && py < a.h;
-        const long long pix = ((long long)img * a.h + py) * a.w + px;
-        // the tensor-memory loads are warp-collective: take the decision per warp
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, a.status));
-        if (!ok) {
-            if (lane == 0)
-                atomicOr(a.status, ST_TIMEOUT_EPILOGUE);
-        } else {
+        int it = 0;
+        for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x, it++) {
+            const int acc = it & 1, use = it >> 1;
+            // the tensor-memory loads are warp-collective: take the decision per warp
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[acc], use & 1, a.status));
+            if (!ok) {
+                if (lane == 0)
+                    atomicOr(a.status, ST_TIMEOUT_EPILOGUE);
+                break;
+            }
             tc_fence_after();
+            int t = tile;
+            const int tw = t % a.tiles_w;
+            t /= a.tiles_w;
+            const int th = t % a.tiles_h;
+            const int img = t / a.tiles_h;
+            const int px = tw * a.wt + r % a.wt, py = th * a.ht + r / a.wt;
+            const bool valid = px < a.w && py < a.h;
+            const long long pix = ((long long)img * a.h + py) * a.w + px;
+#pragma unroll 1
             for (int c0 = 0; c0 < BN; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + c0), v);
                 const int oc = n0 + c0;
                 if (!valid || oc >= a.n_store)
                     continue;
-                if (a.epi == EPI_BIAS || a.epi == EPI_BIAS_LRELU) {
+                if (has_bias) {
 #pragma unroll
                     for (int i = 0; i < 32; i++) {
-                        float z = v[i] + __ldg(&a.bias[oc + i]);
+                        const float z = v[i] + sbias[c0 + i];
                         v[i] = a.epi == EPI_BIAS_LRELU ? lrelu(z) : z;
                     }
                 } else if (a.epi == EPI_SLOPE) {
@@ -355,8 +405,10 @@ __global__ void __launch_bounds__(192, 1)
                         for (int j = 0; j < 8; j++)
                             ((float4 *)o)[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                     } else {
-                        for (int i = 0; i < nst; i++)
-                            o[i] = v[i];
+#pragma unroll
+                        for (int i = 0; i < 32; i++)
+                            if (i < nst)
+                                o[i] = v[i];
                     }
                 } else {
                     bf16 *o = (bf16 *)a.out + pix * a.out_cs + oc;
@@ -371,11 +423,18 @@ __global__ void __launch_bounds__(192, 1)
                             ((uint4 *)o)[j] = u;
                         }
                     } else {
-                        for (int i = 0; i < nst; i++)
-                            o[i] = __float2bfloat16_rn(v[i]);
+#pragma unroll
+                        for (int i = 0; i < 32; i++)
+                            if (i < nst)
+                                o[i] = __float2bfloat16_rn(v[i]);
                     }
                 }
             }
+            // the accumulator is read: hand it back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&acc_empty[acc]);
         }
     }
     tc_fence_before();
