@@ -255,10 +255,12 @@ def _surrogate_leg(args, torch, peaks):
     from paper_2511_09422_gb300 import workloads as W
     net, norm, info = S.train_default(n_instances=args.sur_lattices, steps=args.sur_steps, iters=args.sur_iters)
     big = W.impurity_front(nx=args.size, ny=args.size, radius=200.0 * args.size / 4096.0)
-    cmp = S.compare(big, net, norm, steps=500)
+    cmp = S.compare(big, net, norm, steps=1000)
+    cmp_p = S.compare(big, net, norm, steps=1000, h_project=True)
     held = S.training_workloads(args.sur_lattices, 256)[info["holdout"][0]]
     tf_lb, dt_lb, _ = S.freezing_time(held)
     tf_s, dt_s, st_s = S.freezing_time(held, net, norm)
+    tf_p, dt_p, st_p = S.freezing_time(held, net, norm, h_project=True)
     # forward pass of the network on the large lattice, timed with CUDA events
     x = torch.zeros((1, args.size, args.size, cno.CIN), dtype=torch.bfloat16, device="cuda")
     out = torch.empty((1, args.size, args.size, cno.NF), dtype=torch.float32, device="cuda")
@@ -275,16 +277,23 @@ def _surrogate_leg(args, torch, peaks):
     tflops = flops / (fwd_ms * 1e-3) / 1e12
     peak_tf = peaks.get("bf16_tflops")
     net.close()
-    lb, su = cmp["lb"], cmp["surrogate"]
+    lb, su, sp = cmp["lb"], cmp["surrogate"], cmp_p["surrogate"]
     return {
-        "metric": "LB-step equivalents/s on impurity_front %dx%d with surrogate jumps of %d steps (500 steps)"
+        "metric": "LB-step equivalents/s on impurity_front %dx%d with surrogate jumps of %d steps (1000 steps)"
                   % (args.size, args.size, S.K_JUMP),
         "value": round(su["steps_per_s"], 1), "lb_alone": round(lb["steps_per_s"], 1),
         "speedup": round(su["steps_per_s"] / lb["steps_per_s"], 3), "stepper": su["stats"],
         "front_rel_diff": cmp["front_rel_diff"], "solid_rel_diff": cmp["solid_rel_diff"],
+        "with_enthalpy_projection": {
+            "value": round(sp["steps_per_s"], 1), "lb_alone": round(cmp_p["lb"]["steps_per_s"], 1),
+            "speedup": round(sp["steps_per_s"] / cmp_p["lb"]["steps_per_s"], 3), "stepper": sp["stats"],
+            "front_rel_diff": cmp_p["front_rel_diff"], "solid_rel_diff": cmp_p["solid_rel_diff"]},
         "freezing_time_heldout_droplet": {"lb": round(tf_lb, 1), "surrogate": round(tf_s, 1),
                                           "rel_error": abs(tf_s - tf_lb) / tf_lb, "lb_s": round(dt_lb, 3),
-                                          "surrogate_s": round(dt_s, 3), "stepper": st_s},
+                                          "surrogate_s": round(dt_s, 3), "stepper": st_s,
+                                          "with_enthalpy_projection": {
+                                              "t_f": round(tf_p, 1), "rel_error": abs(tf_p - tf_lb) / tf_lb,
+                                              "s": round(dt_p, 3), "stepper": st_p}},
         "training": info,
         "forward": {"ms": round(fwd_ms, 3), "tflops": round(tflops, 1), "flops": flops,
                     "frac_of_bf16_peak": round(tflops / peak_tf, 4) if peak_tf else None,

@@ -19,6 +19,10 @@ state it started from (both computed by ``cno.field_checks`` in FP64):
 * enthalpy balance (Sec. 2.3): the change of sum rho H over the jump equals
   the rate measured on the last LB chunk times K_JUMP within ``h_tol``.
 
+With ``h_project`` the predicted change of f_s is first rescaled so that the
+enthalpy balance holds (see ``_project_enthalpy``); the check then only
+catches what the rescaling cannot fix (clamping).
+
 The predicted change of phi is applied only inside the interface band
 (|phi| < phi_band, 0.999 by default): away from the interface the order
 parameter sits at its bulk values +-1 and the method keeps it there, while
@@ -233,7 +237,7 @@ class SurrogateStepper:
 
     def __init__(self, solver: lbfreeze.Solver, net: cno.Net, norm: Normaliser, params: dict, k=K_JUMP,
                  mass_tol=1e-3, width_tol=0.05, h_tol=0.1, jumps_per_lb=2, max_backoff=64, phi_band=0.999,
-                 slow_only=True):
+                 slow_only=True, h_project=False):
         import torch
         self.s, self.net, self.norm, self.k = solver, net, norm, k
         self.rho_s, self.rho_l = float(params["rho_s"]), float(params["rho_l"])
@@ -242,10 +246,11 @@ class SurrogateStepper:
                       float(params["rho_g"]) * float(params["cp_g"]), lat)
         self.mass_tol, self.width_tol, self.h_tol = mass_tol, width_tol, h_tol
         self.jumps_per_lb, self.max_backoff = jumps_per_lb, max_backoff
-        self.phi_band, self.slow_only = phi_band, slow_only
+        self.phi_band, self.slow_only, self.h_project = phi_band, slow_only, h_project
         ny, nx = solver.ny, solver.nx
         mk = lambda: {f: torch.empty((ny, nx), dtype=torch.float32, device="cuda") for f in FIELDS}
         self.cur, self.pred = mk(), mk()
+        self.scratch = mk() if h_project else None
         self.x = torch.empty((1, ny, nx, cno.CIN), dtype=torch.bfloat16, device="cuda")
         self.out = torch.empty((1, ny, nx, cno.NF), dtype=torch.float32, device="cuda")
         self.accepted = self.rejected = self.lb_chunks = 0
@@ -294,6 +299,8 @@ class SurrogateStepper:
         hi = [1.0, t0[1], 1.0, inf, inf, inf, inf]
         cno.apply_update([self.cur[f] for f in FIELDS], [self.pred[f] for f in FIELDS], self.out, scale,
                          self.phi_band, lo, hi)
+        if self.h_project and self._fresh:
+            self._project_enthalpy(scale, h0, lo, hi)
         m1, w1, t1, h1 = self._measures(self.pred)
         dm = abs(m1 - m0) / max(abs(m0), 1e-300)
         dw = abs(w1 / w0 - 1.0) if w0 > 0 else float("inf")
@@ -301,10 +308,33 @@ class SurrogateStepper:
         dh = abs((h1 - h0) - want) / max(abs(want), 1e-12 * max(abs(h0), 1.0))
         ok = bool(np.isfinite(m1) and np.isfinite(w1) and np.isfinite(h1) and self._fresh
                   and dm <= self.mass_tol and dw <= self.width_tol and dh <= self.h_tol)
-        self.last = dict(mass_change=dm, width_change=dw, enthalpy_mismatch=dh, accepted=ok)
+        self.last = dict(mass_change=dm, width_change=dw, enthalpy_mismatch=dh, accepted=ok,
+                         fs_scale=getattr(self, "last_c", None) if self.h_project else None)
         if ok:
             self.s.set_fields(self.pred)
         return ok
+
+    def _project_enthalpy(self, scale, h0, lo, hi):
+        """Rescale the predicted change of f_s by the factor c that makes the
+        jump's enthalpy change equal the rate measured on the last LB chunk:
+        at the predicted T the enthalpy is linear in f_s, so with H_a the
+        enthalpy of (predicted T, current f_s) and H_b that of the prediction,
+        c = (H_0 + rate K - H_a) / (H_b - H_a), clamped to [0, 2].  The front
+        then advances at the rate the wall's heat extraction allows (the
+        Stefan condition), with the network's shape of the change."""
+        F = self.pred
+        h_b = cno.field_checks(F["phi"], F["fs"], F["T"], self.hcoef)[7]
+        h_a = cno.field_checks(F["phi"], self.cur["fs"], F["T"], self.hcoef)[7]
+        want = h0 + self.h_rate * self.k
+        c = 1.0 if abs(h_b - h_a) < 1e-12 * max(abs(h0), 1.0) else (want - h_a) / (h_b - h_a)
+        c = min(max(c, 0.0), 2.0)
+        sc = np.zeros(len(FIELDS), np.float32)
+        k = FIELDS.index("fs")
+        sc[k] = c * scale[k]
+        dst = [self.scratch[f] for f in FIELDS]
+        dst[k] = F["fs"]
+        cno.apply_update([self.cur[f] for f in FIELDS], dst, self.out, sc, 0.0, lo, hi)
+        self.last_c = c
 
     def advance(self, nsteps: int):
         """Advance by nsteps LB-step equivalents."""
