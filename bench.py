@@ -113,6 +113,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def max_over_ranks(value: float, dist=None, device="cuda") -> float:
+    """The largest value of a per-rank number over all ranks: a job's time is its
+    slowest rank's.  dist is torch.distributed (initialised) or None for one rank."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling:
+    every rank runs the same work on its own lattice)."""
+    return world * units_per_rank / seconds
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -179,10 +195,7 @@ def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     s.step(args.steps)
     e1.record(stream)
     e1.synchronize()
-    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     s.reduce()  # raises if the half-precision run went non-finite
     s.close()
     mlups = ws * cells * args.steps / (ms * 1e-3) / 1e6
@@ -218,10 +231,7 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
         run(K)
         e1.record(stream)
         e1.synchronize()
-        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(e0.elapsed_time(e1), dist)
 
     inst = [b.instance(i) for i in range(n)]
 
@@ -372,12 +382,10 @@ def run_gpu(args):
     ms_total = e0.elapsed_time(e1)
     red = solver.reduce()
     solver.close()
-    t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
     if ws > 1:
         dist.barrier()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms_total, dist if ws > 1 else None)
+    value = whole_job_rate(cells * args.steps, ms_max * 1e-3, ws) / 1e6
     kernel_ms = ms_total / args.steps
 
     # ---- end to end through the public API with pinned host buffers ---------------------
@@ -395,10 +403,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     s2.close()
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = ws * cells * args.steps / float(te.item()) / 1e6
+    e2e_value = whole_job_rate(cells * args.steps, max_over_ranks(e2e_s, dist if ws > 1 else None), ws) / 1e6
 
     # ---- batched form: a sweep of independent droplets in one launch per step -----------
     fp16 = None
