@@ -168,16 +168,36 @@ static double s_of(int i, double ux, double uy)
  *  l_eq = w C (1 + c.u/cs2)                                     (Sec. 3.4)
  * The i = 0 enthalpy term is printed "rho H - rho C_p,ref T"; it is read with
  * rho_ref so that sum_i h_eq_i = rho H holds exactly. */
+/* Weights of the phase-field and solute sets.  The paper does not name their
+ * lattice (D2Q9 is read everywhere; Sec. 3).  D2Q5 is the five velocities
+ * c_0 .. c_4 of D2Q9 with weights 1/3 and 1/6: written here as D2Q9 with zero
+ * diagonal weights, whose populations 5 .. 8 then stay zero; both lattices have
+ * c_s^2 = 1/3 and the same first moments, which is all the equilibria and
+ * sources of f and l use. */
+static const double W5[9] = {1.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 1.0 / 6.0, 0.0, 0.0, 0.0, 0.0};
+static const double *weights_fl(const orc_params *p) { return p->lattice_fl == 1 ? W5 : WT; }
+
+static void equilibria_w(const orc_params *p, const double *wfl, double phi, double C, double rhoH, double T,
+                         double pr, double ux, double uy, double rho, double rhocp,
+                         double feq[9], double geq[9], double heq[9], double leq[9]);
+
 void orc_equilibria(const orc_params *p, double phi, double C, double rhoH, double T,
                     double pr, double ux, double uy, double rho, double rhocp,
                     double feq[9], double geq[9], double heq[9], double leq[9])
+{
+    equilibria_w(p, WT, phi, C, rhoH, T, pr, ux, uy, rho, rhocp, feq, geq, heq, leq);
+}
+
+static void equilibria_w(const orc_params *p, const double *wfl, double phi, double C, double rhoH, double T,
+                         double pr, double ux, double uy, double rho, double rhocp,
+                         double feq[9], double geq[9], double heq[9], double leq[9])
 {
     double rr = rhocp_ref(p);
     double uu = ux * ux + uy * uy;
     for (int i = 0; i < 9; i++) {
         double cu = CX[i] * ux + CY[i] * uy;
-        feq[i] = WT[i] * phi * (1.0 + cu / CS2);
-        leq[i] = WT[i] * C * (1.0 + cu / CS2);
+        feq[i] = wfl[i] * phi * (1.0 + cu / CS2);
+        leq[i] = wfl[i] * C * (1.0 + cu / CS2);
         geq[i] = pr / CS2 * (WT[i] - (i == 0 ? 1.0 : 0.0)) + rho * s_of(i, ux, uy);
         if (i == 0)
             heq[i] = rhoH - rr * T + WT[0] * rr * T - WT[0] * rhocp * T * uu / (2.0 * CS2);
@@ -193,11 +213,27 @@ void orc_equilibria(const orc_params *p, double phi, double C, double rhoH, doub
  *  L_i = w c.[d_t(C u) + cs2 R]/cs2                                       (Sec. 3.4)
  * H_i is printed without the weight w_i, which is read as a typo (its zeroth
  * moment must be Q).  ``divu`` is the velocity divergence (see pass_local). */
+static void sources_w(const double *wfl, double dphiux, double dphiuy, double nx_, double ny_, double phi,
+                      double eps, double divu, double S, double Fx, double Fy, double rfx, double rfy,
+                      double Ftx, double Fty, double ux, double uy, double Q,
+                      double dCux, double dCuy, double Rx, double Ry,
+                      double Fi[9], double Gi[9], double Hi[9], double Li[9]);
+
 void orc_sources(double dphiux, double dphiuy, double nx_, double ny_, double phi, double eps,
                  double divu, double S, double Fx, double Fy, double rfx, double rfy,
                  double Ftx, double Fty, double ux, double uy, double Q,
                  double dCux, double dCuy, double Rx, double Ry,
                  double Fi[9], double Gi[9], double Hi[9], double Li[9])
+{
+    sources_w(WT, dphiux, dphiuy, nx_, ny_, phi, eps, divu, S, Fx, Fy, rfx, rfy, Ftx, Fty, ux, uy, Q, dCux, dCuy,
+              Rx, Ry, Fi, Gi, Hi, Li);
+}
+
+static void sources_w(const double *wfl, double dphiux, double dphiuy, double nx_, double ny_, double phi,
+                      double eps, double divu, double S, double Fx, double Fy, double rfx, double rfy,
+                      double Ftx, double Fty, double ux, double uy, double Q,
+                      double dCux, double dCuy, double Rx, double Ry,
+                      double Fi[9], double Gi[9], double Hi[9], double Li[9])
 {
     double kf = CS2 * (1.0 - phi * phi) / (sqrt(2.0) * eps);
     double ax = dphiux + kf * nx_, ay = dphiuy + kf * ny_;
@@ -206,12 +242,12 @@ void orc_sources(double dphiux, double dphiuy, double nx_, double ny_, double ph
     for (int i = 0; i < 9; i++) {
         double cx = CX[i], cy = CY[i];
         double cu = cx * ux + cy * uy, cF = cx * Ftx + cy * Fty;
-        Fi[i] = WT[i] * (cx * ax + cy * ay) / CS2 + WT[i] * phi * divu;
+        Fi[i] = wfl[i] * (cx * ax + cy * ay) / CS2 + wfl[i] * phi * divu;
         /* (u Ft + Ft u):(c c - cs2 I) = 2 (c.u)(c.Ft) - 2 cs2 u.Ft */
         Gi[i] = WT[i] * (S + (cx * (Fx + rfx) + cy * (Fy + rfy)) / CS2 +
                          (2.0 * cu * cF - 2.0 * CS2 * uF) / (2.0 * CS2 * CS2));
         Hi[i] = WT[i] * Q;
-        Li[i] = WT[i] * (cx * bx + cy * by) / CS2;
+        Li[i] = wfl[i] * (cx * bx + cy * by) / CS2;
     }
 }
 
@@ -373,7 +409,7 @@ orc_state *orc_create(const orc_grid *g, const orc_params *p, const double *phi0
         double rho = orc_zeta(ph, fs, p->rho_l, p->rho_s, p->rho_g);
         double rhocp = orc_zeta(ph, fs, p->rho_l * p->cp_l, p->rho_s * p->cp_s, p->rho_g * p->cp_g);
         double feq[9], geq[9], heq[9], leq[9];
-        orc_equilibria(p, ph, C, e, Tc, 0.0, ux, uy, rho, rhocp, feq, geq, heq, leq);
+        equilibria_w(p, weights_fl(p), ph, C, e, Tc, 0.0, ux, uy, rho, rhocp, feq, geq, heq, leq);
         for (int i = 0; i < 9; i++) {
             st->f[i * n + c] = feq[i];
             st->gq[i * n + c] = geq[i];
@@ -588,9 +624,9 @@ static void cell_dynamics(const orc_state *st, int x, int y, cell_out *o)
     double Q = rhocp * T * divu;
 
     double feq[9], geq[9], heq[9], leq[9], Fi[9], Gi[9], Hi[9], Li[9];
-    orc_equilibria(p, phi, C, rhoH, T, pr, ux, uy, rho, rhocp, feq, geq, heq, leq);
-    orc_sources(dpx, dpy, nx_, ny_, phi, eps, divu, S, Fx, Fy, rfx, rfy, Ftx, Fty, ux, uy, Q,
-                dcx, dcy, Rx, Ry, Fi, Gi, Hi, Li);
+    equilibria_w(p, weights_fl(p), phi, C, rhoH, T, pr, ux, uy, rho, rhocp, feq, geq, heq, leq);
+    sources_w(weights_fl(p), dpx, dpy, nx_, ny_, phi, eps, divu, S, Fx, Fy, rfx, rfy, Ftx, Fty, ux, uy, Q,
+              dcx, dcy, Rx, Ry, Fi, Gi, Hi, Li);
 
     double hloc[9];
     for (int i = 0; i < 9; i++) hloc[i] = st->h[i * n + c];

@@ -34,6 +34,7 @@ typedef struct {
     double gx, gy;
     int fs_modulated_st, phase_change_on;
     int divu_mode; /* 0: div u = mdot (model value); 1: lagged velocity divergence */
+    int lattice_fl; /* lattice of the phase-field and solute sets: 0 D2Q9, 1 D2Q5 */
 } orc_params;
 
 typedef struct orc_state orc_state;
