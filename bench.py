@@ -178,6 +178,7 @@ def run_reference(args):
 
 
 BYTES_PER_UPDATE_F16 = 216  # 36 populations read + written as FP16, 9 lagged FP32 fields read + written
+BYTES_PER_UPDATE_Q5 = 296   # D2Q5 f and l: 28 populations + 9 lagged fields, FP32, read + written
 
 
 def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
@@ -204,6 +205,32 @@ def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
             "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_F16,
             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
             "dtype": "f32 arithmetic, f16 populations"}
+
+
+def _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
+    """The same lattice with D2Q5 for the phase-field and solute sets: MLUPS, and
+    achieved bandwidth against its own algorithmic bytes (296 B per update)."""
+    s = lbfreeze.Solver(w["grid"], dict(w["params"], lattice_fl=1), f32, stream=stream)
+    s.step(args.warmup)
+    stream.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    s.reduce()  # raises if the run went non-finite
+    s.close()
+    mlups = whole_job_rate(cells * args.steps, ms * 1e-3, ws) / 1e6
+    gbs = BYTES_PER_UPDATE_Q5 * cells * args.steps / (ms * 1e-3) / 1e9
+    return {"metric": "MLUPS (all coupled fields), D2Q5 phase-field and solute sets", "value": round(mlups, 2),
+            "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_Q5,
+            "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
+            "dtype": "f32"}
 
 
 def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
@@ -410,6 +437,10 @@ def run_gpu(args):
     if not args.no_fp16:
         fp16 = _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
                          _peaks()[0].get("hbm_gbs"))
+    d2q5 = None
+    if not args.no_d2q5:
+        d2q5 = _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
+                         _peaks()[0].get("hbm_gbs"))
     batched = None
     if args.batch > 0:
         batched = _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist if ws > 1 else None)
@@ -450,6 +481,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": round(d2h)},
         "gpu_launches": args.steps * launches_per_step,
         "fp16_storage": fp16,
+        "d2q5_fl": d2q5,
         "batched": batched,
         "surrogate": sur,
         "clocks": clk.summary(),
@@ -470,6 +502,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="droplet-sweep instances of the batched leg (0: skip)")
     ap.add_argument("--no-fp16", action="store_true", help="skip the half-precision population storage leg")
+    ap.add_argument("--no-d2q5", action="store_true", help="skip the D2Q5 phase-field / solute lattice leg")
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--sur-iters", type=int, default=3000, help="surrogate training iterations (0: skip the leg)")
     ap.add_argument("--sur-lattices", type=int, default=48, help="LB trajectories the surrogate is trained on")

@@ -33,6 +33,7 @@ struct lb_handle {
     long long nitems = 0;                   // work items of one step
     int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
     bool half = false;           // populations stored in half precision
+    int kind = 0;                // kernel instantiation: 0 FP32 D2Q9, 1 FP16 D2Q9, 2 FP32 with D2Q5 f and l
     size_t pop_bytes() const { return (half ? 2 : 4) * 36 * (size_t)K.plane; }
     int cur = 0;
     cudaStream_t stream = nullptr;
@@ -119,6 +120,10 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
     if (p->divu_mode != 0) return "divu_mode must be 0";
     if (p->pop_storage != LB_STORAGE_F32 && p->pop_storage != LB_STORAGE_F16)
         return "pop_storage must be LB_STORAGE_F32 or LB_STORAGE_F16";
+    if (p->lattice_fl != LB_LATTICE_D2Q9 && p->lattice_fl != LB_LATTICE_D2Q5)
+        return "lattice_fl must be LB_LATTICE_D2Q9 or LB_LATTICE_D2Q5";
+    if (p->lattice_fl == LB_LATTICE_D2Q5 && p->pop_storage != LB_STORAGE_F32)
+        return "lattice_fl = LB_LATTICE_D2Q5 needs pop_storage = LB_STORAGE_F32";
     if (p->phase_change_on && p->T_liq < p->T_sol) return "T_liq < T_sol";
     return "";
 }
@@ -163,6 +168,7 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
     K.segh = LB_SEGH;
+    K.qfl = p->lattice_fl == LB_LATTICE_D2Q5 ? 5 : 9;
     K.phase_change = p->phase_change_on ? 1 : 0;
     return K;
 }
@@ -198,10 +204,12 @@ static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t
 }
 
 template <int MODE>
-static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, bool half, double *partials = nullptr)
+static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, int kind, double *partials = nullptr)
 {
-    if (half)
+    if (kind == 1)
         launch_strip_as<MODE, lbk::PopF16>(K, B, st, partials);
+    else if (kind == 2)
+        launch_strip_as<MODE, lbk::PopF32Q5>(K, B, st, partials);
     else
         launch_strip_as<MODE, lbk::PopF32>(K, B, st, partials);
 }
@@ -252,10 +260,11 @@ static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long 
 }
 
 static cudaError_t launch_step(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
-                               unsigned long long *counter, cudaStream_t st, bool half)
+                               unsigned long long *counter, cudaStream_t st, int kind)
 {
-    return half ? launch_step_as<lbk::PopF16>(rec, ninst, nitems, parity, counter, st)
-                : launch_step_as<lbk::PopF32>(rec, ninst, nitems, parity, counter, st);
+    if (kind == 1) return launch_step_as<lbk::PopF16>(rec, ninst, nitems, parity, counter, st);
+    if (kind == 2) return launch_step_as<lbk::PopF32Q5>(rec, ninst, nitems, parity, counter, st);
+    return launch_step_as<lbk::PopF32>(rec, ninst, nitems, parity, counter, st);
 }
 
 static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
@@ -268,7 +277,7 @@ static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
     B.aout = nullptr;
     B.fields = nullptr;
     B.status = h->status;
-    launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->half, h->partials);
+    launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->kind, h->partials);
     CK(h, cudaGetLastError());
     lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_parts, h->red_out);
     CK(h, cudaGetLastError());
@@ -296,6 +305,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     h->grid = *grid;
     h->params = *params;
     h->half = params->pop_storage == LB_STORAGE_F16;
+    h->kind = h->half ? 1 : (params->lattice_fl == 1 ? 2 : 0);
     h->K = make_consts(grid, params);
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
@@ -395,7 +405,7 @@ extern "C" lb_status lb_step(lb_handle *h, int n)
     if (!h || n < 0) return fail(h, LB_ERR_INVALID_ARG, "null handle or negative step count");
     if (h->sticky != LB_OK) return h->sticky;
     for (int s = 0; s < n; s++) {
-        cudaError_t e = launch_step(h->rec, 1, h->nitems, h->cur, h->counter, h->stream, h->half);
+        cudaError_t e = launch_step(h->rec, 1, h->nitems, h->cur, h->counter, h->stream, h->kind);
         if (e != cudaSuccess) return cuda_fail(h, e, "lb_step_kernel launch");
         h->cur = 1 - h->cur;
         h->steps++;
@@ -423,7 +433,7 @@ extern "C" lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs
     B.aout = nullptr;
     B.fields = h->fields;
     B.status = h->status;
-    launch_strip<lbk::MODE_FIELDS>(K, B, h->stream, h->half);
+    launch_strip<lbk::MODE_FIELDS>(K, B, h->stream, h->kind);
     CK(h, cudaGetLastError());
     float *dst[7] = {phi, T, fs, C, ux, uy, p};
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -528,7 +538,7 @@ extern "C" lb_status lb_save(lb_handle *h, const char *path)
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "LBFRZ01", 8);
-    hd.version = h->half ? 2 : 1;  // 2: half-precision populations
+    hd.version = h->kind + 1;  // 1: FP32, 2: half-precision populations, 3: FP32 with D2Q5 f and l
     hd.nx = K.nx; hd.ny = K.ny; hd.pitch = K.pitch; hd.steps = h->steps; hd.V0 = h->V0;
     bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf, 1, pb + ab, f) == pb + ab;
     ok = (fclose(f) == 0) && ok;
@@ -545,7 +555,7 @@ extern "C" lb_status lb_load(lb_handle *h, const char *path)
     if (!f) return fail(h, LB_ERR_INVALID_ARG, std::string("cannot open ") + path);
     CkptHeader hd;
     if (fread(&hd, sizeof(hd), 1, f) != 1 || memcmp(hd.magic, "LBFRZ01", 8) != 0 || hd.nx != K.nx || hd.ny != K.ny ||
-        hd.pitch != K.pitch || hd.version != (h->half ? 2 : 1)) {
+        hd.pitch != K.pitch || hd.version != h->kind + 1) {
         fclose(f);
         return fail(h, LB_ERR_INVALID_ARG, "checkpoint does not match this lattice");
     }
@@ -681,6 +691,9 @@ extern "C" lb_status lb_reduce_noalloc(lb_handle *h, double out[8])
     if (h->half)
         noalloc_rows_kernel<lbk::PopF16><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
                                                                                   scratch);
+    else if (h->kind == 2)
+        noalloc_rows_kernel<lbk::PopF32Q5><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur],
+                                                                                    h->aux[h->cur], scratch);
     else
         noalloc_rows_kernel<lbk::PopF32><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
                                                                                   scratch);
@@ -766,7 +779,7 @@ static lb_status upload_instances(lb_batch *b)
 // One batched step from buffer `parity` on stream st.
 static lb_status launch_batch(lb_batch *b, int parity, cudaStream_t st)
 {
-    BCK(b, launch_step(b->d_inst, (int)b->h.size(), b->nitems, parity, b->d_counter, st, b->h[0]->half));
+    BCK(b, launch_step(b->d_inst, (int)b->h.size(), b->nitems, parity, b->d_counter, st, b->h[0]->kind));
     return LB_OK;
 }
 
@@ -784,10 +797,10 @@ extern "C" lb_status lb_batch_create(int n, const lb_grid *grids, const lb_param
             return bfail(nullptr, s, why);
         }
         b->h.push_back(h);
-        if (h->half != b->h[0]->half) {
+        if (h->kind != b->h[0]->kind) {
             lb_batch_destroy(b);
             return bfail(nullptr, LB_ERR_INVALID_ARG, "instance " + std::to_string(i) +
-                                                          ": all instances must use the same pop_storage");
+                                                          ": all instances must use the same pop_storage and lattice_fl");
         }
     }
     b->inst.resize(n);

@@ -60,6 +60,15 @@ __host__ __device__ constexpr int cx(int i) { return (i == 1 || i == 5 || i == 8
 __host__ __device__ constexpr int cy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
 __host__ __device__ constexpr real wgt(int i) { return i == 0 ? (R(4.0) / R(9.0)) : (i <= 4 ? (R(1.0) / R(9.0)) : (R(1.0) / R(36.0))); }
+// Weights of the phase-field and solute sets on a lattice of Q = 9 or 5
+// velocities (D2Q5: the first five D2Q9 velocities, weights 1/3 and 1/6, the
+// same c_s^2 = 1/3).
+template <int Q>
+__host__ __device__ constexpr real wfl(int i)
+{
+    return Q == 9 ? wgt(i) : (i == 0 ? (R(1.0) / R(3.0)) : (i <= 4 ? (R(1.0) / R(6.0)) : R(0.0)));
+}
+__host__ __device__ inline real wfl_rt(int q, int i) { return q == 5 ? wfl<5>(i) : wfl<9>(i); }
 
 constexpr int SET_F = 0, SET_G = 1, SET_H = 2, SET_L = 3;
 
@@ -71,15 +80,23 @@ constexpr int SET_F = 0, SET_G = 1, SET_H = 2, SET_L = 3;
 struct PopF32 {
     typedef float T;
     static constexpr bool kHalf = false;
+    static constexpr int QFL = 9;  // lattice of the phase-field and solute sets
     __device__ static real dec(T v) { return v; }
     __device__ static T enc(real d) { return d; }
 };
 struct PopF16 {
     typedef __half T;
     static constexpr bool kHalf = true;
+    static constexpr int QFL = 9;  // lattice of the phase-field and solute sets
     __device__ static real dec(T v) { return __half2float(v) * R(1.0 / 256.0); }
     __device__ static T enc(real d) { return __float2half_rn(d * R(256.0)); }
 };
+// FP32 storage with D2Q5 for the phase-field and solute sets (lb_params.lattice_fl
+// = 1): their populations 5 .. 8 are neither read nor written.
+struct PopF32Q5 : PopF32 {
+    static constexpr int QFL = 5;
+};
+
 constexpr int AUX_FS = 0, AUX_Q = 1, AUX_UX = 2, AUX_UY = 3, AUX_PHI = 4, AUX_C = 5, AUX_P = 6, AUX_S = 7, AUX_T = 8;
 constexpr int NAUX = 9;
 constexpr int WALL_DIRICHLET = 0;
@@ -103,7 +120,8 @@ struct Consts {
     real sigma0, sigma_T, sigma_c, T_ref, c_ref, gx, gy;
     real expand;                // 1 - rho_s / rho_l
     int fs_mod, phase_change;
-    int segh;                   // rows of an inner segment of the strip sweep
+    int segh;
+    int qfl;                    // lattice of the phase-field and solute sets: 9 or 5 velocities                   // rows of an inner segment of the strip sweep
 };
 
 struct Buffers {
@@ -353,10 +371,13 @@ __device__ __forceinline__ real aux_src(const Consts &K, const float *__restrict
 
 // sum_{i>0} w_i (z^n(source_i) - z^n(x)) of a lagged field: the reference
 // offsets of the pulled deviations relative to the own lagged value.
-template <int A, bool W = true>
+template <int A, bool W = true, int Q = 9>
 __device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__restrict__ ain, int x, int y, int cell,
                                             real own)
 {
+    if (Q == 5)  // the same order as the strip kernel's phase A (lag_dev_sums)
+        return wfl<5>(1) * (((aux_src<A, 1, W>(K, ain, x, y, cell) - own) + (aux_src<A, 2, W>(K, ain, x, y, cell) - own)) +
+                            ((aux_src<A, 3, W>(K, ain, x, y, cell) - own) + (aux_src<A, 4, W>(K, ain, x, y, cell) - own)));
     return (wgt(1) * (aux_src<A, 1, W>(K, ain, x, y, cell) - own) + wgt(2) * (aux_src<A, 2, W>(K, ain, x, y, cell) - own) +
             wgt(3) * (aux_src<A, 3, W>(K, ain, x, y, cell) - own) + wgt(4) * (aux_src<A, 4, W>(K, ain, x, y, cell) - own)) +
            (wgt(5) * (aux_src<A, 5, W>(K, ain, x, y, cell) - own) + wgt(6) * (aux_src<A, 6, W>(K, ain, x, y, cell) - own) +
@@ -410,7 +431,7 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const typename PS::T *_
     c.fs_p = __ldg(plane_ptr(ain, AUX_FS, K) + cell);
     c.chi_p = clamp01(R(0.5) * (R(1.0) + c.phi_p));
     pull9<PS, SET_F, W>(K, pin, x, y, cell, v);
-    const real delta = sum9(v) + aux_dev_sum<AUX_PHI, W>(K, ain, x, y, cell, c.phi_p);
+    const real delta = sum9(v) + aux_dev_sum<AUX_PHI, W, PS::QFL>(K, ain, x, y, cell, c.phi_p);
     pull9<PS, SET_H, W>(K, pin, x, y, cell, v, c.T_p);
     const real Q_p = __ldg(plane_ptr(ain, AUX_Q, K) + cell);
     c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T, W>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
@@ -661,10 +682,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         // stored as f_i* - w_i phi_st
         real f[9];
         A.template pops<SET_F>(K, B.pin, x, y, cell, f, R(0.0));
+        constexpr int QF = PS::QFL;
         {
-            const real d = f[0] + wgt(0) * (phi_p - phi_st);
-            const real deq = wgt(0) * phi_lo;
-            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wgt(0) * phi * mdot));
+            const real d = f[0] + wfl<QF>(0) * (phi_p - phi_st);
+            const real deq = wfl<QF>(0) * phi_lo;
+            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wfl<QF>(0) * phi * mdot));
         }
         // lagged phi of the cell that wrote the population pulled into direction i (own cell at a wall)
         auto php = [&](int i) {
@@ -672,9 +694,9 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             return (WALLS && cy(i) != 0 && (ys < 0 || ys >= K.ny)) ? phi_p : A.phip(-cy(i), -cx(i));
         };
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
+        for (int q = 0; q < (QF == 9 ? 2 : 1); q++) {
             const int a = q == 0 ? 1 : 5;
-            const real w = wgt(a), w3 = R(3.0) * w;
+            const real w = wfl<QF>(a), w3 = R(3.0) * w;
             const pf2 ws = splat2(w), ps = splat2(phi_st);
             const pf2 dp = fma2(ws, sub2(pk2(php(a), php(a + 1)), ps), pk2(f[a], f[a + 1]));
             const pf2 dm = fma2(ws, sub2(pk2(php(opp(a)), php(opp(a + 1))), ps), pk2(f[opp(a)], f[opp(a + 1)]));
@@ -698,11 +720,11 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
         real l[9];
         A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
-        put_pop<PS>(K, pout, SET_L, 0, cell, l[0] - (l[0] - wgt(0) * C) * om_l);
+        put_pop<PS>(K, pout, SET_L, 0, cell, l[0] - (l[0] - wfl<QF>(0) * C) * om_l);
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
+        for (int q = 0; q < (QF == 9 ? 2 : 1); q++) {
             const int a = q == 0 ? 1 : 5;
-            const real w = wgt(a), w3 = R(3.0) * w;
+            const real w = wfl<QF>(a), w3 = R(3.0) * w;
             const pf2 eq_e = splat2(w * C), eq_o = mul2(splat2(w3 * C), cdot2(a, ux, uy));
             const pf2 sL = mul2(splat2(src_l * w3), cdot2(a, bx, by));  // src_l L_i, odd
             const pf2 lp = pk2(l[a], l[a + 1]), lm = pk2(l[opp(a)], l[opp(a + 1)]), ol = splat2(om_l);
@@ -871,7 +893,8 @@ __device__ __forceinline__ void load9(const Consts &K, const WarpRing &w, int sl
     constexpr int E = win_elems<T>();
     const T *p = reinterpret_cast<const T *>(&w.pop[slot][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][0]) + idx;
 #pragma unroll
-    for (int i = 0; i < 9; i++) v[i] = dec_pop<PS>(K, S, i, p[i * E - cx(i)]);
+    for (int i = 0; i < 9; i++)
+        v[i] = ((S == SET_F || S == SET_L) && i >= PS::QFL) ? R(0.0) : dec_pop<PS>(K, S, i, p[i * E - cx(i)]);
 }
 
 // The enthalpy wall rule on decoded pulls (W only).
@@ -941,10 +964,12 @@ __device__ __forceinline__ void stage9(const Consts &K, const typename PS::T *__
         cp_async4(dst + 2 * E - cx(2), pull_src<S, 2, W>(K, pin, x, y, cell));
         cp_async4(dst + 3 * E - cx(3), pull_src<S, 3, W>(K, pin, x, y, cell));
         cp_async4(dst + 4 * E - cx(4), pull_src<S, 4, W>(K, pin, x, y, cell));
-        cp_async4(dst + 5 * E - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
-        cp_async4(dst + 6 * E - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
-        cp_async4(dst + 7 * E - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
-        cp_async4(dst + 8 * E - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
+        if ((S != SET_F && S != SET_L) || PS::QFL == 9) {  // D2Q5 f and l: directions 0 .. 4 only
+            cp_async4(dst + 5 * E - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
+            cp_async4(dst + 6 * E - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
+            cp_async4(dst + 7 * E - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
+            cp_async4(dst + 8 * E - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
+        }
     } else {
         dst[0 * E - cx(0)] = __ldg(pull_src<S, 0, W>(K, pin, x, y, cell));
         dst[1 * E - cx(1)] = __ldg(pull_src<S, 1, W>(K, pin, x, y, cell));
@@ -970,7 +995,7 @@ __device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int 
     tt = v.y;
 }
 
-template <bool W>
+template <bool W, int QF>
 __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w, int lane, int y, real phi_own,
                                              real T_own, real &dph, real &dtt)
 {
@@ -983,10 +1008,13 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w,
     lag_src<6, W>(K, w, lane, y, ph[6], tt[6]);
     lag_src<7, W>(K, w, lane, y, ph[7], tt[7]);
     lag_src<8, W>(K, w, lane, y, ph[8], tt[8]);
-    dph = (wgt(1) * (ph[1] - phi_own) + wgt(2) * (ph[2] - phi_own) + wgt(3) * (ph[3] - phi_own) +
-           wgt(4) * (ph[4] - phi_own)) +
-          (wgt(5) * (ph[5] - phi_own) + wgt(6) * (ph[6] - phi_own) + wgt(7) * (ph[7] - phi_own) +
-           wgt(8) * (ph[8] - phi_own));
+    if (QF == 9)
+        dph = (wgt(1) * (ph[1] - phi_own) + wgt(2) * (ph[2] - phi_own) + wgt(3) * (ph[3] - phi_own) +
+               wgt(4) * (ph[4] - phi_own)) +
+              (wgt(5) * (ph[5] - phi_own) + wgt(6) * (ph[6] - phi_own) + wgt(7) * (ph[7] - phi_own) +
+               wgt(8) * (ph[8] - phi_own));
+    else
+        dph = wfl<5>(1) * (((ph[1] - phi_own) + (ph[2] - phi_own)) + ((ph[3] - phi_own) + (ph[4] - phi_own)));
     dtt = (wgt(1) * (tt[1] - T_own) + wgt(2) * (tt[2] - T_own) + wgt(3) * (tt[3] - T_own) + wgt(4) * (tt[4] - T_own)) +
           (wgt(5) * (tt[5] - T_own) + wgt(6) * (tt[6] - T_own) + wgt(7) * (tt[7] - T_own) + wgt(8) * (tt[8] - T_own));
 }
@@ -1052,8 +1080,10 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                     // group wg: set f, h or l; one window per direction, rows y - c_iy
                     const T *src = plane_ptr(pin, wg == 0 ? SET_F * 9 : (wg == 1 ? SET_H * 9 : SET_L * 9), K) + wcol;
                     T *dst = pw + 9 * wg * E + 4 * wpart;
+                    const int nq = wg == 1 ? 9 : PS::QFL;  // D2Q5 f and l: directions 0 .. 4
 #pragma unroll
-                    for (int i = 0; i < 9; i++) cp_async16(dst + i * E, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
+                    for (int i = 0; i < 9; i++)
+                        if (i < nq) cp_async16(dst + i * E, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
                 }
             } else {
                 if (hg < 5) {
@@ -1143,7 +1173,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             const float2 lag0 = w.lag[ya & 7][lane + 1];
             const real phi_p = lag0.x, T_p = lag0.y;
             real dph, dtt, v[9];
-            lag_dev_sums<WALLS>(K, w, lane, ya, phi_p, T_p, dph, dtt);
+            lag_dev_sums<WALLS, PS::QFL>(K, w, lane, ya, phi_p, T_p, dph, dtt);
             load9<PS, SET_F>(K, w, s3, lane + off, v);
             const real delta = sum9(v) + dph;
             load9<PS, SET_H>(K, w, s3, lane + off, v);
@@ -1325,9 +1355,9 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
         for (int i = 0; i < 9; i++) {
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
             const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-            eq[(long long)(SET_F * 9 + i) * K.plane + cell] = wgt(i) * phi * (R(1.0) + R(3.0) * cu);
+            eq[(long long)(SET_F * 9 + i) * K.plane + cell] = wfl_rt(K.qfl, i) * phi * (R(1.0) + R(3.0) * cu);
             eq[(long long)(SET_G * 9 + i) * K.plane + cell] = rho * si;
-            eq[(long long)(SET_L * 9 + i) * K.plane + cell] = wgt(i) * C * (R(1.0) + R(3.0) * cu);
+            eq[(long long)(SET_L * 9 + i) * K.plane + cell] = wfl_rt(K.qfl, i) * C * (R(1.0) + R(3.0) * cu);
             // h_0 - w_0 rr T - latent = e_sens - rr T - w_0 rho Cp T 3u.u/2;  h_i - w_i rr T = w_i rho Cp T (...)
             eq[(long long)(SET_H * 9 + i) * K.plane + cell] =
                 i == 0 ? e_sens - K.rr * T - wgt(0) * rcT * R(1.5) * uu
@@ -1382,7 +1412,7 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
                     if (s == SET_G && i != 0)
                         v += R(3.0) * wgt(i) * ((real)aux[AUX_P * K.plane + ct] - (real)aux[AUX_P * K.plane + cell]);
                 }
-                if (s == SET_F) v -= wgt(i) * phi_here;
+                if (s == SET_F) v -= wfl_rt(K.qfl, i) * phi_here;
                 reinterpret_cast<typename PS::T *>(pops)[(long long)(s * 9 + i) * K.plane + cell] = enc_pop<PS>(K, s, i, v);
             }
         }

@@ -35,7 +35,7 @@ class lb_grid(C.Structure):
 _PARAM_DOUBLES = ("rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lam_l", "lam_s", "lam_g",
                   "cp_l", "cp_s", "cp_g", "latent", "T_sol", "T_liq", "k_p", "D_l", "D_s", "eps",
                   "mobility", "sigma0", "sigma_T", "sigma_c", "T_ref", "c_ref", "gx", "gy")
-_PARAM_INTS = ("fs_modulated_st", "phase_change_on", "divu_mode", "pop_storage")
+_PARAM_INTS = ("fs_modulated_st", "phase_change_on", "divu_mode", "pop_storage", "lattice_fl")
 
 
 class lb_params(C.Structure):
