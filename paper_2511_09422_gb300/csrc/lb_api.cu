@@ -167,7 +167,7 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.gx = (real)p->gx; K.gy = (real)p->gy;
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
-    K.segh = LB_SEGH;
+    K.segh = (p->pop_storage == LB_STORAGE_F16 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
     K.qfl = p->lattice_fl == LB_LATTICE_D2Q5 ? 5 : 9;
     K.phase_change = p->phase_change_on ? 1 : 0;
     return K;

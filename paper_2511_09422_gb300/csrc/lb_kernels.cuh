@@ -827,8 +827,14 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #ifndef LB_SMINB
 #define LB_SMINB 4
 #endif
+// Inner segment height of single-lattice handles, per kernel kind (measured on
+// the 4096^2 step): FP32 D2Q9 is fastest at 8-12 rows (32 rows: 5 % slower);
+// FP16 storage and D2Q5 f/l at 32 rows (12 rows: 5 % and 1.3 % slower).
 #ifndef LB_SEGH
-#define LB_SEGH 32  // inner segment height of single-lattice handles
+#define LB_SEGH 12
+#endif
+#ifndef LB_SEGH_ALT
+#define LB_SEGH_ALT 32
 #endif
 
 constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_s on the column x = nx/2
