@@ -59,6 +59,12 @@ const char *cno_error_string(void);
  * kernel has given up a wait.  Synchronises the device; clear = 1 resets it. */
 cno_status cno_read_status(unsigned *out, int clear);
 
+/* Self-test of the bounded barrier wait that every tensor-core kernel uses:
+ * one thread waits on a barrier that nothing arrives at.  It must give up
+ * after `seconds` (0 < seconds <= 10): *gave_up = 1 and *elapsed the time it
+ * waited.  No data, TMA or tensor core is involved.  Synchronises the device. */
+cno_status cno_wait_selftest(double seconds, int *gave_up, double *elapsed);
+
 /* ---- Primitives on device tensors (asynchronous on `stream`, a cudaStream_t
  * or NULL for the legacy default stream) ---- */
 

@@ -26,7 +26,7 @@ NF = 7                        # phi, T, f_s, C, u_x, u_y, p
 _lib = None
 _lock = threading.Lock()
 
-EXPORTS = ("cno_error_string", "cno_read_status", "cno_conv3x3_forward", "cno_conv3x3_dgrad", "cno_conv3x3_wgrad",
+EXPORTS = ("cno_error_string", "cno_read_status", "cno_wait_selftest", "cno_conv3x3_forward", "cno_conv3x3_dgrad", "cno_conv3x3_wgrad",
            "cno_weights_to_bf16", "cno_create", "cno_destroy", "cno_set_stream", "cno_num_params",
            "cno_set_params", "cno_get_params", "cno_get_grads", "cno_forward", "cno_train_step",
            "cno_last_output", "cno_pack_fields", "cno_pack_delta", "cno_apply_update", "cno_field_checks")
@@ -56,6 +56,7 @@ def load(path: str | None = None):
         sig = {
             "cno_error_string": (C.c_char_p, []),
             "cno_read_status": (i, [C.POINTER(C.c_uint), i]),
+            "cno_wait_selftest": (i, [d, C.POINTER(C.c_int), C.POINTER(d)]),
             "cno_conv3x3_forward": (i, [vp, i, i, i, i, vp, vp, i, i, vp, i, i, i, vp]),
             "cno_conv3x3_dgrad": (i, [vp, i, i, i, i, vp, i, vp, vp, vp]),
             "cno_conv3x3_wgrad": (i, [vp, vp, i, i, i, i, i, vp, vp, vp]),
@@ -95,6 +96,13 @@ def _ptr(t):
 def _stream():
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def wait_selftest(seconds: float = 0.2):
+    """(gave_up, elapsed seconds) of a bounded wait on a barrier nothing arrives at."""
+    g, e = C.c_int(0), C.c_double(0.0)
+    _check(load().cno_wait_selftest(float(seconds), C.byref(g), C.byref(e)))
+    return bool(g.value), float(e.value)
 
 
 def read_status(clear: bool = False) -> int:

@@ -411,6 +411,26 @@ extern "C" cno_status cno_conv3x3_wgrad(const void *dz, const void *x, int n, in
                         (cudaStream_t)stream);
 }
 
+extern "C" cno_status cno_wait_selftest(double seconds, int *gave_up, double *elapsed)
+{
+    if (!gave_up || !elapsed || !(seconds > 0.0) || seconds > 10.0)
+        return fail(CNO_ERR_INVALID_ARG, "seconds must lie in (0, 10]");
+    DevScratch *s;
+    CS(scratch(&s));
+    unsigned long long *d = nullptr, h[2] = {0, 0};
+    CK(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    cnok::wait_selftest_kernel<<<1, 1>>>((unsigned long long)(seconds * 1e9), s->status, d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess)
+        return fail(CNO_ERR_CUDA, cudaGetErrorString(e));
+    *gave_up = (int)h[0];
+    *elapsed = (double)h[1] * 1e-9;
+    return CNO_OK;
+}
+
 extern "C" cno_status cno_weights_to_bf16(const float *w, int cout, int cin, void *wf, void *wd, void *stream)
 {
     if (!w || !wf || !wd || cout < 1 || cin < 1)

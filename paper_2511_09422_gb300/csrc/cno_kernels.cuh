@@ -67,9 +67,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase `parity` of a barrier to complete, for at most WAIT_NS;
+// Wait for the phase `parity` of a barrier to complete, for at most limit_ns;
 // gives up early when another CTA has already reported a failure.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const unsigned *status)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const unsigned *status,
+                                          unsigned long long limit_ns = WAIT_NS)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -80,11 +81,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, const 
         if ((it & 63u) == 0u) {
             if (*(volatile const unsigned *)status != 0u)
                 return false;
-            if (global_ns() - t0 > WAIT_NS)
+            if (global_ns() - t0 > limit_ns)
                 return false;
         }
     }
 }
+
 
 __device__ __forceinline__ void fence_barrier_init()
 {
@@ -94,6 +96,21 @@ __device__ __forceinline__ void fence_barrier_init()
 __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Self-test of the bounded wait: one thread waits on a barrier that nothing
+// arrives at; the wait must give up after limit_ns and report it in out[0]
+// (1: gave up), with the elapsed time in out[1] (ns).
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, const unsigned *status,
+                                     unsigned long long *out)
+{
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    const unsigned long long t0 = global_ns();
+    const bool ok = mbar_wait(&bar, 0, status, limit_ns);
+    out[0] = ok ? 0ull : 1ull;
+    out[1] = global_ns() - t0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1)

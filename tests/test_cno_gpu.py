@@ -207,3 +207,16 @@ def test_training_reduces_loss_on_a_fixed_batch():
     last = net.train_step(x, tt, lr=1e-3, update=False)
     assert last < 0.2 * first, (first, last)
     net.close()
+
+
+def test_bounded_wait_gives_up_and_reports():
+    """Failure detection without a GPU fault: the barrier wait every tensor-core
+    kernel uses gives up after its limit on a barrier that nothing arrives at,
+    and the device stays usable."""
+    from paper_2511_09422_gb300 import cno
+    gave_up, elapsed = cno.wait_selftest(0.2)
+    assert gave_up
+    assert 0.2 <= elapsed <= 2.0, elapsed
+    x = torch.zeros(4, device="cuda") + 1.0   # the context is still usable
+    assert float(x.sum()) == 4.0
+    assert cno.read_status() == 0
