@@ -269,16 +269,57 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
     ms_b = timed(b.step)
     ms_s = timed(sequential)
     b.close()
+    # the same sweep with half-precision population storage
+    sweep16 = [dict(w, params=dict(w["params"], pop_storage=1)) for w in sweep]
+    b16 = lbfreeze.Batch(sweep16, stream=stream)
+    choice16 = b16.tune(trials=3)
+    ms_16 = timed(b16.step)
+    b16.close()
     v_b = ws * n * K / (ms_b * 1e-3)
     v_s = ws * n * K / (ms_s * 1e-3)
+    v_16 = ws * n * K / (ms_16 * 1e-3)
     return {"metric": "instance-steps/s", "value": round(v_b, 1), "unit": "instance-steps/s",
             "workload": "droplet sweep: %d instances, side U[128,512], R U[0.2,0.35] side, Ste U[0.05,0.5], "
-                        "Ma U[0,50], C0 U[0,0.1], seed 20251109" % n,
+                        "Ma U[0,50], C0 U[0,0.1], contact angle U[60,120] deg, seed 20251109" % n,
+            "fp16_storage": {"value": round(v_16, 1), "mlups": round(ws * cells * K / (ms_16 * 1e-3) / 1e6, 1),
+                             "seg_rows_by_class": choice16},
             "instances": n, "cells": cells, "steps": K, "mlups": round(ws * cells * K / (ms_b * 1e-3) / 1e6, 1),
             "seg_rows_by_class": choice, "launches_per_step": 1,
             "sequential": {"value": round(v_s, 1), "mlups": round(ws * cells * K / (ms_s * 1e-3) / 1e6, 1),
                            "launches_per_step": n},
             "speedup": round(v_b / v_s, 3)}
+
+
+def _freezing_leg(args, lbfreeze, W, np, torch):
+    """A 512^2 binary sessile droplet (R = 100, 90 degrees, Ste 0.1, C0 0.05,
+    Ma 10; gas density ratio 0.1) run until 99 % of the phase-change material
+    is solid, with FP32 and with FP16 population storage: freezing time
+    (diagnostics in FP64 every 500 steps, linear interpolation), final V*_sl,
+    and wall time."""
+    w = W.sessile_droplet(nx=512, ny=512, radius=100.0, rho_g=0.1, ste=0.1, c0=0.05, ma_T=10.0, ma_C=10.0)
+    f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
+    out = {}
+    for name, st in (("f32", 0), ("f16", 1)):
+        s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=st), f32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n, prev, tf, r = 0, (0, 0.0), float("nan"), None
+        while n < args.freeze_max_steps:
+            s.step(500)
+            n += 500
+            r = s.reduce()
+            frac = r[3] / r[4]
+            if frac >= 0.99:
+                tf = prev[0] + (0.99 - prev[1]) / (frac - prev[1]) * (n - prev[0])
+                break
+            prev = (n, frac)
+        dt = time.perf_counter() - t0
+        out[name] = {"t_f": round(tf, 1), "steps_run": n, "V_sl": round(float(r[7]), 5), "wall_s": round(dt, 3),
+                     "mlups": round(512 * 512 * n / dt / 1e6, 1)}
+        s.close()
+    out["fp16_rel_error_t_f"] = abs(out["f16"]["t_f"] - out["f32"]["t_f"]) / out["f32"]["t_f"]
+    out["workload"] = "sessile droplet 512x512, R=100, theta=90, Ste=0.1, C0=0.05, Ma_T=Ma_C=10, rho_g/rho_l=0.1"
+    return out
 
 
 def _surrogate_leg(args, torch, peaks):
@@ -444,6 +485,9 @@ def run_gpu(args):
     batched = None
     if args.batch > 0:
         batched = _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist if ws > 1 else None)
+    freeze = None
+    if not args.no_freeze and ws == 1:
+        freeze = _freezing_leg(args, lbfreeze, W, np, torch)
     sur = None
     if args.sur_iters > 0 and ws == 1:
         sur = _surrogate_leg(args, torch, _peaks()[0])
@@ -483,6 +527,7 @@ def run_gpu(args):
         "fp16_storage": fp16,
         "d2q5_fl": d2q5,
         "batched": batched,
+        "droplet_freezing": freeze,
         "surrogate": sur,
         "clocks": clk.summary(),
         "check": {"sum_phi": red[0], "sum_C": red[2], "front": red[5]},
@@ -503,6 +548,8 @@ def main():
     ap.add_argument("--batch", type=int, default=256, help="droplet-sweep instances of the batched leg (0: skip)")
     ap.add_argument("--no-fp16", action="store_true", help="skip the half-precision population storage leg")
     ap.add_argument("--no-d2q5", action="store_true", help="skip the D2Q5 phase-field / solute lattice leg")
+    ap.add_argument("--no-freeze", action="store_true", help="skip the 512^2 droplet run to full freezing")
+    ap.add_argument("--freeze-max-steps", type=int, default=600000)
     ap.add_argument("--batch-steps", type=int, default=100)
     ap.add_argument("--sur-iters", type=int, default=3000, help="surrogate training iterations (0: skip the leg)")
     ap.add_argument("--sur-lattices", type=int, default=48, help="LB trajectories the surrogate is trained on")

@@ -168,6 +168,14 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
     K.segh = (p->pop_storage == LB_STORAGE_F16 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
+    // a small lattice needs shorter segments to give every resident warp work: go
+    // down (to 8 rows at least) until there are two waves of work items
+    {
+        const long long wave = 152LL * LB_SMINB * LB_SW, nstrip = (g->nx + LB_TX - 1) / LB_TX;
+        const int steps[] = {24, 16, 12, 8};
+        for (int c : steps)
+            if (c < K.segh && nstrip * lbk::strip_segments(g->ny, K.segh) < 2 * wave) K.segh = c;
+    }
     K.qfl = p->lattice_fl == LB_LATTICE_D2Q5 ? 5 : 9;
     K.phase_change = p->phase_change_on ? 1 : 0;
     return K;

@@ -236,7 +236,7 @@ class SurrogateStepper:
     freezes too fast or too slow breaks the balance."""
 
     def __init__(self, solver: lbfreeze.Solver, net: cno.Net, norm: Normaliser, params: dict, k=K_JUMP,
-                 mass_tol=1e-3, width_tol=0.05, h_tol=0.1, jumps_per_lb=2, max_backoff=64, phi_band=0.999,
+                 mass_tol=1e-3, width_tol=0.05, h_tol=0.02, jumps_per_lb=2, max_backoff=64, phi_band=0.999,
                  slow_only=True, h_project=False):
         import torch
         self.s, self.net, self.norm, self.k = solver, net, norm, k
