@@ -13,6 +13,16 @@ step kernel against the measured copy bandwidth.
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun (N > 1) every rank runs its own lattice (replicas; the step
 has no data-path exchange in this form) and the whole-job MLUPS is reported.
+
+Besides the headline line's value, roofline, e2e (public API with pinned host
+buffers), cpu_baseline (the FP64 oracle on the host cores) and clocks, the
+JSON line carries the other forms of the step, each on the same GPU:
+fp16_storage (half-precision populations), d2q5_fl (D2Q5 phase-field and
+solute sets), batched (256 droplets in one launch per step, FP32 and FP16
+storage, against stepping them one by one), droplet_freezing (a 512^2
+droplet run to full freezing, FP32 and FP16), and surrogate (the learned
+surrogate trained here, its jumps against the LB alone, and its tensor-core
+forward pass).  --sur-forward-only times the surrogate's forward pass alone.
 """
 from __future__ import annotations
 
