@@ -40,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_UPDATE = 360  # 36 populations read + written, 9 lagged fields read + written, FP32
+NAMEPLATE_HBM_GBS = 7900.0  # HBM3e nameplate of one GB300, next to the measured copy bandwidth
 WORKLOAD = dict(name="impurity_front", nx=4096, ny=4096)
 PROFILE = os.path.join(ROOT, "profiles", "lb_step_kernel_impurity_front.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2511_09422_gb300", "csrc", "lb_kernels.cuh")
@@ -529,6 +530,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks.get("hbm_gbs"),
                      "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs"), 4),
                      "peak_source": src, "bytes_per_update": BYTES_PER_UPDATE,
+                     "frac_of_nameplate": round(achieved / NAMEPLATE_HBM_GBS, 4),
                      "traffic": None if traffic is None else round(traffic)},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d),
