@@ -237,7 +237,7 @@ class SurrogateStepper:
 
     def __init__(self, solver: lbfreeze.Solver, net: cno.Net, norm: Normaliser, params: dict, k=K_JUMP,
                  mass_tol=1e-3, width_tol=0.05, h_tol=0.02, jumps_per_lb=2, max_backoff=64, phi_band=0.999,
-                 slow_only=True, h_project=False):
+                 slow_only=True, h_project=False, device="cuda"):
         import torch
         self.s, self.net, self.norm, self.k = solver, net, norm, k
         self.rho_s, self.rho_l = float(params["rho_s"]), float(params["rho_l"])
@@ -248,11 +248,11 @@ class SurrogateStepper:
         self.jumps_per_lb, self.max_backoff = jumps_per_lb, max_backoff
         self.phi_band, self.slow_only, self.h_project = phi_band, slow_only, h_project
         ny, nx = solver.ny, solver.nx
-        mk = lambda: {f: torch.empty((ny, nx), dtype=torch.float32, device="cuda") for f in FIELDS}
+        mk = lambda: {f: torch.empty((ny, nx), dtype=torch.float32, device=device) for f in FIELDS}
         self.cur, self.pred = mk(), mk()
         self.scratch = mk() if h_project else None
-        self.x = torch.empty((1, ny, nx, cno.CIN), dtype=torch.bfloat16, device="cuda")
-        self.out = torch.empty((1, ny, nx, cno.NF), dtype=torch.float32, device="cuda")
+        self.x = torch.empty((1, ny, nx, cno.CIN), dtype=torch.bfloat16, device=device)
+        self.out = torch.empty((1, ny, nx, cno.NF), dtype=torch.float32, device=device)
         self.accepted = self.rejected = self.lb_chunks = 0
         self._wait, self._backoff, self._jumps = 0, 1, 0
         self.h_rate = None
