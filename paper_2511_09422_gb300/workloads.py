@@ -248,6 +248,30 @@ def wetting_droplet(nx=80, ny=40, radius=16.0, theta_wall=60.0, theta0=90.0, sig
                 steps=steps, meta=dict(radius=radius, theta_wall=theta_wall, theta0=theta0))
 
 
+def liquid_bridge(nx=72, ny=48, half_width=14.0, theta_bottom=60.0, theta_top=45.0, c0=0.05, rho_g=0.1,
+                  T_wall=-1.0, T_top=0.5, ste=0.1, perturb=1e-3, seed=7, steps=100) -> dict:
+    """A binary liquid column spanning the channel from wall to wall (|x - x_c|
+    < half_width, x_c the middle of the lattice), so that its interface meets
+    both walls: bottom wall Dirichlet T_wall (freezing) with contact angle
+    theta_bottom, top wall Dirichlet T_top with theta_top; the sessile
+    droplet's properties (rho_s / rho_l 0.9, k_p 0.5, D_l 0.05, D_s 0.005,
+    sigma0 0.01) with fixed sigma_T = -1e-3 and sigma_c = -2e-2; seeded
+    uniform noise of amplitude ``perturb`` on T (upwards) and, relative, on C."""
+    x, y = _coords(nx, ny)
+    d = half_width - np.abs(x - (nx - 1) / 2.0)
+    phi = tanh_profile(d)
+    rng = np.random.default_rng(seed)
+    T = perturb * rng.uniform(0.0, 1.0, size=phi.shape)
+    C = np.where(phi > 0, c0, 0.0) * (1.0 + perturb * rng.uniform(-1.0, 1.0, size=phi.shape))
+    p = base_params(rho_s=0.9, T_sol=0.0, T_liq=0.0, latent=1.0 * (0.0 - T_wall) / ste, k_p=0.5, D_l=0.05,
+                    D_s=0.005, sigma0=0.01, sigma_T=-1e-3, sigma_c=-2e-2, T_ref=0.0, c_ref=c0)
+    p = gas_properties(p, rho_g)
+    g = grid(nx, ny, WALL_DIRICHLET_T, WALL_DIRICHLET_T, T_bottom=T_wall, T_top=T_top,
+             theta_bottom=theta_bottom, theta_top=theta_top)
+    return dict(name="liquid_bridge_%dx%d" % (nx, ny), grid=g, params=p, fields=_fields(phi, T, C), steps=steps,
+                meta=dict(half_width=half_width, theta_bottom=theta_bottom, theta_top=theta_top, c0=c0))
+
+
 def droplet_sweep(n=256, seed=20251109, side_min=128, side_max=512, rho_g=0.1, steps=1000,
                   theta_range=(60.0, 120.0)) -> list:
     """A parameter sweep of independent freezing sessile droplets (the batched
@@ -304,6 +328,7 @@ def thermocapillary_migration(radius=20.0, T_c=0.0, T_h=32.0, sigma0=2.5e-3, sig
 WORKLOADS = {
     "thermocapillary_migration": thermocapillary_migration,
     "wetting_droplet": wetting_droplet,
+    "liquid_bridge": liquid_bridge,
     "stefan_layer": stefan_layer,
     "thermocapillary_channel": thermocapillary_channel,
     "sessile_droplet": sessile_droplet,

@@ -126,23 +126,33 @@ def test_parity_100_steps(oracle_mod, name, make, steps):
     _assert_reduce(red, wred)
 
 
-@pytest.mark.parametrize("shape", [(1, 40), (2, 17), (31, 1), (5, 3), (30, 30), (31, 31), (60, 61),
-                                   (61, 5), (240, 36), (121, 37), (125, 97)])
-def test_parity_edge_shapes(oracle_mod, shape):
-    """A one-column lattice (x-periodic onto itself), a one-row lattice (both
-    walls on the same row), shapes at and just past a 30-column warp strip and
-    a 4-strip block, and row counts at the edges of the row layout: one inner
-    row (ny = 5), exactly one 32-row inner segment (ny = 36), and a last inner
-    segment of 1 row (ny = 37) or of 29 rows (ny = 97).
-    Equal solid and liquid densities: in a one-row lattice the expansion
-    source drives phi far above 1 and makes the case ill-conditioned."""
-    nx, ny = shape
+EDGE_SHAPES = [(1, 40), (2, 17), (31, 1), (5, 3), (30, 30), (31, 31), (60, 61), (61, 5), (240, 36), (121, 37),
+               (125, 97)]
+
+
+def edge_workload(nx, ny):
+    """The droplet parity case cut to nx x ny (centred in x), with equal solid
+    and liquid density and viscosity."""
     w = W.parity_droplet(nx=max(nx, 8), ny=max(ny, 8))
     w["params"] = dict(w["params"], rho_s=w["params"]["rho_l"], mu_s=w["params"]["mu_l"])
     x0 = (max(nx, 8) - nx) // 2
     for k in w["fields"]:
         w["fields"][k] = np.ascontiguousarray(w["fields"][k][:ny, x0:x0 + nx])
     w["grid"] = dict(w["grid"], nx=nx, ny=ny)
+    return w
+
+
+@pytest.mark.parametrize("shape", EDGE_SHAPES)
+def test_parity_edge_shapes(oracle_mod, shape):
+    """A one-column lattice (x-periodic onto itself), a one-row lattice (both
+    walls on the same row), shapes at and just past a 30-column warp strip and
+    a 4-strip block, and row counts at the edges of the row layout (2-row
+    wall bands, then inner segments, 8 rows long at these sizes): one inner
+    row (ny = 5), whole segments only (ny = 36), and a last inner segment of
+    1 row (ny = 37) or of 5 rows (ny = 97).
+    Equal solid and liquid densities: in a one-row lattice the expansion
+    source drives phi far above 1 and makes the case ill-conditioned."""
+    w = edge_workload(*shape)
     got, red, want, wred = _run_pair(oracle_mod, w, 30)
     _assert_parity(got, want, label=str(shape))
 
