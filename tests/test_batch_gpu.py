@@ -114,3 +114,37 @@ def test_batch_create_reports_the_bad_instance():
         lbfreeze.Batch(ws)
     assert e.value.status == lbfreeze.LB_ERR_INVALID_ARG
     assert "instance 1" in str(e.value)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_sweep_sampled_instances(oracle_mod, storage):
+    """The benchmark's batch at full size: the 256-droplet sweep (28.4 M cells,
+    sides 128..512, contact angles 60..120 degrees), autotuned and stepped
+    through the CUDA graph as the benchmark does, in FP32 and in half storage.
+    Sampled instances (the smallest, the largest, two seeded picks) equal lone
+    lattices bit for bit; the smallest also matches the oracle at the FP32
+    parity bar (FP32 storage)."""
+    import test_parity_gpu as P
+    sweep = W.droplet_sweep(n=256)
+    for w in sweep:
+        w["params"] = dict(w["params"], pop_storage=storage)
+        w["fields"] = _f32(w)
+    sides = [w["meta"]["side"] for w in sweep]
+    rng = np.random.default_rng(3)
+    picks = sorted({int(np.argmin(sides)), int(np.argmax(sides))} | set(int(i) for i in rng.integers(0, 256, 2)))
+    b = lbfreeze.Batch(sweep)
+    b.tune(trials=1)
+    b.use_graph(True)
+    steps = 7
+    b.step(steps)
+    for i in picks:
+        _assert_same(b.instance(i).fields(), _single(sweep[i], steps), "sweep instance %d" % i)
+    if storage == 0:
+        i = int(np.argmin(sides))
+        w = sweep[i]
+        o = oracle_mod.Oracle(w["grid"], w["params"], {k: v.astype(np.float64) for k, v in w["fields"].items()})
+        o.step(steps)
+        want = o.fields()
+        want["_walls"] = P._wall_temperatures(w["grid"])
+        P._assert_parity(b.instance(i).fields(), want, label="sweep instance %d" % i)
+    b.close()

@@ -49,6 +49,17 @@ def test_parity_d2q5(oracle_mod, name, make, steps):
     P._assert_reduce(red, wred)
 
 
+
+def test_d2q5_full_size_bench_workload(oracle_mod):
+    """The 4096 x 4096 impurity front with D2Q5 f and l, as the benchmark's
+    D2Q5 leg runs it, a few steps against the oracle on every cell."""
+    w = _q5(W.impurity_front(nx=4096, ny=4096))
+    got, red, want, wred = P._run_pair(oracle_mod, w, 3, params=w["params"])
+    errs = P._rel_errors(got, want)
+    bad = {k: v for k, v in errs.items() if not v <= TOL_Q5[k]}
+    assert not bad, (bad, errs)
+    P._assert_reduce(red, wred)
+
 def test_d2q5_freezing_time(oracle_mod):
     from paper_2511_09422_gb300 import lbfreeze
     w = _q5(W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.2))

@@ -43,6 +43,15 @@ def test_fp16_fields_against_oracle(oracle_mod, name, make, steps):
     assert all(np.isfinite(got[k]).all() for k in P.FIELDS)
 
 
+
+def test_fp16_full_size_bench_workload(oracle_mod):
+    """The 4096 x 4096 impurity front in half storage, as the benchmark's
+    half-storage leg runs it, a few steps against the oracle on every cell."""
+    w = W.impurity_front(nx=4096, ny=4096)
+    got, red, want, wred = P._run_pair(oracle_mod, w, 3, params=_half(w)["params"])
+    errs = P._rel_errors(got, want)
+    assert all(v <= FIELD_TOL for v in errs.values()), errs
+
 def test_fp16_freezing_time(oracle_mod):
     w = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.2)
     f32 = P._f32(w)
