@@ -352,6 +352,8 @@ def _surrogate_leg(args, torch, peaks):
     tf_p, dt_p, st_p = S.freezing_time(held, net, norm, h_project=True)
     # forward pass of the network on the large lattice, timed with CUDA events
     x = torch.zeros((1, args.size, args.size, cno.CIN), dtype=torch.bfloat16, device="cuda")
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x[..., :cno.NF] = torch.randn((1, args.size, args.size, cno.NF), generator=gen, device="cuda").to(torch.bfloat16)
     out = torch.empty((1, args.size, args.size, cno.NF), dtype=torch.float32, device="cuda")
     for _ in range(2):
         net.forward(x, out=out)

@@ -243,10 +243,12 @@ struct ConvShape {
     static constexpr int A_BYTES = BM * ROW_BYTES;
     static constexpr int B_BYTES = BN * ROW_BYTES;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    // BN <= 128: two CTAs per SM, about 96 KB of stages each; BN = 256: one CTA
-    // per SM (its two accumulators fill the 512 tensor-memory columns), 4 stages
-    static constexpr int CTAS_PER_SM = BN >= 256 ? 1 : 2;
-    static constexpr int STAGES = BN >= 256 ? 4 : ((96 * 1024 / STAGE) < 2 ? 2 : (96 * 1024 / STAGE));
+    // BN = 64: three CTAs per SM with 3 stages of 24 KB each (measured 4 % faster
+    // over the whole forward pass than two CTAs with 4 stages); BN = 128: two
+    // CTAs per SM, 96 KB of stages each (their accumulators fill the 512
+    // tensor-memory columns); BN = 256: one CTA per SM, 4 stages
+    static constexpr int CTAS_PER_SM = BN >= 256 ? 1 : (BN == 64 ? 3 : 2);
+    static constexpr int STAGES = BN >= 256 ? 4 : (BN == 64 ? 3 : ((96 * 1024 / STAGE) < 2 ? 2 : (96 * 1024 / STAGE)));
     static constexpr int BAR_BYTES = 256;
     static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + BAR_BYTES + BN * 4 /* bias */;
     static constexpr int TMEM_COLS = 2 * BN;  // two FP32 accumulators
