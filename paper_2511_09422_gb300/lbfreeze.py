@@ -145,6 +145,18 @@ def _is_cuda_tensor(a) -> bool:
     return _is_torch(a) and bool(a.is_cuda)
 
 
+def _torch_stream(stream_obj):
+    """The torch stream object of a handle's stream: the legacy default stream
+    for None, the object itself for a torch stream, else an external stream
+    over the raw cudaStream_t."""
+    import torch
+    if isinstance(stream_obj, torch.cuda.Stream):
+        return stream_obj
+    ptr = stream_obj if isinstance(stream_obj, int) or stream_obj is None else getattr(stream_obj, "cuda_stream",
+                                                                                      stream_obj)
+    return torch.cuda.ExternalStream(int(ptr)) if ptr else torch.cuda.default_stream()
+
+
 def _host_array(v) -> np.ndarray:
     """A float32 numpy view of host data; a torch CPU tensor (pinned or not) is
     viewed in place, so a pinned buffer stays the one the copy reads from."""
@@ -193,6 +205,9 @@ class Solver:
             else:
                 setattr(f, k, v.ctypes.data_as(_fp))
         f.on_device = 1 if on_device else 0
+        if on_device:
+            import torch
+            torch.cuda.current_stream().synchronize()  # the inputs' producers have finished
         h = C.c_void_p()
         st = L.lb_create(C.byref(self._grid), C.byref(self._params), C.byref(f), C.byref(h))
         if st != LB_OK:
@@ -218,7 +233,7 @@ class Solver:
         s = cls.__new__(cls)
         s.nx, s.ny = nx, ny
         s._h = C.c_void_p(handle)
-        s._stream_obj = None
+        s._stream_obj = getattr(owner, "_stream_obj", None)
         s._owner = owner
         return s
 
@@ -287,7 +302,7 @@ class Solver:
                 if not ok:
                     raise ValueError("fields(out=...): %s must be contiguous float32 with nx*ny values" % k)
                 ptrs.append(C.c_void_p(ptr))
-            self._check(load().lb_get_fields(self._h, *ptrs, 1 if device else 0))
+            self._get_fields(ptrs, device)
             return out
         if device:
             import torch
@@ -296,8 +311,22 @@ class Solver:
         else:
             out = {k: np.empty((self.ny, self.nx), dtype=np.float32) for k in names}
             ptrs = [C.c_void_p(out[k].ctypes.data) if k in out else None for k in FIELD_NAMES]
-        self._check(load().lb_get_fields(self._h, *ptrs, 1 if device else 0))
+        self._get_fields(ptrs, device)
         return out
+
+    def _get_fields(self, ptrs, device: bool):
+        """lb_get_fields into device or host pointers.  Device outputs are
+        written on the handle's stream and read by torch on its current stream,
+        so the current stream waits for the handle's before and after: the
+        outputs' earlier users have finished, and later ones see the values."""
+        if not device:
+            self._check(load().lb_get_fields(self._h, *ptrs, 0))
+            return
+        import torch
+        hs, cur = _torch_stream(self._stream_obj), torch.cuda.current_stream()
+        hs.wait_stream(cur)
+        self._check(load().lb_get_fields(self._h, *ptrs, 1))
+        cur.wait_stream(hs)
 
     def set_fields(self, fields: dict):
         """Replace the state by the equilibrium of the given fields (keys of
@@ -324,7 +353,16 @@ class Solver:
                     raise ValueError("set_fields: %s must have nx*ny values" % k)
                 keep.append(a)
                 ptrs.append(C.c_void_p(a.ctypes.data))
-        self._check(load().lb_set_fields(self._h, *ptrs, 1 if device else 0))
+        if not device:
+            self._check(load().lb_set_fields(self._h, *ptrs, 0))
+            return
+        # device inputs: the handle's stream reads them after torch's producers,
+        # and torch's later writers wait for that read
+        import torch
+        hs, cur = _torch_stream(self._stream_obj), torch.cuda.current_stream()
+        hs.wait_stream(cur)
+        self._check(load().lb_set_fields(self._h, *ptrs, 1))
+        cur.wait_stream(hs)
 
     def reduce(self) -> np.ndarray:
         out = (C.c_double * 8)()
@@ -385,6 +423,7 @@ class Batch:
         self._keep = []
         self._h = h
         self.n = n
+        self._stream_obj = None
         if stream is not None:
             self.set_stream(stream)
 

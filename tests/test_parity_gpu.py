@@ -225,6 +225,37 @@ def test_torch_stream_and_device_io(oracle_mod):
     _assert_parity(got, want, label="torch I/O")
 
 
+
+def test_device_fields_ordered_across_streams():
+    """A solver on a stream of its own hands device fields to work on torch's
+    current stream, and takes them back, with no synchronisation by the
+    caller: after a long queue of steps on the solver's stream, the fields
+    read on the current stream, and the state set from tensors made there,
+    equal those of a solver on the current stream bit for bit."""
+    w = W.parity_droplet(nx=512, ny=512)
+    f32 = _f32(w)
+    side = torch.cuda.Stream()
+    s = lbfreeze.Solver(w["grid"], w["params"], f32, stream=side)
+    ref = lbfreeze.Solver(w["grid"], w["params"], f32)
+    s.step(300)
+    d = s.fields(device=True)
+    got = {k: v.cpu().numpy() for k, v in d.items()}   # read on the current stream
+    ref.step(300)
+    want = ref.fields()
+    for k in FIELDS:
+        assert np.array_equal(got[k], want[k]), k
+    back = {k: (v * 1.0) for k, v in d.items()}         # made on the current stream
+    s.set_fields(back)
+    del back, d
+    ref.set_fields(want)
+    s.step(20)
+    ref.step(20)
+    a, b = s.fields(), ref.fields()
+    for k in FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+    s.close()
+    ref.close()
+
 def test_checkpoint_resume_bitwise(tmp_path):
     w = W.parity_droplet(nx=64, ny=48)
     f32 = _f32(w)
