@@ -251,8 +251,8 @@ lb_status lb_batch_instance(lb_batch *b, int i, lb_handle **out);
 /* Number of instances and total cells (either pointer may be NULL). */
 lb_status lb_batch_size(const lb_batch *b, int *n, long long *cells);
 
-/* Message of the last failure on the batch (or of the last failed
- * lb_batch_create when b is NULL); never NULL. */
+/* Message of the last failure on the batch (or of the calling thread's last
+ * failed lb_batch_create when b is NULL); never NULL. */
 const char *lb_batch_last_error(const lb_batch *b);
 
 /* Free the batch and all of its instances; NULL is a no-op. */
@@ -261,8 +261,8 @@ void lb_batch_destroy(lb_batch *b);
 /* Static description of a status code. */
 const char *lb_error_string(int status);
 
-/* Message of the last failure on this handle (or of the last failed
- * lb_create when h is NULL); never NULL. */
+/* Message of the last failure on this handle (or of the calling thread's
+ * last failed lb_create when h is NULL); never NULL. */
 const char *lb_last_error(const lb_handle *h);
 
 /* Device bytes held by the handle. */

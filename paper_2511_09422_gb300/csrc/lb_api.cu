@@ -44,7 +44,7 @@ struct lb_handle {
     size_t bytes = 0;
 };
 
-static std::string g_create_error = "";
+static thread_local std::string g_create_error;  // last lb_create failure of this thread
 
 static const char *k_status_text[] = {"ok", "invalid argument", "CUDA error", "out of device memory",
                                       "unstable: a non-finite value was produced"};
@@ -742,7 +742,7 @@ struct lb_batch {
     std::string err;
 };
 
-static std::string g_batch_create_error;
+static thread_local std::string g_batch_create_error;  // last lb_batch_create failure of this thread
 
 static lb_status bfail(lb_batch *b, lb_status s, const std::string &msg)
 {

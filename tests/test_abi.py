@@ -90,6 +90,31 @@ def test_invalid_arguments_rejected_without_a_device(lib, bad):
     assert lib.lb_last_error(None)
 
 
+
+def test_create_error_message_is_per_thread(lib):
+    """lb_last_error(NULL) is the calling thread's last lb_create failure: a
+    failure in another thread neither shows nor overwrites it."""
+    import threading
+    w = W.stefan_layer(nx=8, ny=8, h0=4)
+    st, _ = _create(lib, w["grid"], dict(w["params"], eps=0.0), 64)
+    assert st == lbfreeze.LB_ERR_INVALID_ARG
+    mine = lib.lb_last_error(None)
+    assert b"eps" in mine
+    seen = {}
+
+    def other():
+        seen["before"] = lib.lb_last_error(None)
+        st2, _ = _create(lib, dict(w["grid"], nx=0), w["params"], 64)
+        seen["status"] = st2
+        seen["after"] = lib.lb_last_error(None)
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["before"] == b""
+    assert seen["status"] == lbfreeze.LB_ERR_INVALID_ARG and b"nx" in seen["after"]
+    assert lib.lb_last_error(None) == mine
+
 def test_null_arguments(lib):
     assert lib.lb_create(None, None, None, None) == lbfreeze.LB_ERR_INVALID_ARG
     assert lib.lb_step(None, 1) == lbfreeze.LB_ERR_INVALID_ARG
