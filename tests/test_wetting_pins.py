@@ -20,10 +20,13 @@ def _built():
     oracle.build_oracle()
 
 
+@pytest.mark.parametrize("lattice_fl", [0, 1], ids=["D2Q9", "D2Q5"])
 @pytest.mark.parametrize("theta", [60.0, 120.0])
-def test_droplet_relaxes_to_the_wall_contact_angle(theta):
+def test_droplet_relaxes_to_the_wall_contact_angle(theta, lattice_fl):
+    """The wall condition acts on the stencils of phi, so it holds with either
+    lattice of the phase-field set."""
     w = W.wetting_droplet(theta_wall=theta)
-    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o = oracle.Oracle(w["grid"], dict(w["params"], lattice_fl=lattice_fl), w["fields"])
     o.step(9000)
     got, radius, _ = analytic.contact_angle_bottom(o.fields()["phi"])
     assert abs(got - theta) <= 2.0, (theta, got)
