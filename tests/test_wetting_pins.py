@@ -34,6 +34,43 @@ def test_droplet_relaxes_to_the_wall_contact_angle(theta, lattice_fl):
     assert abs(o.reduce()[0] - float(np.sum(w["fields"]["phi"]))) <= 1e-9 * w["fields"]["phi"].size
 
 
+
+def _bridge(theta_b, theta_t, nx=96, ny=40, half=18.0, sigma=0.01):
+    """A liquid column |x - x_c| < half spanning the channel between two
+    adiabatic walls of contact angles theta_b and theta_t: equal densities,
+    no phase change, no solute, uniform temperature."""
+    x, y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))
+    phi = W.tanh_profile(half - np.abs(x - (nx - 1) / 2.0))
+    z = np.zeros_like(phi)
+    p = W.gas_properties(W.base_params(sigma0=sigma, phase_change_on=0, latent=0.0), 1.0, lam_ratio=1.0)
+    g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC, theta_bottom=theta_b, theta_top=theta_t)
+    return g, p, dict(phi=phi, T=z, C=z.copy(), ux=z.copy(), uy=z.copy())
+
+
+@pytest.mark.parametrize("theta_b,theta_t", [(60.0, 60.0), (120.0, 120.0), (45.0, 75.0)])
+def test_liquid_bridge_laplace_pressure(theta_b, theta_t):
+    """Between parallel walls a distance H apart, each free interface of a
+    liquid bridge settles at a circular arc that meets the walls at their
+    angles, so its curvature is (cos theta_b + cos theta_t) / H and the
+    liquid's pressure differs from the gas's by -sigma (cos theta_b +
+    cos theta_t) / H (below it for wetting walls, above it for non-wetting
+    ones).  As in the static-droplet Laplace pin, the isotropic gradient
+    integrates the capillary force of the W = 4 profile to 0.939 of its
+    exact value, which is the jump to expect on the lattice."""
+    nx, ny, sigma = 96, 40, 0.01
+    g, p, f = _bridge(theta_b, theta_t, nx=nx, ny=ny, sigma=sigma)
+    o = oracle.Oracle(g, p, f)
+    o.step(8000)
+    P = o.fields()["p"]
+    xc = (nx - 1) // 2
+    p_liquid = P[8:32, xc - 3:xc + 4].mean()
+    p_gas = np.concatenate([P[8:32, :4], P[8:32, -4:]], axis=1).mean()
+    j = np.arange(-40, 40) + 0.5
+    d = np.gradient(np.tanh(j / 2.0))
+    discrete = float((3 * math.sqrt(2) * W.EPS / 4 * d[2:-2] ** 2).sum())
+    want = -sigma * (math.cos(math.radians(theta_b)) + math.cos(math.radians(theta_t))) / ny * discrete
+    assert abs((p_liquid - p_gas) / want - 1.0) < 0.03, (p_liquid - p_gas, want)
+
 def test_ninety_degree_wall_keeps_the_half_disc():
     w = W.wetting_droplet(theta_wall=90.0)
     assert w["grid"]["cos_theta_bottom"] == 0.0
