@@ -373,6 +373,31 @@ def test_no_solid_reduction(oracle_mod):
         assert np.array_equal(fa[k], fb[k]), k
 
 
+
+@pytest.mark.parametrize("rho_top", [1.0, 0.5, 0.1])
+def test_hydrostatic_pressure_under_gravity(oracle_mod, rho_top):
+    """Two layers at rest between adiabatic walls under the body force
+    F_b = rho g (reading R21): at steady state dp/dy = rho g in each layer,
+    rho_l = 1 below and rho_top above, without surface tension.  A shorter,
+    more viscous column (32 rows, nu = 0.3) damps the start-up sound waves
+    within the run."""
+    nx, ny, h, gy = 8, 32, 16, -1e-5
+    y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))[1]
+    phi = W.tanh_profile((h - 0.5) - y)
+    z = np.zeros_like(phi)
+    p = W.gas_properties(W.base_params(phase_change_on=0, latent=0.0, gy=gy, sigma0=0.0), rho_top, nu=0.3,
+                         lam_ratio=1.0)
+    g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    o = oracle_mod.Oracle(g, p, dict(phi=phi, T=z, C=z.copy(), ux=z.copy(), uy=z.copy()))
+    o.step(6000)
+    f = o.fields()
+    prof = f["p"].mean(axis=1)
+    slope_low = np.polyfit(np.arange(3, 11), prof[3:11], 1)[0]
+    slope_high = np.polyfit(np.arange(21, 29), prof[21:29], 1)[0]
+    assert abs(slope_low / (p["rho_l"] * gy) - 1) < 0.01, slope_low
+    assert abs(slope_high / (rho_top * gy) - 1) < 0.01, slope_high
+    assert np.sqrt(f["ux"] ** 2 + f["uy"] ** 2).max() < 1e-5
+
 def test_table1_final_height(oracle_mod):
     """Table 1 (tests/golden): a film freezes completely in a closed box and its
     final height is h_0 rho_l / rho_s by mass conservation.  In a closed box the
