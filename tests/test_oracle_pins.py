@@ -428,9 +428,15 @@ def test_droplet_expansion_end_state(oracle_mod):
     """Sec. 4.4 (tests/golden): a freezing droplet with rho_s / rho_l = 0.9 ends
     at V*_sl = 1.1107, 3.7e-4 from the mass-conservation value 1 / 0.9.  The
     oracle with the velocity-divergence source (divu_mode = 1, as for Table 1)
-    reaches 1 / 0.9 within 1e-3 on a 48 x 40 lattice (R = 12, Ste = 0.15) once
-    the droplet is solid; with the model value mdot (divu_mode = 0) the closed
-    box's gas takes up most of the expansion and V*_sl stays near 1.04."""
+    reaches 1 / 0.9 within 1e-3 on a 48 x 40 lattice (R = 12, Ste = 0.15,
+    nu = 0.1 in every phase as in all workloads here) once the droplet is
+    solid; with the model value mdot (divu_mode = 0) the closed box's gas takes
+    up most of the expansion and V*_sl stays near 1.04.  The end state moves
+    with the viscosity (1.120 at nu = 0.05, 1.100 at 0.2): part of the
+    expansion goes into compressing the gas, by an amount the viscous damping
+    of the start-up flow sets, so this pins the configuration at nu = 0.1.
+    It fails when the pressure's G_0 term takes tau = 1, 1/2, 2 tau_g or is
+    dropped (reading R8)."""
     kv = dict(r.split("=") for r in _golden("printed_numbers.txt"))
     kv = {k.strip(): float(v) for k, v in kv.items()}
     assert abs(kv["droplet_final_Vsl"] * 0.9 - 1) <= kv["droplet_final_Vsl_error"] + 1e-5
