@@ -377,7 +377,8 @@ def test_no_solid_reduction(oracle_mod):
 @pytest.mark.parametrize("rho_top", [1.0, 0.5, 0.1])
 def test_hydrostatic_pressure_under_gravity(oracle_mod, rho_top):
     """Two layers at rest between adiabatic walls under the body force
-    F_b = rho g (reading R21): at steady state dp/dy = rho g in each layer,
+    F_b = rho g (g is not printed; it is zero unless set): at steady state
+    dp/dy = rho g in each layer,
     rho_l = 1 below and rho_top above, without surface tension.  A shorter,
     more viscous column (32 rows, nu = 0.3) damps the start-up sound waves
     within the run."""
@@ -435,8 +436,8 @@ def test_droplet_expansion_end_state(oracle_mod):
     with the viscosity (1.120 at nu = 0.05, 1.100 at 0.2): part of the
     expansion goes into compressing the gas, by an amount the viscous damping
     of the start-up flow sets, so this pins the configuration at nu = 0.1.
-    It fails when the pressure's G_0 term takes tau = 1, 1/2, 2 tau_g or is
-    dropped (reading R8)."""
+    It fails when the pressure's G_0 term, whose relaxation time the paper
+    leaves unnamed (taken as tau_g), takes tau = 1, 1/2, 2 tau_g or is dropped."""
     kv = dict(r.split("=") for r in _golden("printed_numbers.txt"))
     kv = {k.strip(): float(v) for k, v in kv.items()}
     assert abs(kv["droplet_final_Vsl"] * 0.9 - 1) <= kv["droplet_final_Vsl_error"] + 1e-5
