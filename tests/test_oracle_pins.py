@@ -378,10 +378,9 @@ def test_no_solid_reduction(oracle_mod):
 def test_hydrostatic_pressure_under_gravity(oracle_mod, rho_top):
     """Two layers at rest between adiabatic walls under the body force
     F_b = rho g (g is not printed; it is zero unless set): at steady state
-    dp/dy = rho g in each layer,
-    rho_l = 1 below and rho_top above, without surface tension.  A shorter,
-    more viscous column (32 rows, nu = 0.3) damps the start-up sound waves
-    within the run."""
+    dp/dy = rho g in each layer, rho_l = 1 below and rho_top above, without
+    surface tension.  A short, viscous column (32 rows, nu = 0.3) damps the
+    start-up sound waves within the run."""
     nx, ny, h, gy = 8, 32, 16, -1e-5
     y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))[1]
     phi = W.tanh_profile((h - 0.5) - y)
