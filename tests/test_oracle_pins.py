@@ -339,8 +339,12 @@ def test_poiseuille(oracle_mod):
 
 
 def test_solid_drag(oracle_mod):
-    """The solid-liquid interaction force f = f_s (0 - u*) keeps a frozen region at
-    rest under the same body force that drives a Poiseuille flow."""
+    """The solid-liquid interaction force f = f_s (0 - u*) holds a frozen region
+    under the same body force that drives a Poiseuille flow.  In a uniform
+    solid (f_s = 1) the printed rules rho u* = sum c_i g_i + F/2, u = u* + f/2
+    and the first moment F + rho f of the source G_i have the steady state
+    sum c_i g_i = F/2, so u* = F/rho and u = F/(2 rho) exactly: away from the
+    walls the velocity is g_x / 2."""
     ny, gx = 24, 1e-6
     p = W.base_params(sigma0=0.0, gx=gx)
     g = W.grid(2, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
@@ -349,6 +353,7 @@ def test_solid_drag(oracle_mod):
     f = o.fields()
     assert f["fs"].min() > 1 - 1e-9
     assert np.abs(f["ux"]).max() < 2 * gx
+    assert np.abs(f["ux"][8:16] / gx - 0.5).max() < 1e-6
 
 
 def test_no_solid_reduction(oracle_mod):
