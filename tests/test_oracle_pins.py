@@ -234,6 +234,50 @@ def test_neumann_superheated(oracle_mod):
     assert abs(s / A.neumann_front(4000, kappa, p["lam_s"]) - 1) < 1e-2, s
 
 
+
+def test_solute_diffuses_at_the_solid_diffusivity(oracle_mod):
+    """Inside the solid (f_s = 1) the effective diffusivity D_e / k_eff of
+    Sec. 3.4 is k_p D_s / k_p = D_s: a Gaussian pulse spreads with variance
+    s0^2 + 2 D_s t per direction, as in the liquid pin, not with k_p D_s."""
+    nx = ny = 64
+    s0, Ds, steps = 4.0, 0.02, 400
+    y, x = np.meshgrid(np.arange(ny, dtype=np.float64), np.arange(nx, dtype=np.float64), indexing="ij")
+    C = 0.05 * np.exp(-((x - nx / 2) ** 2 + (y - ny / 2) ** 2) / (2 * s0 * s0))
+    p = W.base_params(D_l=0.05, D_s=Ds, k_p=0.5, sigma0=0.0, latent=10.0, T_sol=0.0, T_liq=0.0)
+    g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+    z = np.zeros_like(C)
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones_like(C), T=np.full_like(C, -1.0), C=C, ux=z, uy=z.copy()))
+    o.step(steps)
+    f = o.fields()
+    assert f["fs"].min() == 1.0
+    m = f["C"].sum()
+    xc = (f["C"] * x).sum() / m
+    var_x = (f["C"] * (x - xc) ** 2).sum() / m
+    want = s0 * s0 + 2 * Ds * steps
+    assert abs(var_x / want - 1) < 0.01, (var_x, want)
+
+
+def test_solute_partition_at_a_stationary_front(oracle_mod):
+    """A column frozen below its middle and liquid above (walls at T = -1 and
+    +1, linear steady temperature, so the front stays put): the solute
+    relaxes until the pseudo-potential C / k_eff is uniform, i.e. C_solid /
+    C_liquid = k_p, through the flux correction of R in Sec. 3.4.  The
+    one-cell front leaves a discretisation error of 7 % (0.467 for k_p = 0.5);
+    without the correction the ratio is 1, with its sign flipped 2.1."""
+    nx, ny, kp = 4, 64, 0.5
+    y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))[1]
+    p = W.base_params(D_l=0.05, D_s=0.05, k_p=kp, sigma0=0.0, latent=10.0, T_sol=0.0, T_liq=0.0)
+    g = W.grid(nx, ny, W.WALL_DIRICHLET_T, W.WALL_DIRICHLET_T, T_bottom=-1.0, T_top=1.0)
+    z = np.zeros((ny, nx))
+    o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, nx)), T=-1.0 + 2.0 * (y + 0.5) / ny,
+                                     C=np.full((ny, nx), 0.05), ux=z, uy=z.copy()))
+    o.step(40000)
+    f = o.fields()
+    assert f["fs"][:, 0].sum() == 32.0                         # the front has not moved
+    assert abs(f["C"].sum() / (0.05 * nx * ny) - 1) < 1e-10     # solute conserved
+    ratio = f["C"][4:24].mean() / f["C"][40:60].mean()
+    assert abs(ratio / kp - 1) < 0.1, ratio
+
 def test_binary_solidification(oracle_mod):
     """Sec. 4.3 without gas (phi = 1 everywhere; the model reduces to the classical
     enthalpy method for a binary material): front, temperature and the solute
