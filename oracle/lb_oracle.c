@@ -32,11 +32,11 @@
  *
  * Parity pins (what fixes each part independently of this code) live in the
  * CPU test-suite; every function here is pinned there, and
- * tests/mutate_oracle.py lists which planted slips the pins catch.  Three
+ * tests/mutate_oracle.py lists which planted slips the pins catch.  Two
  * terms of second order in the Mach number or the grid spacing are parity
- * unpinned by them: -grad p in the effective force of the flow source,
- * d_t(phi u) in the phase-field source, and the link-midpoint position of the
- * Dirichlet wall temperature in the anti-bounce-back rule.
+ * unpinned by them: d_t(phi u) in the phase-field source, and the
+ * link-midpoint position of the Dirichlet wall temperature in the
+ * anti-bounce-back rule.
  */
 #include <math.h>
 #include <stdlib.h>

@@ -36,7 +36,7 @@ M = [
  ("u = u* + f (no half)", "double ux = usx + 0.5 * ffx, uy = usy + 0.5 * ffy;", "double ux = usx + ffx, uy = usy + ffy;", 1),
  ("S without u.grad rho", "double S = rho * mdot + ux * grx + uy * gry;", "double S = rho * mdot;", 1),
  ("F~ without cs2 grad rho", "double Ftx = Fx - gPx + CS2 * grx + CS2 * gSx;", "double Ftx = Fx - gPx + CS2 * gSx;", 1),
- ("F~ without grad p", "double Ftx = Fx - gPx", "double Ftx = Fx", 1),
+ ("F~ without grad p", " - gP", " + 0.0 * gP", 2),
  ("pressure S/2 -> S", "(sg + 0.5 * S + tau_g * G0", "(sg + S + tau_g * G0", 1),
  ("pressure G0 with tau = 1", "tau_g * G0", "1.0 * G0", 1),
  ("g equilibrium without the rest term", "geq[i] = pr / CS2 * (WT[i] - (i == 0 ? 1.0 : 0.0))", "geq[i] = pr / CS2 * WT[i]", 1),

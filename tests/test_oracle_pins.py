@@ -382,6 +382,26 @@ def test_poiseuille(oracle_mod):
     assert np.abs(u - want).max() < 5e-3 * want.max()
 
 
+
+def test_transverse_gravity_leaves_the_shear_flow_unchanged(oracle_mod):
+    """A body force across the channel (g_y) is balanced by the hydrostatic
+    pressure it builds, so the Poiseuille flow along the channel must not
+    change.  In the flow source of Sec. 3.2 the force enters through the
+    effective force F~ = F - grad p + ..., whose cross terms with u would
+    otherwise shear the flow: dropping grad p from F~ changes the profile by
+    4 % at g_y = -3e-3; with it the change is 0.2 %."""
+    nx, ny, gx = 4, 32, 1e-5
+    def profile(gy):
+        p = W.base_params(sigma0=0.0, gx=gx, gy=gy, phase_change_on=0, latent=0.0)
+        g = W.grid(nx, ny, W.WALL_ADIABATIC, W.WALL_ADIABATIC)
+        z = np.zeros((ny, nx))
+        o = oracle_mod.Oracle(g, p, dict(phi=np.ones((ny, nx)), T=z, C=z.copy(), ux=z.copy(), uy=z.copy()))
+        o.step(20000)
+        return o.fields()["ux"][:, 0]
+    u0, u1 = profile(0.0), profile(-3e-3)
+    assert np.abs(u0 / A.poiseuille(np.arange(ny), ny, gx, 0.1) - 1).max() < 0.01
+    assert np.abs(u1 / u0 - 1).max() < 5e-3
+
 def test_solid_drag(oracle_mod):
     """The solid-liquid interaction force f = f_s (0 - u*) holds a frozen region
     under the same body force that drives a Poiseuille flow.  In a uniform
