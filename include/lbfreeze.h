@@ -85,8 +85,14 @@ typedef struct {
  * (gx, gy) the body-force acceleration (F_b = rho g).
  * fs_modulated_st: 1 multiplies the surface force by (1 - f_s) (Sec. 4.5).
  * phase_change_on: 0 drops the latent heat and keeps f_s = 0.
- * divu_mode: 0 takes div u = mdot (the model value of Eq. NS1) in the
- * phase-field and enthalpy sources; other values are rejected.
+ * divu_mode: which velocity divergence enters the div u terms of Sec. 3.1
+ * (the source w_i phi div u of F_i and the moment phi = sum f_i + phi div u/2)
+ * and Sec. 3.3 (H_i and rho H = sum h_i + rho Cp T div u/2).  0: the model
+ * value mdot of Eq. NS1.  1: the isotropic divergence (end of Sec. 3.4) of
+ * the previous step's velocity, with the ghost -u beyond a no-slip wall; the
+ * compression of the surrounding phase by the volume change then reaches the
+ * interface, which reproduces the final heights of Table 1 and the final
+ * droplet volume of Sec. 4.4.  Other values are rejected.
  * pop_storage: how the 36 population planes are stored.  LB_STORAGE_F32 (0):
  * FP32 deviations from lagged references.  LB_STORAGE_F16 (1): the same
  * deviations times 2^8 in IEEE half precision (the solute set shifted by
@@ -137,7 +143,7 @@ typedef struct lb_handle lb_handle;
  * Returns LB_ERR_INVALID_ARG for null pointers, nx or ny < 1, nx*ny above
  * LB_MAX_CELLS, a padded plane (nx rounded up to a multiple of 32, times ny)
  * of 2^31 floats or more, eps <= 0, non-positive densities, a relaxation time <= 1/2
- * anywhere in the property range, or divu_mode != 0.  *out is set only on
+ * anywhere in the property range, or divu_mode not 0 or 1.  *out is set only on
  * success.  Synchronises the device. */
 lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init,
                     lb_handle **out);

@@ -117,7 +117,7 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
     if (!(p->lam_l > 0 && p->lam_s > 0 && p->lam_g > 0)) return "conductivities must be > 0 (tau_h > 1/2)";
     if (!(p->D_l > 0) || p->D_s < 0) return "D_l must be > 0 and D_s >= 0 (tau_l > 1/2 in the liquid)";
     if (!(p->k_p > 0)) return "k_p must be > 0";
-    if (p->divu_mode != 0) return "divu_mode must be 0";
+    if (p->divu_mode != 0 && p->divu_mode != 1) return "divu_mode must be 0 or 1";
     if (p->pop_storage != LB_STORAGE_F32 && p->pop_storage != LB_STORAGE_F16)
         return "pop_storage must be LB_STORAGE_F32 or LB_STORAGE_F16";
     if (p->lattice_fl != LB_LATTICE_D2Q9 && p->lattice_fl != LB_LATTICE_D2Q5)
@@ -177,6 +177,7 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
             if (c < K.segh && nstrip * lbk::strip_segments(g->ny, K.segh) < 2 * wave) K.segh = c;
     }
     K.qfl = p->lattice_fl == LB_LATTICE_D2Q5 ? 5 : 9;
+    K.divu = p->divu_mode;
     K.phase_change = p->phase_change_on ? 1 : 0;
     return K;
 }

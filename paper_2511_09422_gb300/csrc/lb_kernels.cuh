@@ -120,8 +120,9 @@ struct Consts {
     real sigma0, sigma_T, sigma_c, T_ref, c_ref, gx, gy;
     real expand;                // 1 - rho_s / rho_l
     int fs_mod, phase_change;
-    int segh;
-    int qfl;                    // lattice of the phase-field and solute sets: 9 or 5 velocities                   // rows of an inner segment of the strip sweep
+    int segh;                   // rows of an inner segment of the strip sweep
+    int qfl;                    // lattice of the phase-field and solute sets: 9 or 5 velocities
+    int divu;                   // div u in the phi and h sources: 0 the model value mdot, 1 the lagged velocity divergence
 };
 
 struct Buffers {
@@ -384,6 +385,32 @@ __device__ __forceinline__ real aux_dev_sum(const Consts &K, const float *__rest
             wgt(7) * (aux_src<A, 7, W>(K, ain, x, y, cell) - own) + wgt(8) * (aux_src<A, 8, W>(K, ain, x, y, cell) - own));
 }
 
+// Lagged velocity component (plane A = AUX_UX or AUX_UY) at the stencil
+// neighbour (x + dx, y + dy); beyond a no-slip wall the ghost is -u of the
+// adjacent row (linear extrapolation through u = 0 at the half-way wall).
+template <int A, bool W>
+__device__ __forceinline__ real u_nb(const Consts &K, const float *__restrict__ ain, int x, int y, int dx, int dy)
+{
+    const int yy = y + dy, xx = wrapx(x + dx, K.nx);
+    const float *a = plane_ptr(ain, A, K);
+    if (W && (yy < 0 || yy >= K.ny)) return -__ldg(a + (y * K.pitch + xx));
+    return __ldg(a + (yy * K.pitch + xx));
+}
+
+// Isotropic divergence of the lagged velocity (end of Sec. 3.4 stencils):
+// 3 sum_i w_i (c_ix u_x + c_iy u_y)(x + c_i), written per component.
+template <bool W>
+__device__ __forceinline__ real lagged_divu(const Consts &K, const float *__restrict__ ain, int x, int y)
+{
+    const real dudx = wgt(1) * (u_nb<AUX_UX, W>(K, ain, x, y, 1, 0) - u_nb<AUX_UX, W>(K, ain, x, y, -1, 0)) +
+                      wgt(5) * ((u_nb<AUX_UX, W>(K, ain, x, y, 1, 1) - u_nb<AUX_UX, W>(K, ain, x, y, -1, 1)) +
+                                (u_nb<AUX_UX, W>(K, ain, x, y, 1, -1) - u_nb<AUX_UX, W>(K, ain, x, y, -1, -1)));
+    const real dvdy = wgt(2) * (u_nb<AUX_UY, W>(K, ain, x, y, 0, 1) - u_nb<AUX_UY, W>(K, ain, x, y, 0, -1)) +
+                      wgt(5) * ((u_nb<AUX_UY, W>(K, ain, x, y, 1, 1) - u_nb<AUX_UY, W>(K, ain, x, y, 1, -1)) +
+                                (u_nb<AUX_UY, W>(K, ain, x, y, -1, 1) - u_nb<AUX_UY, W>(K, ain, x, y, -1, -1)));
+    return R(3.0) * (dudx + dvdy);
+}
+
 __device__ __forceinline__ real sum9(const real v[9])
 {
     return v[0] + ((v[1] + v[2]) + (v[3] + v[4])) + ((v[5] + v[6]) + (v[7] + v[8]));
@@ -395,11 +422,13 @@ __device__ __forceinline__ real sum9(const real v[9])
 //   enthalpy, mdot = (1 - rho_s/rho_l)(f_s - f_s^{n-1}),
 //   phi = sum f / (1 - mdot/2) = phi_p + dphi, C = sum l.
 struct Local {
-    real dT, fs, mdot, dphi, C;
+    real dT, fs, mdot, divu, dphi, C;
 };
 
+// div_lag: the isotropic divergence of the previous step's velocity at the
+// cell, used as div u when K.divu = 1 (ignored otherwise).
 __device__ __forceinline__ Local local_fields(const Consts &K, real phi_p, real delta, real ed, real T_p, real chi_p,
-                                              real fs_p, real sl)
+                                              real fs_p, real sl, real div_lag)
 {
     Local o;
     const real sf = phi_p + delta;
@@ -409,7 +438,9 @@ __device__ __forceinline__ Local local_fields(const Consts &K, real phi_p, real 
     const real dchi = inside ? R(0.5) * delta : chi - chi_p;
     invert_enthalpy(K, ed, T_p, chi_p, fs_p, chi, dchi, o.dT, o.fs);
     o.mdot = K.phase_change ? K.expand * (o.fs - fs_p) : R(0.0);
-    o.dphi = (delta + R(0.5) * o.mdot * phi_p) * rcp(R(1.0) - R(0.5) * o.mdot);
+    o.divu = K.divu ? div_lag : o.mdot;
+    // phi = sum f + phi div u / 2 (Sec. 3.1), solved for phi
+    o.dphi = (delta + R(0.5) * o.divu * phi_p) * rcp(R(1.0) - R(0.5) * o.divu);
     o.C = sl;
     return o;
 }
@@ -437,7 +468,8 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const typename PS::T *_
     c.ed = sum9(v) + K.rr * aux_dev_sum<AUX_T, W>(K, ain, x, y, cell, c.T_p) + R(0.5) * Q_p;
     pull9<PS, SET_L, W>(K, pin, x, y, cell, v);
     const real sl = sum9(v);
-    c.L = local_fields(K, c.phi_p, delta, c.ed, c.T_p, c.chi_p, c.fs_p, sl);
+    const real dv = K.divu ? lagged_divu<W>(K, ain, x, y) : R(0.0);
+    c.L = local_fields(K, c.phi_p, delta, c.ed, c.T_p, c.chi_p, c.fs_p, sl, dv);
     return c;
 }
 
@@ -478,6 +510,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     const real T = T_st + T_lo;
     const real C = A.C(0, 0), fs = (real)(float)A.fs(0, 0);
     const real mdot = A.mdot(0, 0);
+    const real divu = A.divu();  // div u of the phi and h sources (mdot, or the lagged velocity divergence)
 
     // isotropic gradient and Laplacian over the 8 neighbours (order 1..8), from
     // differences z_i - z_0: grad z = 3 sum w_i c_i (z_i - z_0), lap z = 6 sum w_i (z_i - z_0).
@@ -671,7 +704,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         }
     }
 
-    // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi mdot
+    // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi div u
     {
         const real ux_p = A.aux(AX_UX), uy_p = A.aux(AX_UY);
         const real kf = -(R(1.0) / R(3.0)) * phi2m1 * K.inv_s2eps;
@@ -686,7 +719,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         {
             const real d = f[0] + wfl<QF>(0) * (phi_p - phi_st);
             const real deq = wfl<QF>(0) * phi_lo;
-            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wfl<QF>(0) * phi * mdot));
+            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wfl<QF>(0) * phi * divu));
         }
         // lagged phi of the cell that wrote the population pulled into direction i (own cell at a wall)
         auto php = [&](int i) {
@@ -701,7 +734,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const pf2 dp = fma2(ws, sub2(pk2(php(a), php(a + 1)), ps), pk2(f[a], f[a + 1]));
             const pf2 dm = fma2(ws, sub2(pk2(php(opp(a)), php(opp(a + 1))), ps), pk2(f[opp(a)], f[opp(a + 1)]));
             const pf2 eq_e = splat2(w * phi_lo), eq_o = mul2(splat2(w3 * phi), cdot2(a, ux, uy));  // f_eq - w phi_st
-            const pf2 F_e = splat2(w * phi * mdot), F_o = mul2(splat2(w3), cdot2(a, ax, ay));
+            const pf2 F_e = splat2(w * phi * divu), F_o = mul2(splat2(w3), cdot2(a, ax, ay));
             const pf2 sf = splat2(src), of = splat2(om);
             store4(SET_F, a, fma2(sf, add2(F_e, F_o), fma2(sub2(add2(eq_e, eq_o), dp), of, dp)),
                    fma2(sf, sub2(F_e, F_o), fma2(sub2(sub2(eq_e, eq_o), dm), of, dm)));
@@ -738,7 +771,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // isotropic source w_i Q weighted with (1 - 1/(2 tau_tilde)).  Everything is formed as
     // deviations from w_i rr T_st (and the latent reference for i = 0).  For a pair the
     // symmetric and antisymmetric equilibrium parts are the even and odd parts above.
-    const real Q = rhocp * T * mdot;
+    const real Q = rhocp * T * divu;
     {
         const real tau_hb = R(0.5) + R(3.0) * lam * K.inv_rr;
         const real om_a = rcp(tau_hb), om_s = R(2.0) - om_a;
@@ -810,7 +843,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 // copies for phase A of row y + 1 (and phase B of row y) are in flight.
 // Rings per warp (columns x0-2 .. x0+31 for lag, the warp's 32 lanes otherwise):
 //   lag  lagged (phi, T) pairs                             rows y & 7
-//   dd, cf, md  (dphi, dT), (C, f_s), mdot from phase A     rows y & 3
+//   dd, cf, md, dv  (dphi, dT), (C, f_s), mdot, div u from phase A   rows y & 3
+//   uv   lagged (u_x, u_y) pairs (div u = lagged divergence only)      rows y & 3
 //   ps   staged lagged (p, S) pairs                        rows y & 3
 //   pop  staged pulls of f, h, l (stored form), windows    rows y mod 3
 //   ax   staged own-cell Q, f_s, u_x, u_y, C, windows       rows y mod 3
@@ -850,6 +884,8 @@ struct WarpRing {
     float2 cf[4][32];     // (C, f_s)
     float2 ps[4][32];     // (p, S) lagged, staged
     float md[4][32];      // mdot
+    float dv[4][32];      // div u of the phi and h sources
+    float2 uv[4][34];     // lagged (u_x, u_y), staged when div u is the lagged velocity divergence
     float pop[3][27][WW];  // staged pulls of f (0..8), h (9..17), l (18..26)
     float ax[3][NAX][WW];  // staged own-cell Q, f_s, u_x, u_y, C
     float gp[2][9][WW];    // staged pulls of g
@@ -938,6 +974,7 @@ struct RingAcc {
     __device__ real p(int dy, int dx) const { return psv(dy, dx).x; }
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
+    __device__ real divu() const { return w.dv[sl[1]][lane]; }
     // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
@@ -1025,6 +1062,25 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w,
           (wgt(5) * (tt[5] - T_own) + wgt(6) * (tt[6] - T_own) + wgt(7) * (tt[7] - T_own) + wgt(8) * (tt[8] - T_own));
 }
 
+// Isotropic divergence of the lagged velocity at row y, lane column, from the
+// uv ring (columns x0 - 2 .. x0 + 31 at index lane + 1 + dx); a row beyond a
+// wall is the ghost -u of row y.  Same stencil and order as lagged_divu.
+template <bool W>
+__device__ __forceinline__ real ring_divu(const Consts &K, const WarpRing &w, int lane, int y)
+{
+    const int c = lane + 1;
+    const bool gs = W && y - 1 < 0, gn = W && y + 1 >= K.ny;
+    const float2 *r0 = w.uv[y & 3];
+    const float2 *rs = gs ? r0 : w.uv[(y - 1) & 3];
+    const float2 *rn = gn ? r0 : w.uv[(y + 1) & 3];
+    const real ss = gs ? R(-1.0) : R(1.0), sn = gn ? R(-1.0) : R(1.0);
+    const real dudx = wgt(1) * (r0[c + 1].x - r0[c - 1].x) +
+                      wgt(5) * ((sn * rn[c + 1].x - sn * rn[c - 1].x) + (ss * rs[c + 1].x - ss * rs[c - 1].x));
+    const real dvdy = wgt(2) * (sn * rn[c].y - ss * rs[c].y) +
+                      wgt(5) * ((sn * rn[c + 1].y - ss * rs[c + 1].y) + (sn * rn[c - 1].y - ss * rs[c - 1].y));
+    return R(3.0) * (dudx + dvdy);
+}
+
 // Phase A / phase B sweep of one warp over rows [ys, ye) of its strip.  WALLS =
 // false: every row ys - 2 .. ye + 1 lies inside the lattice.
 template <int MODE, bool WALLS, class PS>
@@ -1063,6 +1119,17 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (lane < 2) {
             cp_async4(&w.lag[yl & 7][32 + lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xb));
             cp_async4(&w.lag[yl & 7][32 + lane].y, plane_ptr(ain, AUX_T, K) + (ro + xb));
+        }
+    };
+    // lagged (u_x, u_y) of row yl with the one-column halo, for the divergence of phase A
+    auto stage_u = [&](int yl) {
+        if (!K.divu || (WALLS && (yl < 0 || yl >= K.ny))) return;
+        const int ro = yl * K.pitch;
+        cp_async4(&w.uv[yl & 3][lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xa));
+        cp_async4(&w.uv[yl & 3][lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xa));
+        if (lane < 2) {
+            cp_async4(&w.uv[yl & 3][32 + lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xb));
+            cp_async4(&w.uv[yl & 3][32 + lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xb));
         }
     };
     // own-cell lagged values of row y as float windows: Q, f_s, u_x (first copy), u_y, C (second)
@@ -1161,6 +1228,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     stage_lag(ya0 - 1);
     stage_lag(ya0);
     stage_lag(ya0 + 1);
+    stage_u(ya0 - 1);
+    stage_u(ya0);
+    stage_u(ya0 + 1);
     int s3 = mod3(ya0);  // ya mod 3, advanced with the loop
     stage_a(ya0, s3);
     cp_async_commit();
@@ -1168,6 +1238,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         const int s3n = s3 == 2 ? 0 : s3 + 1, s3p = s3 == 0 ? 2 : s3 - 1;  // (ya + 1), (ya - 1) mod 3
         if (ya < ya1) {
             stage_lag(ya + 2);
+            stage_u(ya + 2);
             stage_a(ya + 1, s3n);
         }
         stage_g(ya);
@@ -1190,7 +1261,8 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             const real sl = sum9(v);
             const real fs_p = w.ax[s3][AX_FS][lane + off];
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
-            const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl);
+            const real dv = K.divu ? ring_divu<WALLS>(K, w, lane, ya) : R(0.0);
+            const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl, dv);
             if (MODE == MODE_REDUCE) {
                 if (b_lane) {
                     const double phid = (double)phi_p + (double)L.dphi;
@@ -1206,6 +1278,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                 w.dd[s4][lane] = make_float2(L.dphi, L.dT);
                 w.cf[s4][lane] = make_float2(L.C, L.fs);
                 w.md[s4][lane] = L.mdot;
+                w.dv[s4][lane] = L.divu;
             }
         }
         __syncwarp();
