@@ -152,13 +152,24 @@ lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_field
  * for all later work of the handle; NULL selects the legacy default stream. */
 lb_status lb_set_stream(lb_handle *h, void *cuda_stream);
 
-/* Enqueue n >= 0 time steps (one fused kernel launch each).  Asynchronous. */
+/* Enqueue n >= 0 time steps (one fused kernel launch each).  Asynchronous.
+ * One step is the LB update of Sec. 3 for all four sets: streaming with the
+ * wall rules of Sec. 4.5 (half-way bounce-back; anti-bounce-back of the
+ * enthalpy at a Dirichlet wall), the moments of Sec. 3.1-3.4 (phi, rho u*,
+ * u, p, rho H, C), the enthalpy relation Eq. Hfl, the property rule of
+ * Sec. 2, the isotropic stencils at the end of Sec. 3.4, the forces of
+ * Eq. Fs and Sec. 3.2, and the collisions (BGK for f, g, l; two relaxation
+ * times for h).  A non-finite result sets a sticky status that lb_reduce
+ * returns as LB_ERR_UNSTABLE; an error of an earlier call is returned
+ * unchanged and nothing is enqueued. */
 lb_status lb_step(lb_handle *h, int n);
 
 /* Macroscopic fields of the current state -- the values the next step
- * computes before it collides: order parameter phi, temperature T, solid
- * fraction f_s, concentration C, velocity (ux, uy), pressure p.  Each output
- * is nx*ny floats, host or device memory as on_device says; any may be NULL.
+ * computes before it collides (the moments of Sec. 3.1-3.4 and Eq. Hfl):
+ * order parameter phi, temperature T, solid fraction f_s, concentration C,
+ * velocity (ux, uy) (the corrected velocity u = u* + f/2 of Sec. 3.2),
+ * pressure p.  Each output is nx*ny floats, row-major with x fastest, host or
+ * device memory as on_device says, owned by the caller; any may be NULL.
  * With host outputs the call synchronises the stream. */
 lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C, float *ux,
                         float *uy, float *p, int on_device);
@@ -171,14 +182,20 @@ lb_status lb_get_fields(lb_handle *h, float *phi, float *T, float *fs, float *C,
  * then the latent part rho_l L (chi - f_s) plus the sensible part with the
  * mixture rule T (f_s (rho Cp)_s + (chi - f_s) (rho Cp)_l + (1 - chi)
  * (rho Cp)_g).  fs = NULL derives f_s from (T, chi) as lb_create does.
- * ux, uy, p = NULL mean 0.  The step count and V_0 are kept.  This is how a
+ * ux, uy, p = NULL mean 0.  With divu_mode = 1 the rest population of the
+ * phase-field set is lowered by phi div u / 2 (div u of the given velocity),
+ * so that the moment phi = sum f_i + phi div u / 2 of Sec. 3.1 returns the
+ * given phi.  The step count and V_0 are kept.  This is how a
  * learned surrogate's prediction of the fields is handed back to the method;
  * the paper has no counterpart.  With host inputs the call synchronises the
  * stream. */
 lb_status lb_set_fields(lb_handle *h, const float *phi, const float *T, const float *fs, const float *C,
                         const float *ux, const float *uy, const float *p, int on_device);
 
-/* Global diagnostics of the current state in FP64, summed in a fixed order:
+/* Global diagnostics of the current state in FP64, summed in a fixed order
+ * (the conservation checks of Sec. 2 and the freezing measures of Sec. 4.2
+ * and 4.4: solid height on the centre column, the solid and the total
+ * phase-change volume relative to the initial one, V*_s and V*_sl):
  *   out[0] sum phi     out[1] sum rho H    out[2] sum C     out[3] sum f_s
  *   out[4] sum chi, chi = clamp((1 + phi)/2, 0, 1)
  *   out[5] front height: sum over y of f_s on the column x = nx/2
@@ -206,10 +223,12 @@ lb_status lb_reduce_noalloc(lb_handle *h, double out[8]);
 /* Number of steps taken since lb_create (or restored by lb_load). */
 lb_status lb_steps_taken(lb_handle *h, long *out);
 
-/* Checkpoint: write / read the complete state (populations, lagged fields,
- * step count, V_0) of the handle to / from a file.  lb_load requires a file
- * written for the same nx, ny, population storage and lattice_fl; the result continues bit-for-bit
- * as the saved run would have.  Both synchronise the stream. */
+/* Checkpoint: write / read the complete state of the time stepping of Sec. 3
+ * (the stored populations of the four sets, the lagged fields the next step
+ * reads, the step count and V_0) to / from a file at path.  lb_load requires
+ * a file written for the same nx, ny, population storage and lattice_fl
+ * (LB_ERR_INVALID_ARG otherwise, state unchanged); the run then continues
+ * bit-for-bit as the saved run would have.  Both synchronise the stream. */
 lb_status lb_save(lb_handle *h, const char *path);
 lb_status lb_load(lb_handle *h, const char *path);
 

@@ -452,7 +452,10 @@ void orc_destroy(orc_state *st)
 /* Per cell, in this order:
  *   rho H = sum h_i + Q^{n-1}/2  (Sec. 3.3; the correction needs this step's
  *           T, which depends on rho H, so the previous step's Q is used);
- *   T, f_s from the enthalpy (Eq. Hfl) with chi from (1 + sum f_i)/2;
+ *   T, f_s from the enthalpy (Eq. Hfl) with the material fraction chi =
+ *           clamp((1 + phi)/2): phi from the moment below when div u is the
+ *           lagged velocity divergence (known before the enthalpy), sum f_i in
+ *           place of phi when div u = mdot (which needs f_s first);
  *   mdot = (1 - rho_s/rho_l) d_t f_s, backward difference (Eq. NS1);
  *   div u, the velocity divergence in the phase-field and enthalpy sources
  *           and moment corrections (Sec. 3.1, 3.3): by default the model
@@ -480,17 +483,28 @@ static void pass_local(orc_state *st)
             sl += st->l[i * n + c];
         }
         double e = sh + 0.5 * st->Q_prev[c];
-        double T, fs;
-        orc_enthalpy_invert(p, e, chi_of(sf), &T, &fs);
-        double mdot = p->phase_change_on ? (1.0 - p->rho_s / p->rho_l) * (fs - st->fs_prev[c]) : 0.0;
-        double divu = mdot;
+        double T, fs, divu = 0.0, phi = 0.0, chi;
         if (p->divu_mode == 1) {
+            /* div u known before the enthalpy: phi first, and the material
+             * fraction of the enthalpy relation from phi itself, as in the
+             * property rule */
             double dxx, dxy, dyx, dyy;
             stencil(g, st->ux_prev, x, y, GHOST_VELOCITY, &dxx, &dxy, NULL);
             stencil(g, st->uy_prev, x, y, GHOST_VELOCITY, &dyx, &dyy, NULL);
             divu = dxx + dyy;
+            phi = sf / (1.0 - 0.5 * divu);
+            chi = chi_of(phi);
+        } else {
+            /* div u = mdot needs f_s, which needs the enthalpy relation: the
+             * material fraction is taken from sum f_i */
+            chi = chi_of(sf);
         }
-        double phi = sf / (1.0 - 0.5 * divu);
+        orc_enthalpy_invert(p, e, chi, &T, &fs);
+        double mdot = p->phase_change_on ? (1.0 - p->rho_s / p->rho_l) * (fs - st->fs_prev[c]) : 0.0;
+        if (p->divu_mode != 1) {
+            divu = mdot;
+            phi = sf / (1.0 - 0.5 * divu);
+        }
         st->divu[c] = divu;
         st->rhoH[c] = e;
         st->T[c] = T;

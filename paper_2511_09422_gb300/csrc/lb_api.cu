@@ -372,7 +372,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
             eq = eq_tmp;
         }
         lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4],
-                                                                           nullptr, nullptr, eq, h->aux[0]);
+                                                                           nullptr, nullptr, eq, h->aux[0], 0);
         if (h->half)
             lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
                                                                                                  h->pops[0]);
@@ -482,7 +482,7 @@ extern "C" lb_status lb_set_fields(lb_handle *h, const float *phi, const float *
     }
     lbk::lb_init_eq_kernel<<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3],
                                                                                  dev[4], dev[5], dev[6], eq,
-                                                                                 h->aux[h->cur]);
+                                                                                 h->aux[h->cur], 1);
     if (h->half)
         lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
             K, eq, h->aux[h->cur], h->pops[h->cur]);

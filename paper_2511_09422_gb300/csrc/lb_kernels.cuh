@@ -431,16 +431,22 @@ __device__ __forceinline__ Local local_fields(const Consts &K, real phi_p, real 
                                               real fs_p, real sl, real div_lag)
 {
     Local o;
-    const real sf = phi_p + delta;
-    const real hs = R(0.5) * (R(1.0) + sf), hp = R(0.5) * (R(1.0) + phi_p);
+    // phi = sum f + phi div u / 2 (Sec. 3.1), solved for phi.  With the lagged
+    // velocity divergence phi is known before the enthalpy relation, and the
+    // material fraction chi of Eq. Hfl is that of phi; with div u = mdot, which
+    // needs f_s first, chi is taken from sum f.
+    real dphi = R(0.0);
+    if (K.divu) dphi = (delta + R(0.5) * div_lag * phi_p) * rcp(R(1.0) - R(0.5) * div_lag);
+    const real dsf = K.divu ? dphi : delta;  // change of the argument of chi
+    const real hs = R(0.5) * (R(1.0) + (phi_p + dsf)), hp = R(0.5) * (R(1.0) + phi_p);
     const real chi = clamp01(hs);
     const bool inside = hs >= R(0.0) && hs <= R(1.0) && hp >= R(0.0) && hp <= R(1.0);
-    const real dchi = inside ? R(0.5) * delta : chi - chi_p;
+    const real dchi = inside ? R(0.5) * dsf : chi - chi_p;
     invert_enthalpy(K, ed, T_p, chi_p, fs_p, chi, dchi, o.dT, o.fs);
     o.mdot = K.phase_change ? K.expand * (o.fs - fs_p) : R(0.0);
     o.divu = K.divu ? div_lag : o.mdot;
-    // phi = sum f + phi div u / 2 (Sec. 3.1), solved for phi
-    o.dphi = (delta + R(0.5) * o.divu * phi_p) * rcp(R(1.0) - R(0.5) * o.divu);
+    if (!K.divu) dphi = (delta + R(0.5) * o.mdot * phi_p) * rcp(R(1.0) - R(0.5) * o.mdot);
+    o.dphi = dphi;
     o.C = sl;
     return o;
 }
@@ -1404,10 +1410,24 @@ __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst,
 // (post-streaming) layout to `eq`, h as deviations from w_i rr T (with the
 // latent reference for i = 0), and the lagged fields of a state at rest in time.
 // ---------------------------------------------------------------------------------------
+// Velocity component v (dense nx * ny input) at (x + dx, y + dy), with the
+// ghost -u of row y beyond a no-slip wall.
+__device__ __forceinline__ real dense_u_nb(const Consts &K, const float *__restrict__ v, int x, int y, int dx, int dy)
+{
+    const int yy = y + dy, xx = wrapx(x + dx, K.nx);
+    if (yy < 0 || yy >= K.ny) return -v[(long long)y * K.nx + xx];
+    return v[(long long)yy * K.nx + xx];
+}
+
+// match_moment (re-initialisation from fields): when div u is the lagged
+// velocity divergence, the next step reads phi = sum f / (1 - div u / 2) with
+// div u the divergence of the installed velocity; the rest population is then
+// lowered by phi div u / 2 so that this reading returns the given phi.
 __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0, const float *__restrict__ T0,
                                   const float *__restrict__ C0, const float *__restrict__ ux0,
                                   const float *__restrict__ uy0, const float *__restrict__ fs0,
-                                  const float *__restrict__ p0, float *__restrict__ eq, float *__restrict__ aux)
+                                  const float *__restrict__ p0, float *__restrict__ eq, float *__restrict__ aux,
+                                  int match_moment)
 {
     const long long n = (long long)K.nx * K.ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
@@ -1415,6 +1435,16 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
         const long long cell = (long long)y * K.pitch + x;
         const real phi = phi0[k], T = T0[k], C = C0[k];
         const real ux = ux0 ? ux0[k] : R(0.0), uy = uy0 ? uy0[k] : R(0.0);
+        real f0_shift = R(0.0);
+        if (match_moment && K.divu && ux0 && uy0) {
+            const real dudx = wgt(1) * (dense_u_nb(K, ux0, x, y, 1, 0) - dense_u_nb(K, ux0, x, y, -1, 0)) +
+                              wgt(5) * ((dense_u_nb(K, ux0, x, y, 1, 1) - dense_u_nb(K, ux0, x, y, -1, 1)) +
+                                        (dense_u_nb(K, ux0, x, y, 1, -1) - dense_u_nb(K, ux0, x, y, -1, -1)));
+            const real dvdy = wgt(2) * (dense_u_nb(K, uy0, x, y, 0, 1) - dense_u_nb(K, uy0, x, y, 0, -1)) +
+                              wgt(5) * ((dense_u_nb(K, uy0, x, y, 1, 1) - dense_u_nb(K, uy0, x, y, 1, -1)) +
+                                        (dense_u_nb(K, uy0, x, y, -1, 1) - dense_u_nb(K, uy0, x, y, -1, -1)));
+            f0_shift = -R(0.5) * phi * R(3.0) * (dudx + dvdy);
+        }
         const real chi = clamp01(R(0.5) * (R(1.0) + phi));
         real fs;
         real e_sens;
@@ -1434,7 +1464,8 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
         for (int i = 0; i < 9; i++) {
             const real cu = (real)cx(i) * ux + (real)cy(i) * uy;
             const real si = wgt(i) * (R(3.0) * cu + R(4.5) * cu * cu - R(1.5) * uu);
-            eq[(long long)(SET_F * 9 + i) * K.plane + cell] = wfl_rt(K.qfl, i) * phi * (R(1.0) + R(3.0) * cu);
+            eq[(long long)(SET_F * 9 + i) * K.plane + cell] =
+                wfl_rt(K.qfl, i) * phi * (R(1.0) + R(3.0) * cu) + (i == 0 ? f0_shift : R(0.0));
             eq[(long long)(SET_G * 9 + i) * K.plane + cell] = rho * si;
             eq[(long long)(SET_L * 9 + i) * K.plane + cell] = wfl_rt(K.qfl, i) * C * (R(1.0) + R(3.0) * cu);
             // h_0 - w_0 rr T - latent = e_sens - rr T - w_0 rho Cp T 3u.u/2;  h_i - w_i rr T = w_i rho Cp T (...)

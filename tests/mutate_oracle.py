@@ -37,8 +37,10 @@ M = [
  ("S without u.grad rho", "double S = rho * mdot + ux * grx + uy * gry;", "double S = rho * mdot;", 1),
  ("F~ without cs2 grad rho", "double Ftx = Fx - gPx + CS2 * grx + CS2 * gSx;", "double Ftx = Fx - gPx + CS2 * gSx;", 1),
  ("F~ without grad p", " - gP", " + 0.0 * gP", 2),
+ ("F~ without grad p (x component only)", "double Ftx = Fx - gPx", "double Ftx = Fx + 0.0 * gPx", 1),
  ("pressure S/2 -> S", "(sg + 0.5 * S + tau_g * G0", "(sg + S + tau_g * G0", 1),
  ("pressure G0 with tau = 1", "tau_g * G0", "1.0 * G0", 1),
+ ("pressure G0 with tau_f", "tau_g * G0", "tau_f * G0", 1),
  ("g equilibrium without the rest term", "geq[i] = pr / CS2 * (WT[i] - (i == 0 ? 1.0 : 0.0))", "geq[i] = pr / CS2 * WT[i]", 1),
  ("g source without (1 - 1/2tau)", "(1.0 - 0.5 / tau_g) * Gi[i]", "Gi[i]", 1),
  ("f equilibrium without velocity", "feq[i] = wfl[i] * phi * (1.0 + cu / CS2);", "feq[i] = wfl[i] * phi;", 1),
@@ -50,7 +52,8 @@ M = [
  ("H source factor with tau_bar", "(1.0 - 0.5 / tau_hs) * Hi[i]", "(1.0 - 0.5 / tau_hb) * Hi[i]", 1),
  ("rho H correction dropped", "double e = sh + 0.5 * st->Q_prev[c];", "double e = sh;", 1),
  ("mdot with rho_l/rho_s", "(1.0 - p->rho_s / p->rho_l) * (fs - st->fs_prev[c])", "(1.0 - p->rho_l / p->rho_s) * (fs - st->fs_prev[c])", 1),
- ("phi moment correction sign", "sf / (1.0 - 0.5 * divu)", "sf / (1.0 + 0.5 * divu)", 1),
+ ("phi moment correction sign", "sf / (1.0 - 0.5 * divu)", "sf / (1.0 + 0.5 * divu)", 2),
+ ("chi of Eq. Hfl from sum f with the lagged divergence", "chi = chi_of(phi);", "chi = chi_of(sf);", 1),
  ("solute R interface term sign", "(1.0 - phi) * C * nx_ / s2e", "(1.0 + phi) * C * nx_ / s2e", 1),
  ("solute R flux correction sign", "- (p->k_p - 1.0) * C * (-gf", "+ (p->k_p - 1.0) * C * (-gf", 2),
  ("k_eff rule", "double keff = 1.0 - fs * (1.0 - p->k_p);", "double keff = 1.0 - fs * p->k_p;", 1),

@@ -46,8 +46,10 @@ def test_gaussian_solute_spreads_at_the_model_diffusivity(lattice):
 
 
 def test_d2q5_conserves_phi_and_solute_on_a_droplet():
+    """Without phase change and with div u the model value mdot = 0
+    (divu_mode = 0), sum phi and sum C are conserved to round-off."""
     w = W.parity_droplet(nx=64, ny=48)
-    p = dict(w["params"], phase_change_on=0, lattice_fl=1)
+    p = dict(w["params"], phase_change_on=0, lattice_fl=1, divu_mode=0)
     o = oracle.Oracle(w["grid"], p, w["fields"])
     s0 = o.reduce()
     o.step(150)

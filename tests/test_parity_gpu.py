@@ -118,11 +118,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("divu_mode", [0, 1])
 @pytest.mark.parametrize("name,make,steps", CASES, ids=[c[0] for c in CASES])
-def test_parity_100_steps(oracle_mod, name, make, steps):
+def test_parity_100_steps(oracle_mod, name, make, steps, divu_mode):
+    """Each case with both readings of div u in the phase-field and enthalpy
+    sources: the model value mdot (divu_mode = 0) and the lagged velocity
+    divergence (divu_mode = 1, the default of the freezing workloads)."""
     w = make()
-    got, red, want, wred = _run_pair(oracle_mod, w, steps)
-    _assert_parity(got, want, label=name)
+    p = dict(w["params"], divu_mode=divu_mode)
+    got, red, want, wred = _run_pair(oracle_mod, w, steps, params=p)
+    _assert_parity(got, want, label="%s divu_mode %d" % (name, divu_mode))
     _assert_reduce(red, wred)
 
 
@@ -142,8 +147,9 @@ def edge_workload(nx, ny):
     return w
 
 
+@pytest.mark.parametrize("divu_mode", [0, 1])
 @pytest.mark.parametrize("shape", EDGE_SHAPES)
-def test_parity_edge_shapes(oracle_mod, shape):
+def test_parity_edge_shapes(oracle_mod, shape, divu_mode):
     """A one-column lattice (x-periodic onto itself), a one-row lattice (both
     walls on the same row), shapes at and just past a 30-column warp strip and
     a 4-strip block, and row counts at the edges of the row layout (2-row
@@ -153,8 +159,9 @@ def test_parity_edge_shapes(oracle_mod, shape):
     Equal solid and liquid densities: in a one-row lattice the expansion
     source drives phi far above 1 and makes the case ill-conditioned."""
     w = edge_workload(*shape)
-    got, red, want, wred = _run_pair(oracle_mod, w, 30)
-    _assert_parity(got, want, label=str(shape))
+    p = dict(w["params"], divu_mode=divu_mode)
+    got, red, want, wred = _run_pair(oracle_mod, w, 30, params=p)
+    _assert_parity(got, want, label="%s divu_mode %d" % (shape, divu_mode))
 
 
 def test_parity_initial_state(oracle_mod):
@@ -195,8 +202,9 @@ def test_parity_binary_mushy_range(oracle_mod):
 
 def test_parity_full_size_bench_workload(oracle_mod):
     """The benchmark's 4096 x 4096 planar-front / impurity lattice, in the
-    launch configuration the benchmark times, a few steps against the oracle
-    on every cell."""
+    launch configuration the benchmark times (div u the lagged velocity
+    divergence, the workload's default), a few steps against the oracle on
+    every cell."""
     w = W.impurity_front(nx=4096, ny=4096)
     got, red, want, wred = _run_pair(oracle_mod, w, 3)
     _assert_parity(got, want, label="4096^2")
@@ -328,13 +336,17 @@ def _freezing_time(step, reduce, max_steps, frac=0.99):
     raise AssertionError("no full freezing within %d steps" % max_steps)
 
 
-def test_freezing_time_and_final_solid_volume(oracle_mod):
+@pytest.mark.parametrize("divu_mode", [0, 1])
+def test_freezing_time_and_final_solid_volume(oracle_mod, divu_mode):
     """A small sessile droplet (R = 12) run to full freezing: the freezing time
     and the solid volume V*_s at the end of the run (20 % past the oracle's
-    freezing time) agree with the oracle within 1e-3.  (The height of the
-    solid on the centre column is not compared: it is ill-conditioned in the
-    oracle itself, see test_end_of_run_observables_are_well_conditioned.)"""
+    freezing time) agree with the oracle within 1e-3.  With the lagged velocity
+    divergence as div u (divu_mode = 1) the front position -- the solid height
+    on the centre column -- is compared too; with mdot (divu_mode = 0) it is
+    ill-conditioned in the oracle itself and is not (see
+    test_end_of_run_observables_are_well_conditioned)."""
     w = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.2)
+    w["params"] = dict(w["params"], divu_mode=divu_mode)
     f32 = _f32(w)
     s = lbfreeze.Solver(w["grid"], w["params"], f32)
     tf_gpu, _ = _freezing_time(s.step, s.reduce, 5000)
@@ -344,15 +356,20 @@ def test_freezing_time_and_final_solid_volume(oracle_mod):
     n_end = int(1.2 * tf_ora) + 1
     s.step(n_end - s.steps)
     o.step(n_end - o.steps)
-    vs_gpu, vs_ora = s.reduce()[6], o.reduce()[6]
+    red, wred = s.reduce(), o.reduce()
     s.close()
-    assert abs(vs_gpu - vs_ora) <= 1e-3 * vs_ora, (vs_gpu, vs_ora)
+    assert abs(red[6] - wred[6]) <= 1e-3 * wred[6], (red[6], wred[6])
+    if divu_mode == 1:
+        assert abs(red[5] - wred[5]) <= 1e-3 * wred[5], (red[5], wred[5])
 
 
-def test_front_position_stefan_layer_end_of_run(oracle_mod):
+@pytest.mark.parametrize("divu_mode", [0, 1])
+def test_front_position_stefan_layer_end_of_run(oracle_mod, divu_mode):
     """The film-freezing workload over its full 2000 steps: the front position,
-    as the mean solid height sum f_s / nx, within 1e-3 of the oracle's."""
+    as the mean solid height sum f_s / nx, within 1e-3 of the oracle's; with
+    divu_mode = 1 also the solid height on the centre column."""
     w = W.stefan_layer(nx=64, ny=256)
+    w["params"] = dict(w["params"], divu_mode=divu_mode)
     f32 = _f32(w)
     s = lbfreeze.Solver(w["grid"], w["params"], f32)
     s.step(w["steps"])
@@ -365,3 +382,5 @@ def test_front_position_stefan_layer_end_of_run(oracle_mod):
     h_gpu, h_ora = red[3] / nx, wred[3] / nx
     assert h_ora > 5.0  # the front has advanced several cells
     assert abs(h_gpu - h_ora) <= 1e-3 * h_ora, (h_gpu, h_ora)
+    if divu_mode == 1:
+        assert abs(red[5] - wred[5]) <= 1e-3 * wred[5], (red[5], wred[5])

@@ -48,10 +48,19 @@ def _reduce(L, solver):
     return np.array(out[:])
 
 
-def test_noalloc_matches_reduce_on_consecutive_calls(lib):
+@pytest.mark.parametrize("options", [
+    dict(),
+    dict(divu_mode=0),
+    dict(pop_storage=lbfreeze.LB_STORAGE_F16),
+    dict(lattice_fl=lbfreeze.LB_LATTICE_D2Q5),
+], ids=["fp32", "fp32_divu_mdot", "fp16", "d2q5"])
+def test_noalloc_matches_reduce_on_consecutive_calls(lib, options):
+    """Every storage form and lattice of the step (FP32 and half-precision
+    populations, D2Q9 or D2Q5 phase-field and solute sets) and both readings
+    of div u, whose moment correction enters the phi sum."""
     w = W.parity_droplet(nx=96, ny=72)
     f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
-    s = lbfreeze.Solver(w["grid"], w["params"], f32)
+    s = lbfreeze.Solver(w["grid"], dict(w["params"], **options), f32)
     s.step(25)
     ref = _reduce(lib, s)
     a1 = _noalloc(lib, s)
