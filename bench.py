@@ -39,7 +39,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_UPDATE = 360  # 36 populations read + written, 9 lagged fields read + written, FP32
+# Algorithmic bytes of one lattice update: 36 populations and 8 lagged fields (f_s,
+# Q, u_x, u_y, C, p, S, and phi or T), each read and written once, FP32.  The step
+# also keeps the lagged T (phi) beside phi (T) as the reference of its deviation
+# storage, 360 bytes in all; that design choice is reported beside the figure.
+BYTES_PER_UPDATE = 352
+BYTES_MOVED_PER_UPDATE = 360
 NAMEPLATE_HBM_GBS = 7900.0  # HBM3e nameplate of one GB300, next to the measured copy bandwidth
 WORKLOAD = dict(name="impurity_front", nx=4096, ny=4096)
 PROFILE = os.path.join(ROOT, "profiles", "lb_step_kernel_impurity_front.md")
@@ -147,19 +152,26 @@ def _dist():
     return ws, rank, local
 
 
-SAMPLE = "the same workload on a 1024x1024 lattice (impurity r=200 at (nx/2, ny/4), same parameters)"
+def _sample_text(size: int) -> str:
+    return ("the benchmark's own impurity_front %dx%d lattice (impurity r=%g at (nx/2, ny/4), same parameters)"
+            % (size, size, 200.0 * size / 4096.0))
 
 
-def _oracle_sample(steps_min: int, seconds: float, warmup: int = 1):
-    """The FP64 oracle on a 1024 x 1024 lattice of the same workload, timed on
-    the host cores after `warmup` untimed steps: returns (MLUPS, steps, cores, s)."""
+def _oracle_sample(size: int, steps_min: int, seconds: float, warmup: int = 1, threads: int = 0):
+    """The FP64 oracle on the benchmark's size x size impurity-front lattice, timed
+    on the host cores (all of them, or ``threads``) after ``warmup`` untimed steps,
+    for at least ``steps_min`` steps and ``seconds`` seconds: returns (MLUPS,
+    steps, threads used, seconds)."""
     import numpy as np
 
     import oracle
     from paper_2511_09422_gb300 import workloads as W
-    w = W.impurity_front(nx=1024, ny=1024)
+    w = W.impurity_front(nx=size, ny=size, radius=200.0 * size / 4096.0)
     f = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in w["fields"].items()}
+    if threads:
+        oracle.oracle.set_threads(threads)
     o = oracle.Oracle(w["grid"], w["params"], f)
+    del f, w
     o.step(max(warmup, 0))
     t0 = time.perf_counter()
     n = 0
@@ -167,34 +179,42 @@ def _oracle_sample(steps_min: int, seconds: float, warmup: int = 1):
         o.step(1)
         n += 1
     dt = time.perf_counter() - t0
-    return 1024 * 1024 * n / dt / 1e6, n, oracle.oracle.num_threads(), dt
+    cores = oracle.oracle.num_threads()
+    o.close()
+    return size * size * n / dt / 1e6, n, cores, dt
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper ships no code) on the same
+    lattice, workload and step count as the GPU arm, on the host cores."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    mlups, n, cores, dt = _oracle_sample(max(args.steps, 1), 0.0, args.warmup)
+    mlups, n, cores, dt = _oracle_sample(args.size, max(args.steps, 1), 0.0, args.warmup)
+    sample = _sample_text(args.size)
     line = {
         "impl": "reference", "metric": "MLUPS (all coupled fields)", "value": round(mlups, 3),
         "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "impurity_front, FP64 CPU oracle on " + SAMPLE, "steps_timed": n},
+        "config": {"workload": "impurity_front %dx%d (planar front + insoluble impurity r=%g, C0=0.05, Ma=10), "
+                               "FP64 CPU oracle" % (args.size, args.size, 200.0 * args.size / 4096.0),
+                   "steps_timed": n},
         "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": "%d oracle steps on %s" % (n, SAMPLE)},
+                         "sample": "%d oracle steps after %d untimed on %s" % (n, args.warmup, sample)},
         "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
 
 
-BYTES_PER_UPDATE_F16 = 216  # 36 populations read + written as FP16, 9 lagged FP32 fields read + written
-BYTES_PER_UPDATE_Q5 = 296   # D2Q5 f and l: 28 populations + 9 lagged fields, FP32, read + written
+BYTES_PER_UPDATE_F16 = 208  # 36 populations read + written as FP16, 8 lagged FP32 fields read + written
+BYTES_PER_UPDATE_Q5 = 288   # D2Q5 f and l: 28 populations + 8 lagged fields, FP32, read + written
+# with the step's ninth lagged field (the deviation reference) 216 and 296 bytes are moved
 
 
 def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     """The same lattice with half-precision population storage: MLUPS, and
-    achieved bandwidth against its own algorithmic bytes (216 B per update)."""
+    achieved bandwidth against its own algorithmic bytes (208 B per update)."""
     s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=1), f32, stream=stream)
     s.step(args.warmup)
     stream.synchronize()
@@ -214,13 +234,14 @@ def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     gbs = BYTES_PER_UPDATE_F16 * cells * args.steps / (ms * 1e-3) / 1e9
     return {"metric": "MLUPS (all coupled fields), FP16 population storage", "value": round(mlups, 2),
             "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_F16,
+            "bytes_moved_per_update": BYTES_PER_UPDATE_F16 + 8,
             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
             "dtype": "f32 arithmetic, f16 populations"}
 
 
 def _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     """The same lattice with D2Q5 for the phase-field and solute sets: MLUPS, and
-    achieved bandwidth against its own algorithmic bytes (296 B per update)."""
+    achieved bandwidth against its own algorithmic bytes (288 B per update)."""
     s = lbfreeze.Solver(w["grid"], dict(w["params"], lattice_fl=1), f32, stream=stream)
     s.step(args.warmup)
     stream.synchronize()
@@ -240,6 +261,7 @@ def _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     gbs = BYTES_PER_UPDATE_Q5 * cells * args.steps / (ms * 1e-3) / 1e9
     return {"metric": "MLUPS (all coupled fields), D2Q5 phase-field and solute sets", "value": round(mlups, 2),
             "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_Q5,
+            "bytes_moved_per_update": BYTES_PER_UPDATE_Q5 + 8,
             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
             "dtype": "f32"}
 
@@ -392,6 +414,47 @@ def _surrogate_leg(args, torch, peaks):
     }
 
 
+def run_cpu_plan(args):
+    """The FP64 oracle timed on the host cores for the small configurations:
+    the film-freezing layer (64 x 256, 2000 steps), the heated channel
+    (512 x 256, 1000 steps) and the 512^2 sessile droplet (R = 100, 1000
+    steps; gas density ratio 0.1), each on all cores and on one core (one core
+    runs at least 200 steps and 20 s of the configuration, and its rate is
+    reported).  Prints one JSON line; the GPU is not used."""
+    import numpy as np
+
+    import oracle
+    from paper_2511_09422_gb300 import workloads as W
+    cases = [("stefan_layer 64x256", W.stefan_layer(nx=64, ny=256), 2000),
+             ("thermocapillary_channel 512x256", W.thermocapillary_channel(nx=512, ny=256), 1000),
+             ("sessile_droplet 512x512 R=100", W.sessile_droplet(nx=512, ny=512, radius=100.0, rho_g=0.1), 1000)]
+    all_cores = oracle.oracle.num_threads()
+    out = []
+    for name, w, steps in cases:
+        f = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in w["fields"].items()}
+        cells = w["grid"]["nx"] * w["grid"]["ny"]
+        row = {"config": name, "steps": steps}
+        for label, threads in (("all_cores", all_cores), ("one_core", 1)):
+            oracle.oracle.set_threads(threads)
+            o = oracle.Oracle(w["grid"], w["params"], f)
+            o.step(1)
+            t0 = time.perf_counter()
+            n = 0
+            while n < (steps if threads == all_cores else min(steps, 200)) or \
+                    (threads == 1 and n < steps and time.perf_counter() - t0 < 20.0):
+                o.step(1)
+                n += 1
+            dt = time.perf_counter() - t0
+            row[label] = {"mlups": round(cells * n / dt / 1e6, 3), "steps_timed": n, "s": round(dt, 2),
+                          "threads": oracle.oracle.num_threads()}
+            o.close()
+        out.append(row)
+    oracle.oracle.set_threads(all_cores)
+    import platform
+    print(json.dumps({"metric": "FP64 oracle MLUPS on the host cores", "unit": "MLUPS", "host": platform.machine(),
+                      "nproc": os.cpu_count(), "runs": out}))
+
+
 def run_forward_only(args):
     """The surrogate's forward pass alone: 12 tensor-core convolutions and the
     pooling / upsampling kernels on one size x size image."""
@@ -517,9 +580,9 @@ def run_gpu(args):
     traffic = _traffic_per_launch(cells)
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        mlups, n, cores, dt = _oracle_sample(3, 10.0)
+        mlups, n, cores, dt = _oracle_sample(args.size, 3, 10.0)
         cpu = {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
-               "sample": "%d FP64 oracle steps on %s (%.1f s)" % (n, SAMPLE, dt)}
+               "sample": "%d FP64 oracle steps on %s (%.1f s)" % (n, _sample_text(args.size), dt)}
     line = {
         "metric": "MLUPS (all coupled fields)", "value": round(value, 2), "unit": "MLUPS",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -533,6 +596,9 @@ def run_gpu(args):
                      "unit": "GB/s", "frac": round(achieved / peaks.get("hbm_gbs"), 4),
                      "peak_source": src, "bytes_per_update": BYTES_PER_UPDATE,
                      "frac_of_nameplate": round(achieved / NAMEPLATE_HBM_GBS, 4),
+                     "bytes_moved_per_update": BYTES_MOVED_PER_UPDATE,
+                     "frac_at_bytes_moved": round(achieved * BYTES_MOVED_PER_UPDATE / BYTES_PER_UPDATE
+                                                  / peaks.get("hbm_gbs"), 4),
                      "traffic": None if traffic is None else round(traffic)},
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": "MLUPS", "h2d_bytes_per_step": round(h2d),
@@ -571,9 +637,14 @@ def main():
     ap.add_argument("--sur-forward-only", action="store_true",
                     help="time only the surrogate network's forward pass on a size x size lattice (He-normal "
                          "weights, random input) and print one JSON line")
+    ap.add_argument("--cpu-plan", action="store_true",
+                    help="time the FP64 oracle on all cores and on one core for the small configurations "
+                         "(64x256 layer, 512x256 channel, 512^2 droplet) and print one JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.cpu_plan:
+        run_cpu_plan(args)
     elif args.sur_forward_only:
         run_forward_only(args)
     else:

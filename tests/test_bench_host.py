@@ -16,8 +16,8 @@ def test_traffic_is_read_from_the_committed_summary():
     if got is None:
         pytest.skip("the step kernel changed since the ncu capture; its traffic is reported as null")
     per_cell = got / 1000
-    # the capture's DRAM bytes per update lie within a few percent of the algorithmic 360 B
-    assert 0.97 * bench.BYTES_PER_UPDATE < per_cell < 1.10 * bench.BYTES_PER_UPDATE
+    # the capture's DRAM bytes per update lie within a few percent of the 360 B the step moves
+    assert 0.97 * bench.BYTES_MOVED_PER_UPDATE < per_cell < 1.10 * bench.BYTES_MOVED_PER_UPDATE
 
 
 def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
@@ -51,11 +51,15 @@ def test_clock_summary_median_max_and_reasons():
 
 
 def test_roofline_fraction_arithmetic():
-    # 360 B per update at 13.44 GLUPS is 4.84 TB/s: 0.714 of a 6778.7 GB/s copy peak
+    # the algorithmic 352 B per update (36 populations and 8 lagged fields, read
+    # and written) at 13.44 GLUPS is 4.73 TB/s: 0.698 of a 6778.7 GB/s copy peak
+    assert bench.BYTES_PER_UPDATE == 36 * 4 * 2 + 8 * 4 * 2
     achieved = bench.BYTES_PER_UPDATE * 13439.41e6 / 1e9
-    assert achieved == pytest.approx(4838.2, abs=0.1)
-    assert achieved / 6778.7 == pytest.approx(0.7137, abs=1e-4)
-    assert achieved / bench.NAMEPLATE_HBM_GBS == pytest.approx(0.6124, abs=1e-4)
+    assert achieved == pytest.approx(4730.7, abs=0.1)
+    assert achieved / 6778.7 == pytest.approx(0.6979, abs=1e-4)
+    assert achieved / bench.NAMEPLATE_HBM_GBS == pytest.approx(0.5988, abs=1e-4)
+    assert bench.BYTES_PER_UPDATE_F16 == 36 * 2 * 2 + 8 * 4 * 2
+    assert bench.BYTES_PER_UPDATE_Q5 == 28 * 4 * 2 + 8 * 4 * 2
 
 
 def test_peaks_fall_back_when_the_measured_file_is_absent(tmp_path, monkeypatch):
