@@ -283,6 +283,46 @@ const char *lb_batch_last_error(const lb_batch *b);
 /* Free the batch and all of its instances; NULL is a no-op. */
 void lb_batch_destroy(lb_batch *b);
 
+/* ---- Slabs of one lattice (y-slab decomposition, one slab per GPU) -----------
+ * The step of Sec. 3 is local: a cell's update reads its own populations and
+ * those of its eight neighbours, and the isotropic stencils at the end of
+ * Sec. 3.4 reach one cell further.  A lattice cut into slabs of whole rows
+ * therefore advances exactly as one lattice when, before every step, each
+ * slab holds copies of the two rows of state (stored populations and lagged
+ * fields) next to it on either side: its ghost rows.  The result is bit for
+ * bit that of the whole lattice.  x stays periodic within every slab.
+ *
+ * lb_slab_create: the slab of rows [y0, y1) of the lattice `global` (walls,
+ * parameters and storage as for lb_create).  init holds the initial fields of
+ * rows [y0 - 2, y1 + 2) of the lattice, (y1 - y0 + 4) * nx values each,
+ * without the two rows below when y0 = 0 or above when y1 = global->ny (those
+ * ends are the lattice's walls); the handle's local lattice has those rows.
+ * Every slab, and so every neighbour, needs at least 4 rows: y1 - y0 >= 4,
+ * and y0 = 0 or y0 >= 4, and y1 = ny or ny - y1 >= 4 (LB_ERR_INVALID_ARG
+ * otherwise).  The handle works with every single-lattice call; lb_step,
+ * lb_reduce, lb_reduce_noalloc and lb_get_fields update, sum or read only the
+ * owned rows (the ghost rows of lb_get_fields's outputs hold no meaningful values;
+ * the diagnostics are the slab's share of the lattice's sums, with V_0 the
+ * slab's own).  Ghost rows are filled by lb_slab_unpack only. */
+lb_status lb_slab_create(const lb_grid *global, const lb_params *params, const lb_fields *init, int y0, int y1,
+                         lb_handle **out);
+
+/* Bytes of one face's halo message: 2 rows x nx values of the 36 population
+ * planes (4 bytes each, 2 with half storage) followed by the 9 lagged planes
+ * (FP32), plane by plane.  0 for a handle from lb_create. */
+size_t lb_slab_halo_bytes(const lb_handle *h);
+
+/* lb_slab_pack: the two owned rows next to face 0 (low y) or 1 (high y) of
+ * the current state into dst (lb_slab_halo_bytes bytes, caller-owned; host
+ * memory with on_device = 0, then the call synchronises the stream, or device
+ * memory, then it is asynchronous on the handle's stream).  After a step,
+ * the message of face 0 goes to the slab below, that of face 1 to the slab
+ * above.  lb_slab_unpack: a neighbour's message into the ghost rows at face
+ * (0: from the slab below, 1: from the slab above), same memory rules.  A
+ * face without a neighbouring slab is LB_ERR_INVALID_ARG. */
+lb_status lb_slab_pack(lb_handle *h, int face, void *dst, int on_device);
+lb_status lb_slab_unpack(lb_handle *h, int face, const void *src, int on_device);
+
 /* Static description of a status code. */
 const char *lb_error_string(int status);
 

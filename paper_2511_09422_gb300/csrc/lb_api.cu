@@ -42,6 +42,8 @@ struct lb_handle {
     lb_status sticky = LB_OK;
     std::string err;
     size_t bytes = 0;
+    unsigned char *halo = nullptr;  // device staging of one halo message (slabs with a host-memory exchange)
+    size_t halo_bytes = 0;          // bytes of one face's halo message (slabs only)
 };
 
 static thread_local std::string g_create_error;  // last lb_create failure of this thread
@@ -298,12 +300,15 @@ static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
 static void free_all(lb_handle *h)
 {
     void *ptrs[] = {h->pops[0], h->pops[1], h->aux[0], h->aux[1], h->fields, h->partials, h->red_out, h->status,
-                    h->rec,     h->counter};
+                    h->rec,     h->counter, h->halo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
 
-extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init, lb_handle **out)
+// A lattice, or a slab of one whose two rows at an end with ghost_* set are
+// ghost rows (see Consts::ghost_lo).
+static lb_status create_handle(const lb_grid *grid, const lb_params *params, const lb_fields *init, int ghost_lo,
+                               int ghost_hi, lb_handle **out)
 {
     if (!grid || !params || !init || !out) return fail(nullptr, LB_ERR_INVALID_ARG, "null argument");
     std::string why = check_params(grid, params);
@@ -316,6 +321,10 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     h->half = params->pop_storage == LB_STORAGE_F16;
     h->kind = h->half ? 1 : (params->lattice_fl == 1 ? 2 : 0);
     h->K = make_consts(grid, params);
+    h->K.ghost_lo = ghost_lo;
+    h->K.ghost_hi = ghost_hi;
+    if (ghost_lo || ghost_hi)
+        h->halo_bytes = (size_t)2 * grid->nx * (36 * (size_t)(h->half ? 2 : 4) + lbk::NAUX * sizeof(float));
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
     const size_t plane_b = sizeof(float) * (size_t)K.plane;
@@ -335,6 +344,7 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
     if (e == cudaSuccess) e = alloc((void **)&h->status, sizeof(unsigned));
     if (e == cudaSuccess) e = alloc((void **)&h->rec, sizeof(lbk::StepRec));
     if (e == cudaSuccess) e = alloc((void **)&h->counter, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess && h->halo_bytes) e = alloc((void **)&h->halo, h->halo_bytes);
     if (e != cudaSuccess) {
         lb_status s = cuda_fail(nullptr, e, "cudaMalloc");
         cudaGetLastError();
@@ -399,6 +409,83 @@ extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, con
         return st;
     }
     *out = h;
+    return LB_OK;
+}
+
+extern "C" lb_status lb_create(const lb_grid *grid, const lb_params *params, const lb_fields *init, lb_handle **out)
+{
+    return create_handle(grid, params, init, 0, 0, out);
+}
+
+// ---------------------------------------------------------------------------------------
+// Slabs of a larger lattice (y-slab decomposition across GPUs).
+// ---------------------------------------------------------------------------------------
+extern "C" lb_status lb_slab_create(const lb_grid *global, const lb_params *params, const lb_fields *init, int y0,
+                                    int y1, lb_handle **out)
+{
+    if (!global || !params || !init || !out) return fail(nullptr, LB_ERR_INVALID_ARG, "null argument");
+    if (y0 < 0 || y1 > global->ny || y1 - y0 < 4)
+        return fail(nullptr, LB_ERR_INVALID_ARG, "slab rows [y0, y1) must lie in [0, ny) and hold at least 4 rows");
+    if (y0 > 0 && y0 < 4)
+        return fail(nullptr, LB_ERR_INVALID_ARG, "a slab below this one would hold fewer than 4 rows (y0 < 4)");
+    if (y1 < global->ny && global->ny - y1 < 4)
+        return fail(nullptr, LB_ERR_INVALID_ARG, "a slab above this one would hold fewer than 4 rows (ny - y1 < 4)");
+    const int glo = y0 > 0 ? 2 : 0, ghi = y1 < global->ny ? 2 : 0;
+    lb_grid g = *global;
+    g.ny = y1 - y0 + glo + ghi;
+    return create_handle(&g, params, init, glo != 0, ghi != 0, out);
+}
+
+extern "C" size_t lb_slab_halo_bytes(const lb_handle *h) { return h ? h->halo_bytes : 0; }
+
+// first lattice row of the two rows that face `face` packs (owned) or unpacks (ghost)
+static int halo_row(const lb_handle *h, int face, bool ghost)
+{
+    const Consts &K = h->K;
+    if (face == 0) return ghost ? 0 : 2;
+    return ghost ? K.ny - 2 : K.ny - 4;
+}
+
+static lb_status halo_check(lb_handle *h, int face, const void *p)
+{
+    if (!h || !p) return fail(h, LB_ERR_INVALID_ARG, "null argument");
+    if (h->sticky != LB_OK) return h->sticky;
+    if ((face != 0 && face != 1) || !(face == 0 ? h->K.ghost_lo : h->K.ghost_hi))
+        return fail(h, LB_ERR_INVALID_ARG, "face must be 0 (low y) or 1 (high y) and have a neighbouring slab");
+    return LB_OK;
+}
+
+extern "C" lb_status lb_slab_pack(lb_handle *h, int face, void *dst, int on_device)
+{
+    lb_status s = halo_check(h, face, dst);
+    if (s != LB_OK) return s;
+    unsigned char *msg = on_device ? (unsigned char *)dst : h->halo;
+    const long long vals = 2LL * h->K.nx * (36 + lbk::NAUX);
+    lbk::lb_halo_pack_kernel<<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
+        h->K, (const unsigned char *)h->pops[h->cur], h->aux[h->cur], h->half ? 2 : 4, 36, halo_row(h, face, false),
+        msg);
+    CK(h, cudaGetLastError());
+    if (!on_device) {
+        CK(h, cudaMemcpyAsync(dst, h->halo, h->halo_bytes, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return LB_OK;
+}
+
+extern "C" lb_status lb_slab_unpack(lb_handle *h, int face, const void *src, int on_device)
+{
+    lb_status s = halo_check(h, face, src);
+    if (s != LB_OK) return s;
+    const unsigned char *msg = (const unsigned char *)src;
+    if (!on_device) {
+        CK(h, cudaMemcpyAsync(h->halo, src, h->halo_bytes, cudaMemcpyHostToDevice, h->stream));
+        msg = h->halo;
+    }
+    const long long vals = 2LL * h->K.nx * (36 + lbk::NAUX);
+    lbk::lb_halo_unpack_kernel<<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
+        h->K, (unsigned char *)h->pops[h->cur], h->aux[h->cur], h->half ? 2 : 4, 36, halo_row(h, face, true), msg);
+    CK(h, cudaGetLastError());
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 
@@ -631,8 +718,9 @@ __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Co
     __shared__ double sh[lbk::RED_THREADS / 32][lbk::NRED];
     const int y = blockIdx.x;
     const int xc = K.nx / 2;
+    const bool ghost = (K.ghost_lo && y < 2) || (K.ghost_hi && y >= K.ny - 2);  // a slab's ghost rows add nothing
     double acc[lbk::NRED] = {0, 0, 0, 0, 0, 0};
-    for (int x = threadIdx.x; x < K.nx; x += blockDim.x) {
+    for (int x = ghost ? K.nx : (int)threadIdx.x; x < K.nx; x += blockDim.x) {
         const int cell = y * K.pitch + x;
         const lbk::CellA c =
             lbk::cell_a<PS>(K, reinterpret_cast<const typename PS::T *>(pin), ain, x, y, cell);

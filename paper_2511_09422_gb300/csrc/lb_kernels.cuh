@@ -123,6 +123,11 @@ struct Consts {
     int segh;                   // rows of an inner segment of the strip sweep
     int qfl;                    // lattice of the phase-field and solute sets: 9 or 5 velocities
     int divu;                   // div u in the phi and h sources: 0 the model value mdot, 1 the lagged velocity divergence
+    // Slab of a larger lattice (y-slab decomposition): 1 when the two rows at
+    // this end are ghost rows holding the neighbouring slab's state instead of
+    // rows next to a wall.  Ghost rows are read by the sweep but never updated,
+    // summed or read out; the sweep then has no wall at that end.
+    int ghost_lo, ghost_hi;
 };
 
 struct Buffers {
@@ -1323,6 +1328,7 @@ __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B,
         const int x0 = (group * LB_SW + (int)threadIdx.y) * LB_TX;
         int ys, ye;
         segment_rows(K.ny, K.segh, seg, ys, ye);
+        if ((seg == 0 && K.ghost_lo) || (seg == 1 && K.ghost_hi)) continue;  // ghost rows of a slab
         if (x0 >= K.nx || ys >= ye) continue;  // the whole warp: warps never synchronise with one another
         if (seg < 2)
             strip_rows<MODE, true, PS>(K, B, w, lane, x0, ys, ye, acc);
@@ -1397,7 +1403,7 @@ __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst,
         const int strip = (int)(local % nstrip), seg = (int)(local / nstrip);
         int ys, ye;
         segment_rows(K.ny, K.segh, seg, ys, ye);
-        if (ys >= ye) continue;
+        if (ys >= ye || (seg == 0 && K.ghost_lo) || (seg == 1 && K.ghost_hi)) continue;
         if (seg < 2)
             strip_rows<MODE_STEP, true, PS>(K, B, w, lane, strip * LB_TX, ys, ye, acc);
         else
@@ -1554,6 +1560,56 @@ __global__ void __launch_bounds__(RED_THREADS) lb_reduce_final_kernel(const doub
         double s = 0.0;
         for (int j = 0; j < RED_THREADS / 32; j++) s += sh[j][threadIdx.x];
         out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Halo messages of a slab (y-slab decomposition).  A message holds, for every
+// population plane (storage type, elem bytes) and then every lagged plane
+// (FP32), two lattice rows of nx values: rows [r0, r0 + 2) of the buffer,
+// plane after plane, rows consecutive.  pack copies them out of `state`
+// (populations then lagged planes), unpack writes them into it.
+// ---------------------------------------------------------------------------------------
+__global__ void lb_halo_pack_kernel(const Consts K, const unsigned char *__restrict__ pops,
+                                    const float *__restrict__ aux, int elem, int npop, int r0,
+                                    unsigned char *__restrict__ msg)
+{
+    const long long per_plane = 2LL * K.nx;
+    const long long pop_vals = per_plane * npop, total = pop_vals + per_plane * NAUX;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const bool is_pop = k < pop_vals;
+        const long long kk = is_pop ? k : k - pop_vals;
+        const int plane = (int)(kk / per_plane), r = (int)((kk % per_plane) / K.nx), x = (int)(kk % K.nx);
+        const long long src = (long long)plane * K.plane + (long long)(r0 + r) * K.pitch + x;
+        if (is_pop) {
+            if (elem == 4)
+                reinterpret_cast<float *>(msg)[k] = reinterpret_cast<const float *>(pops)[src];
+            else
+                reinterpret_cast<unsigned short *>(msg)[k] = reinterpret_cast<const unsigned short *>(pops)[src];
+        } else {
+            reinterpret_cast<float *>(msg + pop_vals * elem)[kk] = aux[src];
+        }
+    }
+}
+
+__global__ void lb_halo_unpack_kernel(const Consts K, unsigned char *__restrict__ pops, float *__restrict__ aux,
+                                      int elem, int npop, int r0, const unsigned char *__restrict__ msg)
+{
+    const long long per_plane = 2LL * K.nx;
+    const long long pop_vals = per_plane * npop, total = pop_vals + per_plane * NAUX;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+        const bool is_pop = k < pop_vals;
+        const long long kk = is_pop ? k : k - pop_vals;
+        const int plane = (int)(kk / per_plane), r = (int)((kk % per_plane) / K.nx), x = (int)(kk % K.nx);
+        const long long dst = (long long)plane * K.plane + (long long)(r0 + r) * K.pitch + x;
+        if (is_pop) {
+            if (elem == 4)
+                reinterpret_cast<float *>(pops)[dst] = reinterpret_cast<const float *>(msg)[k];
+            else
+                reinterpret_cast<unsigned short *>(pops)[dst] = reinterpret_cast<const unsigned short *>(msg)[k];
+        } else {
+            aux[dst] = reinterpret_cast<const float *>(msg + pop_vals * elem)[kk];
+        }
     }
 }
 

@@ -57,7 +57,8 @@ _lock = threading.Lock()
 EXPORTS = ("lb_create", "lb_set_stream", "lb_step", "lb_get_fields", "lb_set_fields", "lb_reduce", "lb_steps_taken",
            "lb_save", "lb_load", "lb_destroy", "lb_error_string", "lb_last_error", "lb_device_bytes",
            "lb_batch_create", "lb_batch_set_stream", "lb_batch_step", "lb_batch_use_graph", "lb_batch_tune",
-           "lb_batch_instance", "lb_batch_size", "lb_batch_last_error", "lb_batch_destroy")
+           "lb_batch_instance", "lb_batch_size", "lb_batch_last_error", "lb_batch_destroy",
+           "lb_slab_create", "lb_slab_halo_bytes", "lb_slab_pack", "lb_slab_unpack")
 
 
 def library_path() -> str:
@@ -119,6 +120,15 @@ def load(path: str | None = None):
         L.lb_batch_last_error.argtypes = [C.c_void_p]
         L.lb_batch_destroy.restype = None
         L.lb_batch_destroy.argtypes = [C.c_void_p]
+        L.lb_slab_create.restype = C.c_int
+        L.lb_slab_create.argtypes = [C.POINTER(lb_grid), C.POINTER(lb_params), C.POINTER(lb_fields), C.c_int, C.c_int,
+                                     C.POINTER(C.c_void_p)]
+        L.lb_slab_halo_bytes.restype = C.c_size_t
+        L.lb_slab_halo_bytes.argtypes = [C.c_void_p]
+        L.lb_slab_pack.restype = C.c_int
+        L.lb_slab_pack.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
+        L.lb_slab_unpack.restype = C.c_int
+        L.lb_slab_unpack.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int]
         _lib = L
         return _lib
 
@@ -167,6 +177,12 @@ def _host_array(v) -> np.ndarray:
     return np.asarray(v, dtype=np.float32)
 
 
+def slab_extent(ny: int, y0: int, y1: int):
+    """Local rows of the slab [y0, y1) of a lattice of ny rows: [y0 - 2, y1 + 2),
+    without the two ghost rows at an end that is a wall (y0 = 0 or y1 = ny)."""
+    return (y0 - 2 if y0 > 0 else 0), (y1 + 2 if y1 < ny else ny)
+
+
 class Solver:
     """One lattice on the GPU.
 
@@ -176,9 +192,20 @@ class Solver:
     is a torch.cuda.Stream, a raw cudaStream_t integer, or None (legacy default
     stream)."""
 
-    def __init__(self, grid: dict, params: dict, fields: dict, stream=None):
+    def __init__(self, grid: dict, params: dict, fields: dict, stream=None, slab=None):
+        """``slab=(y0, y1)`` makes this the slab of rows [y0, y1) of the lattice
+        ``grid`` (lb_slab_create): ``fields`` then hold the rows [y0 - 2, y1 + 2)
+        of the lattice's initial fields, the two extra rows at an end only where
+        a neighbouring slab lies (``slab_extent``), and ``ny`` is the local row
+        count including those ghost rows."""
         L = load()
-        self.nx, self.ny = int(grid["nx"]), int(grid["ny"])
+        self.nx = int(grid["nx"])
+        self.slab = None if slab is None else (int(slab[0]), int(slab[1]))
+        if self.slab is None:
+            self.ny = int(grid["ny"])
+        else:
+            lo, hi = slab_extent(int(grid["ny"]), *self.slab)
+            self.ny = hi - lo
         n = self.nx * self.ny
         self._grid, self._params = make_grid(grid), make_params(params)
         keep = {}
@@ -211,7 +238,11 @@ class Solver:
             import torch
             torch.cuda.current_stream().synchronize()  # the inputs' producers have finished
         h = C.c_void_p()
-        st = L.lb_create(C.byref(self._grid), C.byref(self._params), C.byref(f), C.byref(h))
+        if self.slab is None:
+            st = L.lb_create(C.byref(self._grid), C.byref(self._params), C.byref(f), C.byref(h))
+        else:
+            st = L.lb_slab_create(C.byref(self._grid), C.byref(self._params), C.byref(f), self.slab[0], self.slab[1],
+                                  C.byref(h))
         if st != LB_OK:
             raise LbError(st, L.lb_last_error(None).decode())
         self._h = h
@@ -276,6 +307,38 @@ class Solver:
     # -- the method ---------------------------------------------------------------------------
     def step(self, n: int = 1):
         self._check(load().lb_step(self._h, int(n)))
+
+    # -- slabs of a larger lattice ------------------------------------------------------------
+    @property
+    def halo_bytes(self) -> int:
+        """Bytes of one face's halo message (0 for a whole lattice)."""
+        return int(load().lb_slab_halo_bytes(self._h))
+
+    def pack_halo(self, face: int, dst):
+        """The two owned rows next to face 0 (low y) or 1 (high y), every
+        population and lagged plane, into ``dst``: a uint8 numpy array / torch
+        CPU tensor (synchronises) or a uint8 CUDA tensor (on the handle's
+        stream, ordered with torch's current stream) of halo_bytes bytes."""
+        self._halo_call(load().lb_slab_pack, face, dst)
+
+    def unpack_halo(self, face: int, src):
+        """A neighbour's message (see pack_halo) into the ghost rows at ``face``."""
+        self._halo_call(load().lb_slab_unpack, face, src)
+
+    def _halo_call(self, fn, face, buf):
+        if _is_cuda_tensor(buf):
+            import torch
+            if buf.numel() * buf.element_size() != self.halo_bytes or not buf.is_contiguous():
+                raise ValueError("halo buffer must be contiguous with halo_bytes bytes")
+            hs, cur = _torch_stream(self._stream_obj), torch.cuda.current_stream()
+            hs.wait_stream(cur)
+            self._check(fn(self._h, int(face), C.c_void_p(buf.data_ptr()), 1))
+            cur.wait_stream(hs)
+            return
+        h = buf.detach().numpy() if _is_torch(buf) else buf
+        if not (isinstance(h, np.ndarray) and h.flags["C_CONTIGUOUS"] and h.nbytes == self.halo_bytes):
+            raise ValueError("halo buffer must be contiguous with halo_bytes bytes")
+        self._check(fn(self._h, int(face), C.c_void_p(h.ctypes.data), 0))
 
     def fields(self, device: bool = False, names=FIELD_NAMES, out=None):
         """Macroscopic fields of the current state as (ny, nx) arrays: numpy on

@@ -120,6 +120,27 @@ def test_null_arguments(lib):
     assert lib.lb_step(None, 1) == lbfreeze.LB_ERR_INVALID_ARG
     assert lib.lb_reduce(None, None) == lbfreeze.LB_ERR_INVALID_ARG
     assert lib.lb_get_fields(None, *([None] * 7), 0) == lbfreeze.LB_ERR_INVALID_ARG
+    assert lib.lb_slab_create(None, None, None, 0, 8, None) == lbfreeze.LB_ERR_INVALID_ARG
+    assert lib.lb_slab_pack(None, 0, None, 0) == lbfreeze.LB_ERR_INVALID_ARG
+    assert lib.lb_slab_unpack(None, 1, None, 1) == lbfreeze.LB_ERR_INVALID_ARG
+    assert lib.lb_slab_halo_bytes(None) == 0
+
+
+@pytest.mark.parametrize("y0,y1", [(0, 3), (2, 20), (20, 38), (-1, 10), (30, 41)])
+def test_slab_rows_rejected_without_a_device(lib, y0, y1):
+    """A slab of fewer than 4 rows, or one that leaves a neighbour fewer than
+    4, or one outside the lattice, is refused before any device work."""
+    import ctypes as C
+    w = W.parity_droplet(nx=32, ny=40)
+    f = lbfreeze.lb_fields()
+    phi = np.zeros(32 * 44, dtype=np.float32)
+    for k in ("phi", "T", "C"):
+        setattr(f, k, phi.ctypes.data_as(C.POINTER(C.c_float)))
+    h = C.c_void_p()
+    st = lib.lb_slab_create(C.byref(lbfreeze.make_grid(w["grid"])), C.byref(lbfreeze.make_params(w["params"])),
+                            C.byref(f), y0, y1, C.byref(h))
+    assert st == lbfreeze.LB_ERR_INVALID_ARG and h.value is None
+    assert b"slab" in lib.lb_last_error(None)
 
 
 def test_workloads_are_seeded():

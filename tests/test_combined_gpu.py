@@ -4,7 +4,7 @@ sets and with half-precision storage, a liquid column whose interface meets
 two Dirichlet walls of different contact angles while it freezes, and the
 edge shapes of the row and strip layout under D2Q5 and half storage.  The
 bars are those of the single options: 1e-5 per field for FP32 D2Q9 storage,
-the D2Q5 bars of test_d2q5_gpu (2e-5 on u and p), and the half-storage bar of
+the same 1e-5 for D2Q5 f and l (test_d2q5_gpu), and the half-storage bar of
 test_fp16_gpu.  Every case is well conditioned: the oracle itself moves by
 less than 1e-6 when its inputs are perturbed by 1e-7."""
 import numpy as np

@@ -29,25 +29,66 @@ def _q5(w):
     return dict(w, params=dict(w["params"], lattice_fl=Q5))
 
 
-# The conserved and thermal fields keep the 1e-5 bar of the D2Q9 path.  The
-# velocity and pressure get 2e-5: on the ragged 97 x 71 droplet one gas cell
-# under the top wall jumps to 1.3e-5 (u_y) between steps 95 and 100, while the
-# error elsewhere stays at the D2Q9 level (1e-7 .. 1e-6) and the oracle's own
-# response to FP32-sized input noise there is 1e-7: an FP32 rounding event at
-# that cell, not a systematic difference (the end-of-run freezing-time check
-# below holds at 1e-3).
-TOL_Q5 = {"phi": 1e-5, "T": 1e-5, "fs": 1e-5, "C": 1e-5, "ux": 2e-5, "uy": 2e-5, "p": 2e-5}
+# Every field keeps the 1e-5 bar of the D2Q9 path.
+TOL_Q5 = {"phi": 1e-5, "T": 1e-5, "fs": 1e-5, "C": 1e-5, "ux": 1e-5, "uy": 1e-5, "p": 1e-5}
+
+# The ragged 97 x 71 droplet with div u = mdot (divu_mode = 0) passes through a
+# short ill-conditioned transient at the top wall: between steps 99 and 105 the
+# expansion flow reaches the gas layer under the wall, where the D2Q5 phase field
+# overshoots to phi = -1.014, and any perturbation there grows about 100-fold and
+# decays again by step 107.  Two GPU runs whose inputs differ by 1e-7 differ by
+# 1.2e-5 in u_y at step 100 and 2.3e-5 at step 102, as much as GPU and oracle do
+# (test_d2q5_top_wall_transient_is_ill_conditioned), so that case is compared at
+# step 150, after the transient (measured 4e-6).  All other cases, and this one
+# with the lagged velocity divergence, are compared at step 100.
+STEPS_Q5 = {("ragged_droplet_97x71", 0): 150}
 
 
+@pytest.mark.parametrize("divu_mode", [0, 1])
 @pytest.mark.parametrize("name,make,steps", P.CASES, ids=[c[0] for c in P.CASES])
-def test_parity_d2q5(oracle_mod, name, make, steps):
+def test_parity_d2q5(oracle_mod, name, make, steps, divu_mode):
     w = _q5(make())
-    got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=w["params"])
+    p = dict(w["params"], divu_mode=divu_mode)
+    steps = STEPS_Q5.get((name, divu_mode), steps)
+    got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=p)
     errs = P._rel_errors(got, want)
     bad = {k: v for k, v in errs.items() if not v <= TOL_Q5[k]}
-    assert not bad, (name, bad, errs)
+    assert not bad, (name, divu_mode, bad, errs)
     P._assert_reduce(red, wred)
 
+
+def test_d2q5_top_wall_transient_is_ill_conditioned(oracle_mod):
+    """The transient that makes the mdot-reading 97 x 71 droplet unfit for a
+    comparison at step 100 is a property of the case, not a difference between
+    GPU and oracle: a GPU run from inputs perturbed by 1e-7 (relative) moves
+    away from the unperturbed GPU run by more than 1e-5 in u_y at step 102, and
+    the GPU-oracle difference there is of the same size; by step 150 both are
+    back below 1e-5."""
+    from paper_2511_09422_gb300 import lbfreeze
+    w = _q5(W.parity_droplet(nx=97, ny=71, seed=3))
+    p = dict(w["params"], divu_mode=0)
+    f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
+    rng = np.random.default_rng(5)
+    g32 = {k: (v.astype(np.float64) * (1 + 1e-7 * rng.uniform(-1, 1, size=v.shape))).astype(np.float32)
+           for k, v in f32.items()}
+    a, b = lbfreeze.Solver(w["grid"], p, f32), lbfreeze.Solver(w["grid"], p, g32)
+    o = oracle_mod.Oracle(w["grid"], p, {k: v.astype(np.float64) for k, v in f32.items()})
+    out = {}
+    for n in (102, 150):
+        a.step(n - a.steps)
+        b.step(n - b.steps)
+        o.step(n - o.steps)
+        fa, fb, fo = a.fields(), b.fields(), o.fields()
+        speed = float(np.sqrt(fo["ux"] ** 2 + fo["uy"] ** 2).max())
+        gg = float(np.abs(fa["uy"].astype(np.float64) - fb["uy"]).max()) / speed
+        go = float(np.abs(fa["uy"].astype(np.float64) - fo["uy"]).max()) / speed
+        out[n] = (gg, go)
+    a.close()
+    b.close()
+    gg, go = out[102]
+    assert gg > 1e-5, out
+    assert go < 3.0 * gg, out
+    assert max(out[150]) < 1e-5, out
 
 
 def test_d2q5_full_size_bench_workload(oracle_mod):
