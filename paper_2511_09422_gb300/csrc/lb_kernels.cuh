@@ -718,7 +718,8 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
     // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi div u
     {
-        const real ux_p = A.aux(AX_UX), uy_p = A.aux(AX_UY);
+        const float2 u_p = K.divu ? A.lagu() : make_float2(A.aux(AX_UX), A.aux(AX_UY));
+        const real ux_p = u_p.x, uy_p = u_p.y;
         const real kf = -(R(1.0) / R(3.0)) * phi2m1 * K.inv_s2eps;
         const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
         const real ay = (phi * uy - phi_p * uy_p) + kf * nyv;
@@ -987,6 +988,7 @@ struct RingAcc {
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
     __device__ real divu() const { return w.dv[sl[1]][lane]; }
+    __device__ float2 lagu() const { return w.uv[sl[1]][lane + 1]; }  // own lagged (u_x, u_y), divu mode only
     // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
@@ -1149,8 +1151,10 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (wg < 3) {
             const int k0 = wg, k1 = wg + 3;
             const int a0 = k0 == 0 ? AUX_Q : (k0 == 1 ? AUX_FS : AUX_UX);
-            if (PB || k0 < 2) cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
-            if (PB && k1 < NAX)
+            // with the lagged velocity divergence the own-cell u comes from the uv ring
+            if ((PB && !(K.divu && k0 == 2)) || k0 < 2)
+                cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
+            if (PB && k1 < NAX && !(K.divu && k1 == 3))
                 cp_async16(&w.ax[s3][k1][4 * wpart], plane_ptr(ain, k1 == 3 ? AUX_UY : AUX_C, K) + (y * K.pitch + wcol));
         }
     };
@@ -1194,8 +1198,10 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
             cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
             if (PB) {
-                cp_async4(pa + AX_UX * WW, plane_ptr(ain, AUX_UX, K) + cell);
-                cp_async4(pa + AX_UY * WW, plane_ptr(ain, AUX_UY, K) + cell);
+                if (!K.divu) {  // else from the uv ring
+                    cp_async4(pa + AX_UX * WW, plane_ptr(ain, AUX_UX, K) + cell);
+                    cp_async4(pa + AX_UY * WW, plane_ptr(ain, AUX_UY, K) + cell);
+                }
                 cp_async4(pa + AX_C * WW, plane_ptr(ain, AUX_C, K) + cell);
             }
         }
