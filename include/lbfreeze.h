@@ -100,9 +100,14 @@ typedef struct {
  * FP32 and the lagged fields stay FP32.  Half storage rounds every stored
  * population to 11 bits, so its results differ from the FP32 ones (tests state
  * the difference per field); a deviation beyond 2^8 x 65504 becomes infinite and
- * is reported as LB_ERR_UNSTABLE. */
+ * is reported as LB_ERR_UNSTABLE.  LB_STORAGE_F16_H32 (2): f, g and l as with
+ * LB_STORAGE_F16, the enthalpy set h in FP32 as with LB_STORAGE_F32 (252
+ * instead of 360 bytes per update); the rounding of the stored enthalpy
+ * deviations is what moves the freezing time of a long run in half storage, so
+ * this form keeps it at the FP32 level. */
 #define LB_STORAGE_F32 0
 #define LB_STORAGE_F16 1
+#define LB_STORAGE_F16_H32 2
 /* lattice_fl: velocity set of the phase-field (f) and solute (l) sets.  The
  * paper does not name it; LB_LATTICE_D2Q9 (0) uses D2Q9 for all four sets.
  * LB_LATTICE_D2Q5 (1) uses D2Q5 for f and l: the five velocities c_0 .. c_4

@@ -32,9 +32,10 @@ struct lb_handle {
     unsigned long long *counter = nullptr;  // the step kernel's work counters (2)
     long long nitems = 0;                   // work items of one step
     int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
-    bool half = false;           // populations stored in half precision
-    int kind = 0;                // kernel instantiation: 0 FP32 D2Q9, 1 FP16 D2Q9, 2 FP32 with D2Q5 f and l
-    size_t pop_bytes() const { return (half ? 2 : 4) * 36 * (size_t)K.plane; }
+    bool half = false;           // some populations stored in half precision
+    // kernel instantiation: 0 FP32 D2Q9, 1 FP16 D2Q9, 2 FP32 with D2Q5 f and l, 3 FP16 f, g, l with FP32 h
+    int kind = 0;
+    size_t pop_bytes() const;
     int cur = 0;
     cudaStream_t stream = nullptr;
     double V0 = 0.0;
@@ -45,6 +46,21 @@ struct lb_handle {
     unsigned char *halo = nullptr;  // device staging of one halo message (slabs with a host-memory exchange)
     size_t halo_bytes = 0;          // bytes of one face's halo message (slabs only)
 };
+
+// Calls f(PS{}) with the storage trait of kernel kind `kind`.
+template <class F>
+static auto with_storage(int kind, F f)
+{
+    if (kind == 1) return f(lbk::PopF16{});
+    if (kind == 2) return f(lbk::PopF32Q5{});
+    if (kind == 3) return f(lbk::PopF16H{});
+    return f(lbk::PopF32{});
+}
+
+size_t lb_handle::pop_bytes() const
+{
+    return with_storage(kind, [&](auto ps) { return (size_t)lbk::pop_cell_bytes<decltype(ps)>() * (size_t)K.plane; });
+}
 
 static thread_local std::string g_create_error;  // last lb_create failure of this thread
 
@@ -120,8 +136,8 @@ static std::string check_params(const lb_grid *g, const lb_params *p)
     if (!(p->D_l > 0) || p->D_s < 0) return "D_l must be > 0 and D_s >= 0 (tau_l > 1/2 in the liquid)";
     if (!(p->k_p > 0)) return "k_p must be > 0";
     if (p->divu_mode != 0 && p->divu_mode != 1) return "divu_mode must be 0 or 1";
-    if (p->pop_storage != LB_STORAGE_F32 && p->pop_storage != LB_STORAGE_F16)
-        return "pop_storage must be LB_STORAGE_F32 or LB_STORAGE_F16";
+    if (p->pop_storage != LB_STORAGE_F32 && p->pop_storage != LB_STORAGE_F16 && p->pop_storage != LB_STORAGE_F16_H32)
+        return "pop_storage must be LB_STORAGE_F32, LB_STORAGE_F16 or LB_STORAGE_F16_H32";
     if (p->lattice_fl != LB_LATTICE_D2Q9 && p->lattice_fl != LB_LATTICE_D2Q5)
         return "lattice_fl must be LB_LATTICE_D2Q9 or LB_LATTICE_D2Q5";
     if (p->lattice_fl == LB_LATTICE_D2Q5 && p->pop_storage != LB_STORAGE_F32)
@@ -169,7 +185,7 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.gx = (real)p->gx; K.gy = (real)p->gy;
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
-    K.segh = (p->pop_storage == LB_STORAGE_F16 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
+    K.segh = (p->pop_storage != LB_STORAGE_F32 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
     // a small lattice needs shorter segments to give every resident warp work: go
     // down (to 8 rows at least) until there are two waves of work items
     {
@@ -217,12 +233,7 @@ static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t
 template <int MODE>
 static void launch_strip(const Consts &K, const lbk::Buffers &B, cudaStream_t st, int kind, double *partials = nullptr)
 {
-    if (kind == 1)
-        launch_strip_as<MODE, lbk::PopF16>(K, B, st, partials);
-    else if (kind == 2)
-        launch_strip_as<MODE, lbk::PopF32Q5>(K, B, st, partials);
-    else
-        launch_strip_as<MODE, lbk::PopF32>(K, B, st, partials);
+    with_storage(kind, [&](auto ps) { launch_strip_as<MODE, decltype(ps)>(K, B, st, partials); });
 }
 
 static int flat_blocks(long long n, int threads)
@@ -273,9 +284,9 @@ static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long 
 static cudaError_t launch_step(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
                                unsigned long long *counter, cudaStream_t st, int kind)
 {
-    if (kind == 1) return launch_step_as<lbk::PopF16>(rec, ninst, nitems, parity, counter, st);
-    if (kind == 2) return launch_step_as<lbk::PopF32Q5>(rec, ninst, nitems, parity, counter, st);
-    return launch_step_as<lbk::PopF32>(rec, ninst, nitems, parity, counter, st);
+    return with_storage(kind, [&](auto ps) {
+        return launch_step_as<decltype(ps)>(rec, ninst, nitems, parity, counter, st);
+    });
 }
 
 static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
@@ -318,13 +329,17 @@ static lb_status create_handle(const lb_grid *grid, const lb_params *params, con
     lb_handle *h = new lb_handle();
     h->grid = *grid;
     h->params = *params;
-    h->half = params->pop_storage == LB_STORAGE_F16;
-    h->kind = h->half ? 1 : (params->lattice_fl == 1 ? 2 : 0);
+    h->half = params->pop_storage != LB_STORAGE_F32;
+    h->kind = params->pop_storage == LB_STORAGE_F16 ? 1
+                                                    : (params->pop_storage == LB_STORAGE_F16_H32 ? 3
+                                                                                                 : (params->lattice_fl == 1 ? 2 : 0));
     h->K = make_consts(grid, params);
     h->K.ghost_lo = ghost_lo;
     h->K.ghost_hi = ghost_hi;
     if (ghost_lo || ghost_hi)
-        h->halo_bytes = (size_t)2 * grid->nx * (36 * (size_t)(h->half ? 2 : 4) + lbk::NAUX * sizeof(float));
+        h->halo_bytes = with_storage(h->kind, [&](auto ps) {
+            return (size_t)lbk::halo_message_bytes<decltype(ps)>(grid->nx);
+        });
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
     const size_t plane_b = sizeof(float) * (size_t)K.plane;
@@ -383,12 +398,11 @@ static lb_status create_handle(const lb_grid *grid, const lb_params *params, con
         }
         lbk::lb_init_eq_kernel<<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3], dev[4],
                                                                            nullptr, nullptr, eq, h->aux[0], 0);
-        if (h->half)
-            lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
-                                                                                                 h->pops[0]);
-        else
-            lbk::lb_init_unstream_kernel<lbk::PopF32><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
-                                                                                                 h->pops[0]);
+        with_storage(h->kind, [&](auto ps) {
+            lbk::lb_init_unstream_kernel<decltype(ps)><<<flat_blocks(n, 256), 256, 0, h->stream>>>(K, eq, h->aux[0],
+                                                                                                  h->pops[0]);
+            return 0;
+        });
         cudaError_t ce = cudaGetLastError();
         if (eq_tmp) {
             cudaError_t fe = cudaStreamSynchronize(h->stream);
@@ -461,9 +475,11 @@ extern "C" lb_status lb_slab_pack(lb_handle *h, int face, void *dst, int on_devi
     if (s != LB_OK) return s;
     unsigned char *msg = on_device ? (unsigned char *)dst : h->halo;
     const long long vals = 2LL * h->K.nx * (36 + lbk::NAUX);
-    lbk::lb_halo_pack_kernel<<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
-        h->K, (const unsigned char *)h->pops[h->cur], h->aux[h->cur], h->half ? 2 : 4, 36, halo_row(h, face, false),
-        msg);
+    with_storage(h->kind, [&](auto ps) {
+        lbk::lb_halo_kernel<decltype(ps), true><<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
+            h->K, (unsigned char *)h->pops[h->cur], h->aux[h->cur], halo_row(h, face, false), msg);
+        return 0;
+    });
     CK(h, cudaGetLastError());
     if (!on_device) {
         CK(h, cudaMemcpyAsync(dst, h->halo, h->halo_bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -482,8 +498,12 @@ extern "C" lb_status lb_slab_unpack(lb_handle *h, int face, const void *src, int
         msg = h->halo;
     }
     const long long vals = 2LL * h->K.nx * (36 + lbk::NAUX);
-    lbk::lb_halo_unpack_kernel<<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
-        h->K, (unsigned char *)h->pops[h->cur], h->aux[h->cur], h->half ? 2 : 4, 36, halo_row(h, face, true), msg);
+    with_storage(h->kind, [&](auto ps) {
+        lbk::lb_halo_kernel<decltype(ps), false><<<flat_blocks(vals, 256), 256, 0, h->stream>>>(
+            h->K, (unsigned char *)h->pops[h->cur], h->aux[h->cur], halo_row(h, face, true),
+            const_cast<unsigned char *>(msg));
+        return 0;
+    });
     CK(h, cudaGetLastError());
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
     return LB_OK;
@@ -570,12 +590,11 @@ extern "C" lb_status lb_set_fields(lb_handle *h, const float *phi, const float *
     lbk::lb_init_eq_kernel<<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(K, dev[0], dev[1], dev[2], dev[3],
                                                                                  dev[4], dev[5], dev[6], eq,
                                                                                  h->aux[h->cur], 1);
-    if (h->half)
-        lbk::lb_init_unstream_kernel<lbk::PopF16><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
+    with_storage(h->kind, [&](auto ps) {
+        lbk::lb_init_unstream_kernel<decltype(ps)><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
             K, eq, h->aux[h->cur], h->pops[h->cur]);
-    else
-        lbk::lb_init_unstream_kernel<lbk::PopF32><<<flat_blocks((long long)n, 256), 256, 0, h->stream>>>(
-            K, eq, h->aux[h->cur], h->pops[h->cur]);
+        return 0;
+    });
     CK(h, cudaGetLastError());
     if (eq_tmp) CK(h, cudaFreeAsync(eq_tmp, h->stream));
     if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
@@ -723,7 +742,7 @@ __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Co
     for (int x = ghost ? K.nx : (int)threadIdx.x; x < K.nx; x += blockDim.x) {
         const int cell = y * K.pitch + x;
         const lbk::CellA c =
-            lbk::cell_a<PS>(K, reinterpret_cast<const typename PS::T *>(pin), ain, x, y, cell);
+            lbk::cell_a<PS>(K, pin, ain, x, y, cell);
         const double phid = (double)c.phi_p + (double)c.L.dphi;
         acc[0] += phid;
         acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
@@ -785,15 +804,11 @@ extern "C" lb_status lb_reduce_noalloc(lb_handle *h, double out[8])
         }
         scratch = g_noalloc_addr[dev];
     }
-    if (h->half)
-        noalloc_rows_kernel<lbk::PopF16><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
-                                                                                  scratch);
-    else if (h->kind == 2)
-        noalloc_rows_kernel<lbk::PopF32Q5><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur],
-                                                                                    h->aux[h->cur], scratch);
-    else
-        noalloc_rows_kernel<lbk::PopF32><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur], h->aux[h->cur],
-                                                                                  scratch);
+    with_storage(h->kind, [&](auto ps) {
+        noalloc_rows_kernel<decltype(ps)><<<K.ny, lbk::RED_THREADS, 0, h->stream>>>(K, h->pops[h->cur],
+                                                                                   h->aux[h->cur], scratch);
+        return 0;
+    });
     CK(h, cudaGetLastError());
     noalloc_total_kernel<<<1, 32, 0, h->stream>>>(scratch, K.ny);
     CK(h, cudaGetLastError());

@@ -45,6 +45,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 // Arithmetic type of the step (FP32; the diagnostics sums are FP64).
 typedef float real;
 #define R(x) ((real)(x))
@@ -72,30 +74,58 @@ __host__ __device__ inline real wfl_rt(int q, int i) { return q == 5 ? wfl<5>(i)
 
 constexpr int SET_F = 0, SET_G = 1, SET_H = 2, SET_L = 3;
 
-// Storage of the 36 population planes.  PopF32: FP32 deviations (see the top of
-// this file).  PopF16: the same deviations times 2^8 in IEEE half precision, the
-// solute set additionally shifted by w_i c_ref, halving the population bytes; the
-// arithmetic stays FP32.  A deviation beyond 2^8 * 65504 overflows to infinity,
-// which the step reports as non-finite.
+// Storage of the 36 population planes, per set (f, g, h, l).  PopF32: FP32
+// deviations (see the top of this file).  PopF16: the same deviations times 2^8
+// in IEEE half precision, the solute set additionally shifted by w_i c_ref,
+// halving the population bytes.  PopF16H: f, g and l as PopF16, the enthalpy set
+// h in FP32 (its rounding sets the freezing-time error of half storage).  The
+// arithmetic is FP32 in every form.  A half deviation beyond 2^8 * 65504
+// overflows to infinity, which the step reports as non-finite.  esize(s) is the
+// bytes of one stored value of set s; the sets' planes follow each other in the
+// order f, g, h, l, nine planes each.
 struct PopF32 {
-    typedef float T;
-    static constexpr bool kHalf = false;
-    static constexpr int QFL = 9;  // lattice of the phase-field and solute sets
-    __device__ static real dec(T v) { return v; }
-    __device__ static T enc(real d) { return d; }
+    static constexpr bool kHalf = false;  // some set stored in half precision
+    static constexpr int QFL = 9;         // lattice of the phase-field and solute sets
+    __host__ __device__ static constexpr int esize(int) { return 4; }
 };
 struct PopF16 {
-    typedef __half T;
     static constexpr bool kHalf = true;
-    static constexpr int QFL = 9;  // lattice of the phase-field and solute sets
-    __device__ static real dec(T v) { return __half2float(v) * R(1.0 / 256.0); }
-    __device__ static T enc(real d) { return __float2half_rn(d * R(256.0)); }
+    static constexpr int QFL = 9;
+    __host__ __device__ static constexpr int esize(int) { return 2; }
+};
+struct PopF16H {
+    static constexpr bool kHalf = true;
+    static constexpr int QFL = 9;
+    __host__ __device__ static constexpr int esize(int s) { return s == SET_H ? 4 : 2; }
 };
 // FP32 storage with D2Q5 for the phase-field and solute sets (lb_params.lattice_fl
 // = 1): their populations 5 .. 8 are neither read nor written.
 struct PopF32Q5 : PopF32 {
     static constexpr int QFL = 5;
 };
+
+// Element type of set S under storage PS, and the encoding of a deviation.
+template <class PS, int S>
+using SetT = typename std::conditional<PS::esize(S) == 2, __half, float>::type;
+
+__device__ __forceinline__ real dec_val(float v) { return v; }
+__device__ __forceinline__ real dec_val(__half v) { return __half2float(v) * R(1.0 / 256.0); }
+template <class T>
+__device__ __forceinline__ T enc_val(real d);
+template <>
+__device__ __forceinline__ float enc_val<float>(real d) { return d; }
+template <>
+__device__ __forceinline__ __half enc_val<__half>(real d) { return __float2half_rn(d * R(256.0)); }
+
+// Bytes per cell of the planes before set s.
+template <class PS>
+__host__ __device__ constexpr int set_bytes_before(int s)
+{
+    return s <= 0 ? 0 : set_bytes_before<PS>(s - 1) + 9 * PS::esize(s - 1);
+}
+// Bytes per cell of all 36 planes.
+template <class PS>
+__host__ __device__ constexpr int pop_cell_bytes() { return set_bytes_before<PS>(4); }
 
 constexpr int AUX_FS = 0, AUX_Q = 1, AUX_UX = 2, AUX_UY = 3, AUX_PHI = 4, AUX_C = 5, AUX_P = 6, AUX_S = 7, AUX_T = 8;
 constexpr int NAUX = 9;
@@ -155,6 +185,20 @@ template <class T>
 __device__ __forceinline__ T *plane_ptr(T *base, int k, const Consts &K)
 {
     return base + (size_t)(unsigned)K.plane * (unsigned)k;
+}
+
+// Plane i of set S in a population buffer (base: the buffer's first byte).
+template <class PS, int S>
+__device__ __forceinline__ const SetT<PS, S> *set_plane(const float *base, int i, const Consts &K)
+{
+    const char *b = reinterpret_cast<const char *>(base) + (size_t)(unsigned)K.plane * (unsigned)set_bytes_before<PS>(S);
+    return reinterpret_cast<const SetT<PS, S> *>(b) + (size_t)(unsigned)K.plane * (unsigned)i;
+}
+template <class PS, int S>
+__device__ __forceinline__ SetT<PS, S> *set_plane(float *base, int i, const Consts &K)
+{
+    char *b = reinterpret_cast<char *>(base) + (size_t)(unsigned)K.plane * (unsigned)set_bytes_before<PS>(S);
+    return reinterpret_cast<SetT<PS, S> *>(b) + (size_t)(unsigned)K.plane * (unsigned)i;
 }
 
 __device__ __forceinline__ real clamp01(real v) { return fmin(fmax(v, R(0.0)), R(1.0)); }
@@ -296,13 +340,14 @@ __device__ __forceinline__ real forward_sensible(const Consts &K, real T, real c
 // temperature at the foot of the cell on the wall, for all three links that
 // cross it there) is applied in deviation form relative to w rr T_own.
 // pull_src gives the address read, abb_fix the wall rule applied to its value.
-template <int S, int I, bool W, class T>
-__device__ __forceinline__ const T *pull_src(const Consts &K, const T *__restrict__ pin, int x, int y, int cell)
+template <class PS, int S, int I, bool W>
+__device__ __forceinline__ const SetT<PS, S> *pull_src(const Consts &K, const float *__restrict__ pin, int x, int y,
+                                                       int cell)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return plane_ptr(pin, S * 9 + opp(I), K) + cell;
-    return plane_ptr(pin, S * 9 + I, K) + (ys * K.pitch + wrapx(x - cx(I), K.nx));
+    if (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) return set_plane<PS, S>(pin, opp(I), K) + cell;
+    return set_plane<PS, S>(pin, I, K) + (ys * K.pitch + wrapx(x - cx(I), K.nx));
 }
 
 template <int S, int I, bool W>
@@ -320,38 +365,37 @@ __device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, r
     return v;
 }
 
-// Decoded stored value of set S, direction I: the deviation, and for the solute
-// set in half storage the w_I c_ref shift added back.
-template <class PS>
-__device__ __forceinline__ real dec_pop(const Consts &K, int s, int i, typename PS::T v)
+// Decoded stored value of set S, direction i: the deviation, and for the solute
+// set in half storage the w_i c_ref shift added back.
+template <class PS, int S>
+__device__ __forceinline__ real dec_pop(const Consts &K, int i, SetT<PS, S> v)
 {
-    return (PS::kHalf && s == SET_L) ? PS::dec(v) + wgt(i) * K.c_ref : PS::dec(v);
+    return (PS::esize(S) == 2 && S == SET_L) ? dec_val(v) + wgt(i) * K.c_ref : dec_val(v);
 }
 
-template <class PS>
-__device__ __forceinline__ typename PS::T enc_pop(const Consts &K, int s, int i, real v)
+template <class PS, int S>
+__device__ __forceinline__ SetT<PS, S> enc_pop(const Consts &K, int i, real v)
 {
-    return PS::enc((PS::kHalf && s == SET_L) ? v - wgt(i) * K.c_ref : v);
+    return enc_val<SetT<PS, S>>((PS::esize(S) == 2 && S == SET_L) ? v - wgt(i) * K.c_ref : v);
 }
 
-// Store population (set s, direction i) of cell into the output planes.
-template <class PS>
-__device__ __forceinline__ void put_pop(const Consts &K, float *pout, int s, int i, int cell, real v)
+// Store population (set S, direction i) of cell into the output planes.
+template <class PS, int S>
+__device__ __forceinline__ void put_pop(const Consts &K, float *pout, int i, int cell, real v)
 {
-    plane_ptr(reinterpret_cast<typename PS::T *>(pout), s * 9 + i, K)[cell] = enc_pop<PS>(K, s, i, v);
+    set_plane<PS, S>(pout, i, K)[cell] = enc_pop<PS, S>(K, i, v);
 }
 
 template <class PS, int S, int I, bool W>
-__device__ __forceinline__ real pull(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
-                                     real T_own)
+__device__ __forceinline__ real pull(const Consts &K, const float *__restrict__ pin, int x, int y, int cell, real T_own)
 {
-    return abb_fix<S, I, W>(K, dec_pop<PS>(K, S, I, __ldg(pull_src<S, I, W>(K, pin, x, y, cell))), x, y, T_own);
+    return abb_fix<S, I, W>(K, dec_pop<PS, S>(K, I, __ldg(pull_src<PS, S, I, W>(K, pin, x, y, cell))), x, y, T_own);
 }
 
 // W = false: the caller guarantees that no source row lies beyond a wall.
 template <class PS, int S, bool W = true>
-__device__ __forceinline__ void pull9(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
-                                      real v[9], real T_own = R(0.0))
+__device__ __forceinline__ void pull9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell, real v[9],
+                                      real T_own = R(0.0))
 {
     v[0] = pull<PS, S, 0, W>(K, pin, x, y, cell, T_own);
     v[1] = pull<PS, S, 1, W>(K, pin, x, y, cell, T_own);
@@ -464,8 +508,8 @@ struct CellA {
 };
 
 template <class PS, bool W = true>
-__device__ __forceinline__ CellA cell_a(const Consts &K, const typename PS::T *__restrict__ pin,
-                                        const float *__restrict__ ain, int x, int y, int cell)
+__device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict__ pin, const float *__restrict__ ain,
+                                        int x, int y, int cell)
 {
     CellA c;
     real v[9];
@@ -673,12 +717,13 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
     // pairs go two at a time, (1, 2) and (5, 6) -- each two of equal weight -- as
     // packed f32x2 values: "p" holds directions (a, a + 1), "m" their opposites.
     float *__restrict__ pout = B.pout;
-    auto store4 = [&](int set, int a, const pf2 vp, const pf2 vm) {
+    auto store4 = [&](auto set, int a, const pf2 vp, const pf2 vm) {  // set: integral_constant of the set
+        constexpr int S = decltype(set)::value;
         const float2 op = up2(vp), om2 = up2(vm);
-        put_pop<PS>(K, pout, set, a, cell, op.x);
-        put_pop<PS>(K, pout, set, a + 1, cell, op.y);
-        put_pop<PS>(K, pout, set, opp(a), cell, om2.x);
-        put_pop<PS>(K, pout, set, opp(a + 1), cell, om2.y);
+        put_pop<PS, S>(K, pout, a, cell, op.x);
+        put_pop<PS, S>(K, pout, a + 1, cell, op.y);
+        put_pop<PS, S>(K, pout, opp(a), cell, om2.x);
+        put_pop<PS, S>(K, pout, opp(a + 1), cell, om2.y);
     };
     // (c_a . v, c_{a+1} . v)
     auto cdot2 = [](int a, real vx, real vy) {
@@ -697,7 +742,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const real d = dg[0] + wp * dpp;
             const real deq = wp * p_lo + rho * (wgt(0) * (-R(1.5) * uu));
             const real G0 = wgt(0) * (S - R(3.0) * uF);
-            put_pop<PS>(K, pout, SET_G, 0, cell, d - (d - deq) * om_g + src_g * G0);
+            put_pop<PS, SET_G>(K, pout, 0, cell, d - (d - deq) * om_g + src_g * G0);
         }
 #pragma unroll
         for (int q = 0; q < 2; q++) {
@@ -711,7 +756,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const pf2 sh = splat2(w3 * dpp);
             const pf2 dp = add2(pk2(dg[a], dg[a + 1]), sh), dm = add2(pk2(dg[opp(a)], dg[opp(a + 1)]), sh);
             const pf2 sg = splat2(src_g), og = splat2(om_g);
-            store4(SET_G, a, fma2(sg, add2(G_e, G_o), fma2(sub2(add2(eq_e, eq_o), dp), og, dp)),
+            store4(std::integral_constant<int, SET_G>{}, a, fma2(sg, add2(G_e, G_o), fma2(sub2(add2(eq_e, eq_o), dp), og, dp)),
                    fma2(sg, sub2(G_e, G_o), fma2(sub2(sub2(eq_e, eq_o), dm), og, dm)));
         }
     }
@@ -732,7 +777,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         {
             const real d = f[0] + wfl<QF>(0) * (phi_p - phi_st);
             const real deq = wfl<QF>(0) * phi_lo;
-            put_pop<PS>(K, pout, SET_F, 0, cell, d - (d - deq) * om + src * (wfl<QF>(0) * phi * divu));
+            put_pop<PS, SET_F>(K, pout, 0, cell, d - (d - deq) * om + src * (wfl<QF>(0) * phi * divu));
         }
         // lagged phi of the cell that wrote the population pulled into direction i (own cell at a wall)
         auto php = [&](int i) {
@@ -749,7 +794,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const pf2 eq_e = splat2(w * phi_lo), eq_o = mul2(splat2(w3 * phi), cdot2(a, ux, uy));  // f_eq - w phi_st
             const pf2 F_e = splat2(w * phi * divu), F_o = mul2(splat2(w3), cdot2(a, ax, ay));
             const pf2 sf = splat2(src), of = splat2(om);
-            store4(SET_F, a, fma2(sf, add2(F_e, F_o), fma2(sub2(add2(eq_e, eq_o), dp), of, dp)),
+            store4(std::integral_constant<int, SET_F>{}, a, fma2(sf, add2(F_e, F_o), fma2(sub2(add2(eq_e, eq_o), dp), of, dp)),
                    fma2(sf, sub2(F_e, F_o), fma2(sub2(sub2(eq_e, eq_o), dm), of, dm)));
         }
 
@@ -766,7 +811,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
         const real by = (C * uy - C_p * uy_p) + (R(1.0) / R(3.0)) * Ry;
         real l[9];
         A.template pops<SET_L>(K, B.pin, x, y, cell, l, R(0.0));
-        put_pop<PS>(K, pout, SET_L, 0, cell, l[0] - (l[0] - wfl<QF>(0) * C) * om_l);
+        put_pop<PS, SET_L>(K, pout, 0, cell, l[0] - (l[0] - wfl<QF>(0) * C) * om_l);
 #pragma unroll
         for (int q = 0; q < (QF == 9 ? 2 : 1); q++) {
             const int a = q == 0 ? 1 : 5;
@@ -774,7 +819,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const pf2 eq_e = splat2(w * C), eq_o = mul2(splat2(w3 * C), cdot2(a, ux, uy));
             const pf2 sL = mul2(splat2(src_l * w3), cdot2(a, bx, by));  // src_l L_i, odd
             const pf2 lp = pk2(l[a], l[a + 1]), lm = pk2(l[opp(a)], l[opp(a + 1)]), ol = splat2(om_l);
-            store4(SET_L, a, add2(fma2(sub2(add2(eq_e, eq_o), lp), ol, lp), sL),
+            store4(std::integral_constant<int, SET_L>{}, a, add2(fma2(sub2(add2(eq_e, eq_o), lp), ol, lp), sL),
                    sub2(fma2(sub2(sub2(eq_e, eq_o), lm), ol, lm), sL));
         }
     }
@@ -811,7 +856,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             const pf2 hs = mul2(half, add2(dhp, dhm)), ha = mul2(half, sub2(dhp, dhm));
             const pf2 rel_s = mul2(sub2(hs, es), splat2(om_s)), rel_a = mul2(sub2(ha, ea), splat2(om_a));
             const pf2 base = sub2(splat2(src_h * w * Q), rel_s);
-            store4(SET_H, a, add2(sub2(dhp, rel_a), base), add2(add2(dhm, rel_a), base));
+            store4(std::integral_constant<int, SET_H>{}, a, add2(sub2(dhp, rel_a), base), add2(add2(dhm, rel_a), base));
             snz2 = add2(snz2, add2(dhp, dhm));
         }
         const float2 snzv = up2(snz2);
@@ -827,7 +872,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
             // sum_{i>0} h_i - (1 - w_0) rr T = sum_{i>0} dh_i - (1 - w_0) rr T_lo
             const real dev0 = wgt(0) * rcT * R(1.5) * uu - (snz - (R(1.0) - wgt(0)) * rr * T_lo) - R(0.5) * Q_p;
             const real dref = wgt(0) * rr * (T_p - T_st) + K.lat_l * ((chi_p - chi_n) - (fs_p - fs));
-            put_pop<PS>(K, pout, SET_H, 0, cell, h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q);
+            put_pop<PS, SET_H>(K, pout, 0, cell, h[0] + dref - dev0 * om_s + src_h * wgt(0) * Q);
         }
     }
 
@@ -944,12 +989,12 @@ __host__ __device__ constexpr int win_elems()
 template <class PS, int S>
 __device__ __forceinline__ void load9(const Consts &K, const WarpRing &w, int slot, int idx, real v[9])
 {
-    typedef typename PS::T T;
+    typedef SetT<PS, S> T;
     constexpr int E = win_elems<T>();
     const T *p = reinterpret_cast<const T *>(&w.pop[slot][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][0]) + idx;
 #pragma unroll
     for (int i = 0; i < 9; i++)
-        v[i] = ((S == SET_F || S == SET_L) && i >= PS::QFL) ? R(0.0) : dec_pop<PS>(K, S, i, p[i * E - cx(i)]);
+        v[i] = ((S == SET_F || S == SET_L) && i >= PS::QFL) ? R(0.0) : dec_pop<PS, S>(K, i, p[i * E - cx(i)]);
 }
 
 // The enthalpy wall rule on decoded pulls (W only).
@@ -971,7 +1016,7 @@ __device__ __forceinline__ void abb_fix9(const Consts &K, real v[9], int x, int 
 template <class PS, bool W>
 struct RingAcc {
     const WarpRing &w;
-    int lane, off;              // off: window offset of the staged planes
+    int lane, off, off_h;       // window offsets of the staged planes: all but h, and h
     int sl[3], sg[3], sp, sgp;  // loc slots, lag slots (rows y-1, y, y+1), pop / ax slot, gp slot
     // pairs read together (one 64-bit shared load each)
     __device__ float2 lagv(int dy, int dx) const { return w.lag[sg[dy + 1]][lane + 1 + dx]; }
@@ -993,16 +1038,16 @@ struct RingAcc {
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
     {
-        load9<PS, S>(K, w, sp, lane + off, v);
+        load9<PS, S>(K, w, sp, lane + (S == SET_H ? off_h : off), v);
         if (S == SET_H) abb_fix9<W>(K, v, x, y, T_own);
     }
     __device__ void gpops(const Consts &K, real v[9]) const
     {
-        typedef typename PS::T T;
+        typedef SetT<PS, SET_G> T;
         constexpr int E = win_elems<T>();
         const T *p = reinterpret_cast<const T *>(&w.gp[sgp][0][0]) + lane + off;
 #pragma unroll
-        for (int i = 0; i < 9; i++) v[i] = PS::dec(p[i * E - cx(i)]);
+        for (int i = 0; i < 9; i++) v[i] = dec_val(p[i * E - cx(i)]);
     }
     __device__ real aux(int k) const { return w.ax[sp][k][lane + off]; }
 };
@@ -1011,32 +1056,32 @@ struct RingAcc {
 // (E the window slot size; raw stored values, decoded and given the wall rule
 // when read).  FP32 values go by cp.async; half values are loaded and stored.
 template <class PS, int S, bool W>
-__device__ __forceinline__ void stage9(const Consts &K, const typename PS::T *__restrict__ pin, int x, int y, int cell,
-                                       typename PS::T *dst)
+__device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
+                                       SetT<PS, S> *dst)
 {
-    constexpr int E = win_elems<typename PS::T>();
-    if constexpr (!PS::kHalf) {
-        cp_async4(dst + 0 * E - cx(0), pull_src<S, 0, W>(K, pin, x, y, cell));
-        cp_async4(dst + 1 * E - cx(1), pull_src<S, 1, W>(K, pin, x, y, cell));
-        cp_async4(dst + 2 * E - cx(2), pull_src<S, 2, W>(K, pin, x, y, cell));
-        cp_async4(dst + 3 * E - cx(3), pull_src<S, 3, W>(K, pin, x, y, cell));
-        cp_async4(dst + 4 * E - cx(4), pull_src<S, 4, W>(K, pin, x, y, cell));
+    constexpr int E = win_elems<SetT<PS, S>>();
+    if constexpr (PS::esize(S) == 4) {
+        cp_async4(dst + 0 * E - cx(0), pull_src<PS, S, 0, W>(K, pin, x, y, cell));
+        cp_async4(dst + 1 * E - cx(1), pull_src<PS, S, 1, W>(K, pin, x, y, cell));
+        cp_async4(dst + 2 * E - cx(2), pull_src<PS, S, 2, W>(K, pin, x, y, cell));
+        cp_async4(dst + 3 * E - cx(3), pull_src<PS, S, 3, W>(K, pin, x, y, cell));
+        cp_async4(dst + 4 * E - cx(4), pull_src<PS, S, 4, W>(K, pin, x, y, cell));
         if ((S != SET_F && S != SET_L) || PS::QFL == 9) {  // D2Q5 f and l: directions 0 .. 4 only
-            cp_async4(dst + 5 * E - cx(5), pull_src<S, 5, W>(K, pin, x, y, cell));
-            cp_async4(dst + 6 * E - cx(6), pull_src<S, 6, W>(K, pin, x, y, cell));
-            cp_async4(dst + 7 * E - cx(7), pull_src<S, 7, W>(K, pin, x, y, cell));
-            cp_async4(dst + 8 * E - cx(8), pull_src<S, 8, W>(K, pin, x, y, cell));
+            cp_async4(dst + 5 * E - cx(5), pull_src<PS, S, 5, W>(K, pin, x, y, cell));
+            cp_async4(dst + 6 * E - cx(6), pull_src<PS, S, 6, W>(K, pin, x, y, cell));
+            cp_async4(dst + 7 * E - cx(7), pull_src<PS, S, 7, W>(K, pin, x, y, cell));
+            cp_async4(dst + 8 * E - cx(8), pull_src<PS, S, 8, W>(K, pin, x, y, cell));
         }
     } else {
-        dst[0 * E - cx(0)] = __ldg(pull_src<S, 0, W>(K, pin, x, y, cell));
-        dst[1 * E - cx(1)] = __ldg(pull_src<S, 1, W>(K, pin, x, y, cell));
-        dst[2 * E - cx(2)] = __ldg(pull_src<S, 2, W>(K, pin, x, y, cell));
-        dst[3 * E - cx(3)] = __ldg(pull_src<S, 3, W>(K, pin, x, y, cell));
-        dst[4 * E - cx(4)] = __ldg(pull_src<S, 4, W>(K, pin, x, y, cell));
-        dst[5 * E - cx(5)] = __ldg(pull_src<S, 5, W>(K, pin, x, y, cell));
-        dst[6 * E - cx(6)] = __ldg(pull_src<S, 6, W>(K, pin, x, y, cell));
-        dst[7 * E - cx(7)] = __ldg(pull_src<S, 7, W>(K, pin, x, y, cell));
-        dst[8 * E - cx(8)] = __ldg(pull_src<S, 8, W>(K, pin, x, y, cell));
+        dst[0 * E - cx(0)] = __ldg(pull_src<PS, S, 0, W>(K, pin, x, y, cell));
+        dst[1 * E - cx(1)] = __ldg(pull_src<PS, S, 1, W>(K, pin, x, y, cell));
+        dst[2 * E - cx(2)] = __ldg(pull_src<PS, S, 2, W>(K, pin, x, y, cell));
+        dst[3 * E - cx(3)] = __ldg(pull_src<PS, S, 3, W>(K, pin, x, y, cell));
+        dst[4 * E - cx(4)] = __ldg(pull_src<PS, S, 4, W>(K, pin, x, y, cell));
+        dst[5 * E - cx(5)] = __ldg(pull_src<PS, S, 5, W>(K, pin, x, y, cell));
+        dst[6 * E - cx(6)] = __ldg(pull_src<PS, S, 6, W>(K, pin, x, y, cell));
+        dst[7 * E - cx(7)] = __ldg(pull_src<PS, S, 7, W>(K, pin, x, y, cell));
+        dst[8 * E - cx(8)] = __ldg(pull_src<PS, S, 8, W>(K, pin, x, y, cell));
     }
 }
 
@@ -1101,15 +1146,21 @@ template <int MODE, bool WALLS, class PS>
 __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing &w, int lane, int x0, int ys, int ye,
                                            double acc[NRED])
 {
-    typedef typename PS::T T;
+    typedef SetT<PS, SET_F> TF;  // f and l
+    typedef SetT<PS, SET_G> TG;
+    typedef SetT<PS, SET_H> TH;
     constexpr bool PB = MODE != MODE_REDUCE;  // phase B follows phase A
-    constexpr int E = win_elems<T>();         // window slot size in T
-    constexpr int CH = 16 / (int)sizeof(T);   // elements of a 16-byte chunk
-    constexpr int PLEN = PS::kHalf ? 48 : 40; // staged columns of a population window
+    constexpr bool HALF = PS::kHalf;          // f, g and l in half precision
+    constexpr bool HMIX = HALF && PS::esize(SET_H) == 4;  // ... and h in FP32
+    constexpr int EF = win_elems<TF>();       // window slot size in elements of f / l, g, h
+    constexpr int EG = win_elems<TG>();
+    constexpr int EH = win_elems<TH>();
+    constexpr int CH = HALF ? 8 : 4;          // elements of a 16-byte chunk of f, g and l
+    constexpr int PLEN = HALF ? 48 : 40;      // staged columns of a population window
     const int ex = x0 - 1 + lane;
     const int xg = ((ex % K.nx) + K.nx) % K.nx;
     const bool b_lane = lane >= 1 && lane <= LB_TX && ex < K.nx;
-    const T *__restrict__ pin = reinterpret_cast<const T *>(B.pin);
+    const float *__restrict__ pin = B.pin;
     const float *__restrict__ ain = B.ain;
     const int xa = (((x0 - 2 + lane) % K.nx) + K.nx) % K.nx;
     const int xb = (((x0 + 30 + (lane & 1)) % K.nx) + K.nx) % K.nx;
@@ -1118,9 +1169,11 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     // 16-byte chunks, a group of lanes per window; the wall bands and the strips
     // at the x ends copy one value per lane (pull rules, periodic wrap) into the
     // same layout.
-    const int x_lo = (x0 - 2) & ~(CH - 1);
-    const bool win = !WALLS && x0 >= 2 && x_lo + PLEN <= K.nx && x_lo + WW <= K.nx;
+    const int x_lo = (x0 - 2) & ~(CH - 1);           // windows of f, g, l and the lagged planes
+    const int x_lo_h = HMIX ? ((x0 - 2) & ~3) : x_lo;  // windows of h
+    const bool win = !WALLS && x0 >= 2 && x_lo + PLEN <= K.nx && x_lo + WW <= K.nx && x_lo_h + WW <= K.nx;
     const int off = win ? x0 - 1 - x_lo : 4;
+    const int off_h = win ? x0 - 1 - x_lo_h : 4;
     const int wg = lane / 10, wpart = lane - 10 * wg;  // float windows: 10 chunks, 3 windows per copy
     const int wcol = x_lo + 4 * wpart;
     const int hg = lane / 6, hpart = lane - 6 * hg;    // half windows: 6 chunks, 5 windows per copy
@@ -1162,38 +1215,60 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     auto stage_a = [&](int y, int s3) {  // s3 = y mod 3
         if (WALLS && (y < 0 || y >= K.ny)) return;
         const int cell = y * K.pitch + xg;
-        T *pw = reinterpret_cast<T *>(&w.pop[s3][0][0]);  // window 0 of the slot
         if (win) {
-            if constexpr (!PS::kHalf) {
+            if constexpr (!HALF) {
                 if (wg < 3) {
                     // group wg: set f, h or l; one window per direction, rows y - c_iy
-                    const T *src = plane_ptr(pin, wg == 0 ? SET_F * 9 : (wg == 1 ? SET_H * 9 : SET_L * 9), K) + wcol;
-                    T *dst = pw + 9 * wg * E + 4 * wpart;
+                    const float *src = (wg == 0 ? set_plane<PS, SET_F>(pin, 0, K)
+                                                : (wg == 1 ? set_plane<PS, SET_H>(pin, 0, K) : set_plane<PS, SET_L>(pin, 0, K))) +
+                                       wcol;
+                    float *dst = &w.pop[s3][9 * wg][0] + 4 * wpart;
                     const int nq = wg == 1 ? 9 : PS::QFL;  // D2Q5 f and l: directions 0 .. 4
 #pragma unroll
                     for (int i = 0; i < 9; i++)
-                        if (i < nq) cp_async16(dst + i * E, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
+                        if (i < nq) cp_async16(dst + i * EF, plane_ptr(src, i, K) + (y - cy(i)) * K.pitch);
                 }
             } else {
+                // half windows: f and l (and h unless it is FP32), six 16-byte chunks each
+                constexpr int NHW = HMIX ? 18 : 27;
                 if (hg < 5) {
 #pragma unroll
-                    for (int q = 0; q < 6; q++) {
-                        const int wi = 5 * q + hg;  // window: f 0..8, h 9..17, l 18..26
-                        if (wi < 27) {
-                            const int set = wi / 9, i = wi - 9 * set;
-                            const int plane = (set == 0 ? SET_F * 9 : (set == 1 ? SET_H * 9 : SET_L * 9)) + i;
-                            cp_async16(pw + wi * E + CH * hpart,
-                                       plane_ptr(pin, plane, K) + ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
+                    for (int q = 0; q < (NHW + 4) / 5; q++) {
+                        const int wi = 5 * q + hg;
+                        if (wi < NHW) {
+                            // HMIX: f 0..8, l 9..17 (ring windows 0..8, 18..26); else f, h, l = ring windows
+                            const int set = HMIX ? (wi < 9 ? SET_F : SET_L) : (wi < 9 ? SET_F : (wi < 18 ? SET_H : SET_L));
+                            const int i = wi % 9;
+                            const int slot = HMIX ? (wi < 9 ? wi : wi + 9) : wi;
+                            const int before = set == SET_F ? set_bytes_before<PS>(SET_F)
+                                                             : (set == SET_H ? set_bytes_before<PS>(SET_H)
+                                                                             : set_bytes_before<PS>(SET_L));
+                            const __half *src = reinterpret_cast<const __half *>(
+                                                    reinterpret_cast<const char *>(pin) +
+                                                    (size_t)(unsigned)K.plane * (unsigned)(before + 2 * i)) +
+                                                ((y - cy(i)) * K.pitch + x_lo + CH * hpart);
+                            cp_async16(reinterpret_cast<__half *>(&w.pop[s3][slot][0]) + CH * hpart, src);
+                        }
+                    }
+                }
+                if constexpr (HMIX) {
+                    // FP32 windows of h: ten 16-byte chunks each, three windows per copy
+                    if (wg < 3) {
+#pragma unroll
+                        for (int q = 0; q < 3; q++) {
+                            const int i = 3 * q + wg;
+                            const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
+                            cp_async16(&w.pop[s3][9 + i][0] + 4 * wpart,
+                                       set_plane<PS, SET_H>(pin, i, K) + ((y - cyi) * K.pitch + x_lo_h + 4 * wpart));
                         }
                     }
                 }
             }
             stage_ax_win(y, s3);
         } else {
-            T *pp = pw + lane + off;
-            stage9<PS, SET_F, WALLS>(K, pin, xg, y, cell, pp);
-            stage9<PS, SET_H, WALLS>(K, pin, xg, y, cell, pp + 9 * E);
-            stage9<PS, SET_L, WALLS>(K, pin, xg, y, cell, pp + 18 * E);
+            stage9<PS, SET_F, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TF *>(&w.pop[s3][0][0]) + lane + off);
+            stage9<PS, SET_H, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TH *>(&w.pop[s3][9][0]) + lane + off_h);
+            stage9<PS, SET_L, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TF *>(&w.pop[s3][18][0]) + lane + off);
             float *pa = &w.ax[s3][0][lane + off];
             cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
             cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
@@ -1213,31 +1288,34 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     // pulled g of row y, for its phase B one iteration later
     auto stage_g = [&](int y) {
         if (!PB || y < ys || y >= ye) return;
-        T *gw = reinterpret_cast<T *>(&w.gp[y & 1][0][0]);
         if (win) {
-            if constexpr (!PS::kHalf) {
+            if constexpr (!HALF) {
                 if (wg < 3) {
-                    const T *src = plane_ptr(pin, SET_G * 9, K) + wcol;
+                    const float *src = set_plane<PS, SET_G>(pin, 0, K) + wcol;
+                    float *gw = &w.gp[y & 1][0][0];
 #pragma unroll
                     for (int q = 0; q < 3; q++) {
                         const int i = 3 * q + wg;  // direction of this group's window
                         const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
-                        cp_async16(gw + i * E + 4 * wpart, plane_ptr(src, i, K) + (y - cyi) * K.pitch);
+                        cp_async16(gw + i * EG + 4 * wpart, plane_ptr(src, i, K) + (y - cyi) * K.pitch);
                     }
                 }
             } else {
                 if (hg < 5) {
+                    __half *gw = reinterpret_cast<__half *>(&w.gp[y & 1][0][0]);
 #pragma unroll
                     for (int q = 0; q < 2; q++) {
                         const int i = 5 * q + hg;
                         if (i < 9)
-                            cp_async16(gw + i * E + CH * hpart,
-                                       plane_ptr(pin, SET_G * 9 + i, K) + ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
+                            cp_async16(gw + i * EG + CH * hpart,
+                                       reinterpret_cast<const __half *>(set_plane<PS, SET_G>(pin, i, K)) +
+                                           ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
                     }
                 }
             }
         } else if (b_lane) {
-            stage9<PS, SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex, gw + lane + off);
+            stage9<PS, SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex,
+                                     reinterpret_cast<TG *>(&w.gp[y & 1][0][0]) + lane + off);
         }
     };
 
@@ -1271,7 +1349,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             lag_dev_sums<WALLS, PS::QFL>(K, w, lane, ya, phi_p, T_p, dph, dtt);
             load9<PS, SET_F>(K, w, s3, lane + off, v);
             const real delta = sum9(v) + dph;
-            load9<PS, SET_H>(K, w, s3, lane + off, v);
+            load9<PS, SET_H>(K, w, s3, lane + off_h, v);
             abb_fix9<WALLS>(K, v, xg, ya, T_p);
             const real Q_p = w.ax[s3][AX_Q][lane + off];
             const real ed = sum9(v) + K.rr * dtt + R(0.5) * Q_p;
@@ -1303,7 +1381,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
         if (PB && yb >= ys && yb < ye && b_lane) {
-            const RingAcc<PS, WALLS> A{w, lane, off, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
+            const RingAcc<PS, WALLS> A{w, lane, off, off_h, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
                                        {(yb - 1) & 7, yb & 7, (yb + 1) & 7}, s3p, yb & 1};
             phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
@@ -1501,6 +1579,38 @@ __global__ void lb_init_eq_kernel(const Consts K, const float *__restrict__ phi0
 // Inverse streaming: the stored state is post-collision, so the initial
 // post-streaming populations `eq` are placed where the next pull finds them,
 // f, g and h as deviations from the references of the cell that holds them.
+template <class PS, int S>
+__device__ __forceinline__ void unstream_set(const Consts &K, const float *__restrict__ eq,
+                                             const float *__restrict__ aux, float *__restrict__ pops, int x, int y,
+                                             long long cell, real phi_here, real T_here)
+{
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const int yt = y + cy(i);
+        real v;
+        if (yt < 0 || yt >= K.ny) {
+            v = eq[(long long)(S * 9 + opp(i)) * K.plane + cell];
+            if (S == SET_H) {
+                const bool bottom = yt < 0;
+                if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
+                    // stored h_i(x) = 2 w rr T_w - h_eq_opp(x), as a deviation from w rr T(x)
+                    real Tw = bottom ? wall_T_bottom(K, (real)x) : K.T_top;
+                    v = R(2.0) * wgt(i) * K.rr * (Tw - T_here) - v;
+                }
+            }
+        } else {
+            const int xt = wrapx(x + cx(i), K.nx);
+            const long long ct = (long long)yt * K.pitch + xt;
+            v = eq[(long long)(S * 9 + i) * K.plane + ct];
+            if (S == SET_H && i != 0) v += wgt(i) * K.rr * ((real)aux[AUX_T * K.plane + ct] - T_here);
+            if (S == SET_G && i != 0)
+                v += R(3.0) * wgt(i) * ((real)aux[AUX_P * K.plane + ct] - (real)aux[AUX_P * K.plane + cell]);
+        }
+        if (S == SET_F) v -= wfl_rt(K.qfl, i) * phi_here;
+        set_plane<PS, S>(pops, i, K)[cell] = enc_pop<PS, S>(K, i, v);
+    }
+}
+
 template <class PS>
 __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict__ eq, const float *__restrict__ aux,
                                         float *__restrict__ pops)
@@ -1511,34 +1621,10 @@ __global__ void lb_init_unstream_kernel(const Consts K, const float *__restrict_
         const long long cell = (long long)y * K.pitch + x;
         const real phi_here = aux[AUX_PHI * K.plane + cell];
         const real T_here = aux[AUX_T * K.plane + cell];
-#pragma unroll
-        for (int s = 0; s < 4; s++) {
-#pragma unroll
-            for (int i = 0; i < 9; i++) {
-                const int yt = y + cy(i);
-                real v;
-                if (yt < 0 || yt >= K.ny) {
-                    v = eq[(long long)(s * 9 + opp(i)) * K.plane + cell];
-                    if (s == SET_H) {
-                        const bool bottom = yt < 0;
-                        if ((bottom ? K.bc_bottom : K.bc_top) == WALL_DIRICHLET) {
-                            // stored h_i(x) = 2 w rr T_w - h_eq_opp(x), as a deviation from w rr T(x)
-                            real Tw = bottom ? wall_T_bottom(K, (real)x) : K.T_top;
-                            v = R(2.0) * wgt(i) * K.rr * (Tw - T_here) - v;
-                        }
-                    }
-                } else {
-                    const int xt = wrapx(x + cx(i), K.nx);
-                    const long long ct = (long long)yt * K.pitch + xt;
-                    v = eq[(long long)(s * 9 + i) * K.plane + ct];
-                    if (s == SET_H && i != 0) v += wgt(i) * K.rr * ((real)aux[AUX_T * K.plane + ct] - T_here);
-                    if (s == SET_G && i != 0)
-                        v += R(3.0) * wgt(i) * ((real)aux[AUX_P * K.plane + ct] - (real)aux[AUX_P * K.plane + cell]);
-                }
-                if (s == SET_F) v -= wfl_rt(K.qfl, i) * phi_here;
-                reinterpret_cast<typename PS::T *>(pops)[(long long)(s * 9 + i) * K.plane + cell] = enc_pop<PS>(K, s, i, v);
-            }
-        }
+        unstream_set<PS, SET_F>(K, eq, aux, pops, x, y, cell, phi_here, T_here);
+        unstream_set<PS, SET_G>(K, eq, aux, pops, x, y, cell, phi_here, T_here);
+        unstream_set<PS, SET_H>(K, eq, aux, pops, x, y, cell, phi_here, T_here);
+        unstream_set<PS, SET_L>(K, eq, aux, pops, x, y, cell, phi_here, T_here);
     }
 }
 
@@ -1571,50 +1657,63 @@ __global__ void __launch_bounds__(RED_THREADS) lb_reduce_final_kernel(const doub
 
 // ---------------------------------------------------------------------------------------
 // Halo messages of a slab (y-slab decomposition).  A message holds, for every
-// population plane (storage type, elem bytes) and then every lagged plane
-// (FP32), two lattice rows of nx values: rows [r0, r0 + 2) of the buffer,
-// plane after plane, rows consecutive.  pack copies them out of `state`
-// (populations then lagged planes), unpack writes them into it.
+// population plane (in its storage type) and then every lagged plane (FP32),
+// two lattice rows of nx values: rows [r0, r0 + 2) of the buffer, plane after
+// plane, rows consecutive.  pack copies them out of the state (populations
+// then lagged planes), unpack writes them into it.
 // ---------------------------------------------------------------------------------------
-__global__ void lb_halo_pack_kernel(const Consts K, const unsigned char *__restrict__ pops,
-                                    const float *__restrict__ aux, int elem, int npop, int r0,
-                                    unsigned char *__restrict__ msg)
+template <class PS>
+__device__ __forceinline__ void halo_plane(int k, int &esz, long long &byte_off, const Consts &K)
 {
-    const long long per_plane = 2LL * K.nx;
-    const long long pop_vals = per_plane * npop, total = pop_vals + per_plane * NAUX;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
-        const bool is_pop = k < pop_vals;
-        const long long kk = is_pop ? k : k - pop_vals;
-        const int plane = (int)(kk / per_plane), r = (int)((kk % per_plane) / K.nx), x = (int)(kk % K.nx);
-        const long long src = (long long)plane * K.plane + (long long)(r0 + r) * K.pitch + x;
-        if (is_pop) {
-            if (elem == 4)
-                reinterpret_cast<float *>(msg)[k] = reinterpret_cast<const float *>(pops)[src];
-            else
-                reinterpret_cast<unsigned short *>(msg)[k] = reinterpret_cast<const unsigned short *>(pops)[src];
-        } else {
-            reinterpret_cast<float *>(msg + pop_vals * elem)[kk] = aux[src];
-        }
-    }
+    // population plane k = 9 s + i: element bytes and byte offset in the buffer
+    const int s = k / 9, i = k - 9 * s;
+    esz = PS::esize(s);
+    const int before = s == 0 ? 0 : (s == 1 ? set_bytes_before<PS>(1) : (s == 2 ? set_bytes_before<PS>(2)
+                                                                                : set_bytes_before<PS>(3)));
+    byte_off = (long long)K.plane * (before + esz * i);
 }
 
-__global__ void lb_halo_unpack_kernel(const Consts K, unsigned char *__restrict__ pops, float *__restrict__ aux,
-                                      int elem, int npop, int r0, const unsigned char *__restrict__ msg)
+// bytes of one halo message: 36 population planes and NAUX lagged planes, 2 rows of nx
+template <class PS>
+__host__ __device__ constexpr long long halo_message_bytes(int nx)
+{
+    return 2LL * nx * (pop_cell_bytes<PS>() + 4 * NAUX);
+}
+
+template <class PS, bool PACK>
+__global__ void lb_halo_kernel(const Consts K, unsigned char *__restrict__ pops, float *__restrict__ aux, int r0,
+                               unsigned char *__restrict__ msg)
 {
     const long long per_plane = 2LL * K.nx;
-    const long long pop_vals = per_plane * npop, total = pop_vals + per_plane * NAUX;
+    const long long total = per_plane * (36 + NAUX);
+    const long long pop_bytes = per_plane * pop_cell_bytes<PS>();
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
-        const bool is_pop = k < pop_vals;
-        const long long kk = is_pop ? k : k - pop_vals;
-        const int plane = (int)(kk / per_plane), r = (int)((kk % per_plane) / K.nx), x = (int)(kk % K.nx);
-        const long long dst = (long long)plane * K.plane + (long long)(r0 + r) * K.pitch + x;
-        if (is_pop) {
-            if (elem == 4)
-                reinterpret_cast<float *>(pops)[dst] = reinterpret_cast<const float *>(msg)[k];
-            else
-                reinterpret_cast<unsigned short *>(pops)[dst] = reinterpret_cast<const unsigned short *>(msg)[k];
+        const int plane = (int)(k / per_plane);
+        const long long in = k - (long long)plane * per_plane;
+        const int r = (int)(in / K.nx), x = (int)(in % K.nx);
+        const long long at = (long long)(r0 + r) * K.pitch + x;  // element index within a plane
+        if (plane < 36) {
+            int esz;
+            long long off;
+            halo_plane<PS>(plane, esz, off, K);
+            // message offset: the planes before, each per_plane values of their own size
+            const int s = plane / 9, i = plane - 9 * s;
+            const long long m = per_plane * ((s == 0 ? 0 : (s == 1 ? set_bytes_before<PS>(1)
+                                                     : (s == 2 ? set_bytes_before<PS>(2) : set_bytes_before<PS>(3)))) +
+                                             esz * i) + in * esz;
+            unsigned char *g = pops + off + at * esz;
+            if (esz == 4) {
+                if (PACK) *reinterpret_cast<float *>(msg + m) = *reinterpret_cast<const float *>(g);
+                else *reinterpret_cast<float *>(g) = *reinterpret_cast<const float *>(msg + m);
+            } else {
+                if (PACK) *reinterpret_cast<unsigned short *>(msg + m) = *reinterpret_cast<const unsigned short *>(g);
+                else *reinterpret_cast<unsigned short *>(g) = *reinterpret_cast<const unsigned short *>(msg + m);
+            }
         } else {
-            aux[dst] = reinterpret_cast<const float *>(msg + pop_vals * elem)[kk];
+            float *a = aux + (long long)(plane - 36) * K.plane + at;
+            float *mm = reinterpret_cast<float *>(msg + pop_bytes) + (long long)(plane - 36) * per_plane + in;
+            if (PACK) *mm = *a;
+            else *a = *mm;
         }
     }
 }

@@ -16,7 +16,7 @@ import numpy as np
 from . import _build
 
 LB_OK, LB_ERR_INVALID_ARG, LB_ERR_CUDA, LB_ERR_OOM, LB_ERR_UNSTABLE = 0, 1, 2, 3, 4
-LB_STORAGE_F32, LB_STORAGE_F16 = 0, 1      # lb_params.pop_storage
+LB_STORAGE_F32, LB_STORAGE_F16, LB_STORAGE_F16_H32 = 0, 1, 2  # lb_params.pop_storage
 LB_LATTICE_D2Q9, LB_LATTICE_D2Q5 = 0, 1    # lb_params.lattice_fl
 FIELD_NAMES = ("phi", "T", "fs", "C", "ux", "uy", "p")
 REDUCE_NAMES = ("sum_phi", "sum_rhoH", "sum_C", "sum_fs", "sum_chi", "front", "Vs", "Vsl")

@@ -81,11 +81,12 @@ def test_d2q5_edge_shapes(oracle_mod, shape):
     _check(got, want, Q.TOL_Q5, "D2Q5 %s" % (shape,))
 
 
+@pytest.mark.parametrize("form", H.HALF_FORMS)
 @pytest.mark.parametrize("shape", P.EDGE_SHAPES)
-def test_half_storage_edge_shapes(oracle_mod, shape):
+def test_half_storage_edge_shapes(oracle_mod, shape, form):
     w = P.edge_workload(*shape)
-    got, red, want, wred = P._run_pair(oracle_mod, w, 30, params=dict(w["params"], pop_storage=H.F16))
-    _check(got, want, H.FIELD_TOL, "FP16 %s" % (shape,))
+    got, red, want, wred = P._run_pair(oracle_mod, w, 30, params=dict(w["params"], pop_storage=form))
+    _check(got, want, H.FIELD_TOL, "half storage %d %s" % (form, shape))
 
 
 def test_batch_of_wetting_bridges_equals_lone_lattices():

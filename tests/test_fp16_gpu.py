@@ -1,4 +1,6 @@
-"""Half-precision population storage (lb_params.pop_storage = LB_STORAGE_F16).
+"""Half-precision population storage: every set in FP16 (lb_params.pop_storage
+= LB_STORAGE_F16), or f, g and l in FP16 with the enthalpy set h in FP32
+(LB_STORAGE_F16_H32).
 
 The populations are stored as scaled FP16 deviations and the arithmetic stays
 FP32, so the results differ from the oracle by the rounding of every stored
@@ -18,6 +20,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 F16 = 1
+F16_H32 = 2
+HALF_FORMS = [F16, F16_H32]
 FIELD_TOL = 6e-3  # measured at most 2.1e-3 (pressure, heated channel) after 100 steps
 
 
@@ -30,32 +34,35 @@ def _built():
     lbfreeze.load()
 
 
-def _half(w):
-    return dict(w, params=dict(w["params"], pop_storage=F16))
+def _half(w, form=F16):
+    return dict(w, params=dict(w["params"], pop_storage=form))
 
 
+@pytest.mark.parametrize("form", HALF_FORMS)
 @pytest.mark.parametrize("name,make,steps", P.CASES[:1] + P.CASES[3:], ids=[c[0] for c in P.CASES[:1] + P.CASES[3:]])
-def test_fp16_fields_against_oracle(oracle_mod, name, make, steps):
+def test_fp16_fields_against_oracle(oracle_mod, name, make, steps, form):
     w = make()
-    got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=_half(w)["params"])
+    got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=_half(w, form)["params"])
     errs = P._rel_errors(got, want)
     assert all(v <= FIELD_TOL for v in errs.values()), (name, errs)
     assert all(np.isfinite(got[k]).all() for k in P.FIELDS)
 
 
 
-def test_fp16_full_size_bench_workload(oracle_mod):
+@pytest.mark.parametrize("form", HALF_FORMS)
+def test_fp16_full_size_bench_workload(oracle_mod, form):
     """The 4096 x 4096 impurity front in half storage, as the benchmark's
-    half-storage leg runs it, a few steps against the oracle on every cell."""
+    half-storage legs run it, a few steps against the oracle on every cell."""
     w = W.impurity_front(nx=4096, ny=4096)
-    got, red, want, wred = P._run_pair(oracle_mod, w, 3, params=_half(w)["params"])
+    got, red, want, wred = P._run_pair(oracle_mod, w, 3, params=_half(w, form)["params"])
     errs = P._rel_errors(got, want)
     assert all(v <= FIELD_TOL for v in errs.values()), errs
 
-def test_fp16_freezing_time(oracle_mod):
+@pytest.mark.parametrize("form", HALF_FORMS)
+def test_fp16_freezing_time(oracle_mod, form):
     w = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.2)
     f32 = P._f32(w)
-    s = lbfreeze.Solver(w["grid"], _half(w)["params"], f32)
+    s = lbfreeze.Solver(w["grid"], _half(w, form)["params"], f32)
     tf_gpu, _ = P._freezing_time(s.step, s.reduce, 5000)
     s.close()
     o = oracle_mod.Oracle(w["grid"], w["params"], {k: v.astype(np.float64) for k, v in f32.items()})
@@ -63,10 +70,11 @@ def test_fp16_freezing_time(oracle_mod):
     assert abs(tf_gpu - tf_ora) <= 1e-3 * tf_ora, (tf_gpu, tf_ora)
 
 
-def test_fp16_front_height_end_of_run(oracle_mod):
+@pytest.mark.parametrize("form", HALF_FORMS)
+def test_fp16_front_height_end_of_run(oracle_mod, form):
     w = W.stefan_layer(nx=64, ny=256)
     f32 = P._f32(w)
-    s = lbfreeze.Solver(w["grid"], _half(w)["params"], f32)
+    s = lbfreeze.Solver(w["grid"], _half(w, form)["params"], f32)
     s.step(w["steps"])
     red = s.reduce()
     s.close()
@@ -76,8 +84,9 @@ def test_fp16_front_height_end_of_run(oracle_mod):
     assert abs(red[3] - wred[3]) <= 1e-3 * wred[3], (red[3] / 64, wred[3] / 64)
 
 
-def test_fp16_checkpoint_resume_bitwise(tmp_path):
-    w = _half(W.parity_droplet(nx=64, ny=48))
+@pytest.mark.parametrize("form", HALF_FORMS)
+def test_fp16_checkpoint_resume_bitwise(tmp_path, form):
+    w = _half(W.parity_droplet(nx=64, ny=48), form)
     f32 = P._f32(w)
     a = lbfreeze.Solver(w["grid"], w["params"], f32)
     a.step(30)
@@ -95,9 +104,10 @@ def test_fp16_checkpoint_resume_bitwise(tmp_path):
         c.load_state(str(tmp_path / "ck16.bin"))  # written with the other storage
 
 
-def test_fp16_batch_matches_single_and_rejects_mixed_storage():
-    ws = [_half(W.parity_droplet(nx=40, ny=33, seed=1)), _half(W.impurity_front(nx=128, ny=100, radius=15.0)),
-          _half(W.sessile_droplet(nx=150, ny=130, radius=40.0, rho_g=0.1, ste=0.3, c0=0.07))]
+@pytest.mark.parametrize("form", HALF_FORMS)
+def test_fp16_batch_matches_single_and_rejects_mixed_storage(form):
+    ws = [_half(W.parity_droplet(nx=40, ny=33, seed=1), form), _half(W.impurity_front(nx=128, ny=100, radius=15.0), form),
+          _half(W.sessile_droplet(nx=150, ny=130, radius=40.0, rho_g=0.1, ste=0.3, c0=0.07), form)]
     for w in ws:
         w["fields"] = P._f32(w)
     b = lbfreeze.Batch(ws)
@@ -111,7 +121,22 @@ def test_fp16_batch_matches_single_and_rejects_mixed_storage():
         for k in P.FIELDS:
             assert np.array_equal(got[k], want[k]), (i, k)
     b.close()
-    mixed = [ws[0], dict(ws[1], params=dict(ws[1]["params"], pop_storage=0))]
+    mixed = [ws[0], dict(ws[1], params=dict(ws[1]["params"], pop_storage=3 - form))]
     with pytest.raises(lbfreeze.LbError) as e:
         lbfreeze.Batch(mixed)
     assert "pop_storage" in str(e.value)
+
+
+def test_half_forms_with_fp32_enthalpy_store_fewer_bytes():
+    """Device bytes of the population buffers: FP32 144, FP16 72, FP16 with an
+    FP32 enthalpy set 90 bytes per cell and buffer."""
+    w = W.parity_droplet(nx=64, ny=48)
+    f32 = P._f32(w)
+    sizes = {}
+    for form in (0, F16, F16_H32):
+        s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=form), f32)
+        sizes[form] = s.device_bytes
+        s.close()
+    plane = 64 * 48  # pitch 64
+    assert sizes[0] - sizes[F16] == 2 * (144 - 72) * plane
+    assert sizes[0] - sizes[F16_H32] == 2 * (144 - 90) * plane

@@ -82,6 +82,8 @@ CASES = [
     ("droplet_128x96_mdot", lambda: W.parity_droplet(nx=128, ny=96), [0, 48, 96], dict(divu_mode=0)),
     ("droplet_97x71_fp16", lambda: W.parity_droplet(nx=97, ny=71, seed=3), [0, 30, 71],
      dict(pop_storage=lbfreeze.LB_STORAGE_F16)),
+    ("droplet_97x71_fp16_h32", lambda: W.parity_droplet(nx=97, ny=71, seed=3), [0, 37, 71],
+     dict(pop_storage=lbfreeze.LB_STORAGE_F16_H32)),
     ("droplet_97x71_d2q5", lambda: W.parity_droplet(nx=97, ny=71, seed=3), [0, 4, 67, 71],
      dict(lattice_fl=lbfreeze.LB_LATTICE_D2Q5)),
     ("impurity_front_160x128_4slabs", lambda: W.impurity_front(nx=160, ny=128, radius=20.0), [0, 32, 64, 96, 128],

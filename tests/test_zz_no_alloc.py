@@ -52,8 +52,9 @@ def _reduce(L, solver):
     dict(),
     dict(divu_mode=0),
     dict(pop_storage=lbfreeze.LB_STORAGE_F16),
+    dict(pop_storage=lbfreeze.LB_STORAGE_F16_H32),
     dict(lattice_fl=lbfreeze.LB_LATTICE_D2Q5),
-], ids=["fp32", "fp32_divu_mdot", "fp16", "d2q5"])
+], ids=["fp32", "fp32_divu_mdot", "fp16", "fp16_h32", "d2q5"])
 def test_noalloc_matches_reduce_on_consecutive_calls(lib, options):
     """Every storage form and lattice of the step (FP32 and half-precision
     populations, D2Q9 or D2Q5 phase-field and solute sets) and both readings
