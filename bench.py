@@ -209,13 +209,16 @@ def run_reference(args):
 
 BYTES_PER_UPDATE_F16 = 208  # 36 populations read + written as FP16, 8 lagged FP32 fields read + written
 BYTES_PER_UPDATE_Q5 = 288   # D2Q5 f and l: 28 populations + 8 lagged fields, FP32, read + written
+BYTES_PER_UPDATE_F16H = 244  # 27 FP16 populations (f, g, l) + 9 FP32 (h) + 8 lagged FP32 fields, read + written
 # with the step's ninth lagged field (the deviation reference) 216 and 296 bytes are moved
 
 
-def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
-    """The same lattice with half-precision population storage: MLUPS, and
-    achieved bandwidth against its own algorithmic bytes (208 B per update)."""
-    s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=1), f32, stream=stream)
+def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs, form=1):
+    """The same lattice with half-precision population storage (form 1: every
+    set; form 2: f, g, l in half, h in FP32): MLUPS, and achieved bandwidth
+    against its own algorithmic bytes (208 or 244 B per update)."""
+    nbytes = BYTES_PER_UPDATE_F16 if form == 1 else BYTES_PER_UPDATE_F16H
+    s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=form), f32, stream=stream)
     s.step(args.warmup)
     stream.synchronize()
     if dist is not None:
@@ -231,12 +234,13 @@ def _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
     s.reduce()  # raises if the half-precision run went non-finite
     s.close()
     mlups = ws * cells * args.steps / (ms * 1e-3) / 1e6
-    gbs = BYTES_PER_UPDATE_F16 * cells * args.steps / (ms * 1e-3) / 1e9
-    return {"metric": "MLUPS (all coupled fields), FP16 population storage", "value": round(mlups, 2),
-            "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": BYTES_PER_UPDATE_F16,
-            "bytes_moved_per_update": BYTES_PER_UPDATE_F16 + 8,
+    gbs = nbytes * cells * args.steps / (ms * 1e-3) / 1e9
+    what = "FP16 population storage" if form == 1 else "FP16 f, g, l populations, FP32 enthalpy populations"
+    return {"metric": "MLUPS (all coupled fields), " + what, "value": round(mlups, 2),
+            "unit": "MLUPS", "ms_per_step": round(ms / args.steps, 4), "bytes_per_update": nbytes,
+            "bytes_moved_per_update": nbytes + 8,
             "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak_gbs, 4) if peak_gbs else None,
-            "dtype": "f32 arithmetic, f16 populations"}
+            "dtype": "f32 arithmetic, " + ("f16 populations" if form == 1 else "f16 f/g/l and f32 h populations")}
 
 
 def _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist, peak_gbs):
@@ -308,6 +312,11 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
     choice16 = b16.tune(trials=3)
     ms_16 = timed(b16.step)
     b16.close()
+    sweep16h = [dict(w, params=dict(w["params"], pop_storage=2)) for w in sweep]
+    b16h = lbfreeze.Batch(sweep16h, stream=stream)
+    choice16h = b16h.tune(trials=3)
+    ms_16h = timed(b16h.step)
+    b16h.close()
     v_b = ws * n * K / (ms_b * 1e-3)
     v_s = ws * n * K / (ms_s * 1e-3)
     v_16 = ws * n * K / (ms_16 * 1e-3)
@@ -316,6 +325,9 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
                         "Ma U[0,50], C0 U[0,0.1], contact angle U[60,120] deg, seed 20251109" % n,
             "fp16_storage": {"value": round(v_16, 1), "mlups": round(ws * cells * K / (ms_16 * 1e-3) / 1e6, 1),
                              "seg_rows_by_class": choice16},
+            "fp16_h32_storage": {"value": round(ws * n * K / (ms_16h * 1e-3), 1),
+                                 "mlups": round(ws * cells * K / (ms_16h * 1e-3) / 1e6, 1),
+                                 "seg_rows_by_class": choice16h},
             "instances": n, "cells": cells, "steps": K, "mlups": round(ws * cells * K / (ms_b * 1e-3) / 1e6, 1),
             "seg_rows_by_class": choice, "launches_per_step": 1,
             "sequential": {"value": round(v_s, 1), "mlups": round(ws * cells * K / (ms_s * 1e-3) / 1e6, 1),
@@ -326,13 +338,13 @@ def _batched_leg(args, lbfreeze, W, np, torch, stream, ws, dist):
 def _freezing_leg(args, lbfreeze, W, np, torch):
     """A 512^2 binary sessile droplet (R = 100, 90 degrees, Ste 0.1, C0 0.05,
     Ma 10; gas density ratio 0.1) run until 99 % of the phase-change material
-    is solid, with FP32 and with FP16 population storage: freezing time
+    is solid, with FP32, FP16 and FP16-with-FP32-enthalpy population storage: freezing time
     (diagnostics in FP64 every 500 steps, linear interpolation), final V*_sl,
     and wall time."""
     w = W.sessile_droplet(nx=512, ny=512, radius=100.0, rho_g=0.1, ste=0.1, c0=0.05, ma_T=10.0, ma_C=10.0)
     f32 = {k: np.asarray(v, dtype=np.float32) for k, v in w["fields"].items()}
     out = {}
-    for name, st in (("f32", 0), ("f16", 1)):
+    for name, st in (("f32", 0), ("f16", 1), ("f16_h32", 2)):
         s = lbfreeze.Solver(w["grid"], dict(w["params"], pop_storage=st), f32)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -351,6 +363,7 @@ def _freezing_leg(args, lbfreeze, W, np, torch):
                      "mlups": round(512 * 512 * n / dt / 1e6, 1)}
         s.close()
     out["fp16_rel_error_t_f"] = abs(out["f16"]["t_f"] - out["f32"]["t_f"]) / out["f32"]["t_f"]
+    out["fp16_h32_rel_error_t_f"] = abs(out["f16_h32"]["t_f"] - out["f32"]["t_f"]) / out["f32"]["t_f"]
     out["workload"] = "sessile droplet 512x512, R=100, theta=90, Ste=0.1, C0=0.05, Ma_T=Ma_C=10, rho_g/rho_l=0.1"
     return out
 
@@ -551,9 +564,12 @@ def run_gpu(args):
 
     # ---- batched form: a sweep of independent droplets in one launch per step -----------
     fp16 = None
+    fp16h = None
     if not args.no_fp16:
         fp16 = _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
                          _peaks()[0].get("hbm_gbs"))
+        fp16h = _fp16_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
+                          _peaks()[0].get("hbm_gbs"), form=2)
     d2q5 = None
     if not args.no_d2q5:
         d2q5 = _d2q5_leg(args, lbfreeze, w, f32, cells, torch, stream, ws, dist if ws > 1 else None,
@@ -605,6 +621,7 @@ def run_gpu(args):
                 "d2h_bytes_per_step": round(d2h)},
         "gpu_launches": args.steps * launches_per_step,
         "fp16_storage": fp16,
+        "fp16_h32_storage": fp16h,
         "d2q5_fl": d2q5,
         "batched": batched,
         "droplet_freezing": freeze,

@@ -60,6 +60,7 @@ def test_roofline_fraction_arithmetic():
     assert achieved / bench.NAMEPLATE_HBM_GBS == pytest.approx(0.5988, abs=1e-4)
     assert bench.BYTES_PER_UPDATE_F16 == 36 * 2 * 2 + 8 * 4 * 2
     assert bench.BYTES_PER_UPDATE_Q5 == 28 * 4 * 2 + 8 * 4 * 2
+    assert bench.BYTES_PER_UPDATE_F16H == 27 * 2 * 2 + 9 * 4 * 2 + 8 * 4 * 2
 
 
 def test_peaks_fall_back_when_the_measured_file_is_absent(tmp_path, monkeypatch):
