@@ -76,8 +76,9 @@ def _create(lib, grid, params, n, phi=True):
     dict(grid=dict(nx=1, ny=1 << 26)),
     dict(params=dict(eps=0.0)), dict(params=dict(rho_g=0.0)), dict(params=dict(mu_l=0.0)),
     dict(params=dict(mobility=-1.0)), dict(params=dict(lam_s=0.0)), dict(params=dict(D_l=0.0)),
-    dict(params=dict(divu_mode=2)), dict(params=dict(divu_mode=-1)), dict(params=dict(pop_storage=2)), dict(params=dict(sigma0=float("nan"))),
+    dict(params=dict(divu_mode=2)), dict(params=dict(divu_mode=-1)), dict(params=dict(pop_storage=3)), dict(params=dict(sigma0=float("nan"))),
     dict(params=dict(lattice_fl=2)), dict(params=dict(lattice_fl=1, pop_storage=1)),
+    dict(params=dict(lattice_fl=1, pop_storage=2)),
     dict(grid=dict(cos_theta_bottom=1.5)), dict(grid=dict(cos_theta_top=float("nan"))),
     dict(params=dict(T_sol=1.0, T_liq=0.0)), dict(grid=dict(bc_top=7)), dict(phi=False)])
 def test_invalid_arguments_rejected_without_a_device(lib, bad):
