@@ -32,7 +32,11 @@
  *
  * Parity pins (what fixes each part independently of this code) live in the
  * CPU test-suite; every function here is pinned there, and
- * tests/mutate_oracle.py lists which planted slips the pins catch.
+ * tests/mutate_oracle.py lists which planted slips the pins catch.  One term
+ * is parity unpinned on its own: the x component of -grad p in the effective
+ * force F~ of pass_local (no closed form puts a steady pressure gradient along
+ * the periodic x beside a flow along x); its y component, the same arithmetic,
+ * is pinned by a body force across a channel flow.
  */
 #include <math.h>
 #include <stdlib.h>
