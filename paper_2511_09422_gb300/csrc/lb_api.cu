@@ -218,16 +218,16 @@ static unsigned reduce_blocks(const Consts &K)
 template <int MODE, class PS>
 static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials)
 {
-    if (lbk::STRIP_SMEM > 48 * 1024) {  // rings above the default dynamic shared-memory limit need the opt-in
-        static bool opted = false;      // per instantiation
-        if (!opted) {
-            cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbk::STRIP_SMEM);
-            opted = true;
-        }
+    constexpr size_t smem = lbk::strip_smem<PS>();
+    static bool opted = false;  // per instantiation: rings above 48 KB need the opt-in, and the
+    if (!opted) {               // largest shared-memory carveout lets every resident block fit
+        cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        opted = true;
     }
     const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks(K) : strip_blocks(K);
-    lbk::lb_strip_kernel<MODE, PS><<<grid, dim3(32, LB_SW, 1), lbk::STRIP_SMEM, st>>>(K, B, partials);
+    lbk::lb_strip_kernel<MODE, PS><<<grid, dim3(32, LB_SW, 1), smem, st>>>(K, B, partials);
 }
 
 template <int MODE>
@@ -267,17 +267,18 @@ template <class PS>
 static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
                                   unsigned long long *counter, cudaStream_t st)
 {
-    if (lbk::STEP_SMEM > 48 * 1024) {
-        static bool opted = false;
-        if (!opted) {
-            cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lbk::STEP_SMEM);
-            opted = true;
-        }
+    constexpr size_t smem = lbk::strip_smem<PS>();
+    static bool opted = false;
+    if (!opted) {
+        cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        opted = true;
     }
-    const long long wave = 152LL * LB_SMINB, need = (nitems + LB_SW - 1) / LB_SW;
+    // one persistent wave: as many blocks per SM as the rings of PS allow
+    const long long wave = 152LL * lbk::strip_min_blocks<PS>(), need = (nitems + LB_SW - 1) / LB_SW;
     const unsigned grid = (unsigned)(need < wave ? (need < 1 ? 1 : need) : wave);
-    lbk::lb_step_kernel<PS><<<grid, dim3(32, LB_SW, 1), lbk::STEP_SMEM, st>>>(rec, ninst, nitems, parity, counter);
+    lbk::lb_step_kernel<PS><<<grid, dim3(32, LB_SW, 1), smem, st>>>(rec, ninst, nitems, parity, counter);
     return cudaGetLastError();
 }
 

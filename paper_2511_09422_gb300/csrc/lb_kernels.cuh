@@ -936,20 +936,61 @@ constexpr int NRED = 6;  // diagnostics: sums of phi, rho H, C, f_s, chi, and f_
 // at index l + off - c_ix, off = x0 - 1 - x_lo (in 1 .. 4).
 constexpr int WW = 40;
 
+// Bytes of a staged window slot of set S: 40 FP32 or 48 half columns.
+template <class PS>
+__host__ __device__ constexpr int win_bytes(int s)
+{
+    return PS::esize(s) == 2 ? 96 : 160;
+}
+// Elements of a staged window slot of set S in its storage type.
+template <class PS, int S>
+__host__ __device__ constexpr int win_elems()
+{
+    return win_bytes<PS>(S) / PS::esize(S);
+}
+
+// The rings of one warp under storage PS (windows of half sets take 96 bytes,
+// so a warp's rings are smaller and more warps fit on an SM).
+template <class PS>
 struct WarpRing {
+    static constexpr int OFF_H = 9 * win_bytes<PS>(SET_F);            // h windows in a pop row
+    static constexpr int OFF_L = OFF_H + 9 * win_bytes<PS>(SET_H);    // l windows
+    static constexpr int POPROW = OFF_L + 9 * win_bytes<PS>(SET_L);   // bytes of one pop row
     float2 lag[8][34];    // (phi, T) lagged
-    float2 dd[4][32];     // (dphi, dT)
-    float2 cf[4][32];     // (C, f_s)
-    float2 ps[4][32];     // (p, S) lagged, staged
-    float md[4][32];      // mdot
-    float dv[4][32];      // div u of the phi and h sources
+    float2 dd[3][32];     // (dphi, dT)                 rows y mod 3
+    float2 cf[3][32];     // (C, f_s)                   rows y mod 3
+    float2 ps[4][32];     // (p, S) lagged, staged      rows y & 3
+    float md[3][32];      // mdot                       rows y mod 3
+    float dv[3][32];      // div u of the phi and h sources, rows y mod 3
     float2 uv[4][34];     // lagged (u_x, u_y), staged when div u is the lagged velocity divergence
-    float pop[3][27][WW];  // staged pulls of f (0..8), h (9..17), l (18..26)
     float ax[3][NAX][WW];  // staged own-cell Q, f_s, u_x, u_y, C
-    float gp[2][9][WW];    // staged pulls of g
+    alignas(16) unsigned char pop[3][POPROW];       // staged pulls of f, h, l (windows 0..8 of each)
+    alignas(16) unsigned char gp[2][9 * win_bytes<PS>(SET_G)];  // staged pulls of g
+    // first element of window i of set S (f, h or l) in pop row r, or of g in gp row r
+    template <int S>
+    __device__ SetT<PS, S> *win(int r, int i)
+    {
+        unsigned char *b = S == SET_G ? &gp[r][0] : &pop[r][S == SET_F ? 0 : (S == SET_H ? OFF_H : OFF_L)];
+        return reinterpret_cast<SetT<PS, S> *>(b) + i * win_elems<PS, S>();
+    }
+    template <int S>
+    __device__ const SetT<PS, S> *win(int r, int i) const
+    {
+        const unsigned char *b = S == SET_G ? &gp[r][0] : &pop[r][S == SET_F ? 0 : (S == SET_H ? OFF_H : OFF_L)];
+        return reinterpret_cast<const SetT<PS, S> *>(b) + i * win_elems<PS, S>();
+    }
 };
 
-constexpr size_t STRIP_SMEM = sizeof(WarpRing) * LB_SW;
+template <class PS>
+__host__ __device__ constexpr size_t strip_smem() { return sizeof(WarpRing<PS>) * LB_SW; }
+
+// Blocks (of LB_SW warps) resident per SM: as many as the rings of storage PS
+// allow in the 228 KB of shared memory (1 KB reserved per block), at most 6.
+template <class PS>
+__host__ __device__ constexpr int strip_min_blocks()
+{
+    return (int)((228 * 1024) / (strip_smem<PS>() + 1024)) < 6 ? (int)((228 * 1024) / (strip_smem<PS>() + 1024)) : 6;
+}
 
 __host__ __device__ inline int strip_groups(int nx) { return ((nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW; }
 __host__ __device__ inline int strip_segments(int ny, int segh) { return 2 + (ny >= 5 ? (ny - 4 + segh - 1) / segh : 0); }
@@ -978,20 +1019,13 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Elements of a staged window slot (160 bytes) in the storage type T.
-template <class T>
-__host__ __device__ constexpr int win_elems()
-{
-    return WW * (int)(sizeof(float) / sizeof(T));
-}
-
 // Decoded staged pulls of set S for the lane whose window index is idx.
 template <class PS, int S>
-__device__ __forceinline__ void load9(const Consts &K, const WarpRing &w, int slot, int idx, real v[9])
+__device__ __forceinline__ void load9(const Consts &K, const WarpRing<PS> &w, int slot, int idx, real v[9])
 {
     typedef SetT<PS, S> T;
-    constexpr int E = win_elems<T>();
-    const T *p = reinterpret_cast<const T *>(&w.pop[slot][S == SET_F ? 0 : (S == SET_H ? 9 : 18)][0]) + idx;
+    constexpr int E = win_elems<PS, S>();
+    const T *p = w.template win<S>(slot, 0) + idx;
 #pragma unroll
     for (int i = 0; i < 9; i++)
         v[i] = ((S == SET_F || S == SET_L) && i >= PS::QFL) ? R(0.0) : dec_pop<PS, S>(K, i, p[i * E - cx(i)]);
@@ -1015,14 +1049,14 @@ __device__ __forceinline__ void abb_fix9(const Consts &K, real v[9], int x, int 
 // Accessor of phase_b for the strip kernel.
 template <class PS, bool W>
 struct RingAcc {
-    const WarpRing &w;
-    int lane, off, off_h;       // window offsets of the staged planes: all but h, and h
-    int sl[3], sg[3], sp, sgp;  // loc slots, lag slots (rows y-1, y, y+1), pop / ax slot, gp slot
+    const WarpRing<PS> &w;
+    int lane, off, off_h;              // window offsets of the staged planes: all but h, and h
+    int sl[3], sq[3], sg[3], sp, sgp;  // rows y-1, y, y+1 in the mod-3, mod-4 and lag rings; pop / ax row, gp row
     // pairs read together (one 64-bit shared load each)
     __device__ float2 lagv(int dy, int dx) const { return w.lag[sg[dy + 1]][lane + 1 + dx]; }
     __device__ float2 ddv(int dy, int dx) const { return w.dd[sl[dy + 1]][lane + dx]; }
     __device__ float2 cfv(int dy, int dx) const { return w.cf[sl[dy + 1]][lane + dx]; }
-    __device__ float2 psv(int dy, int dx) const { return w.ps[sl[dy + 1]][lane + dx]; }
+    __device__ float2 psv(int dy, int dx) const { return w.ps[sq[dy + 1]][lane + dx]; }
     __device__ real phip(int dy, int dx) const { return lagv(dy, dx).x; }
     __device__ real Tp(int dy, int dx) const { return lagv(dy, dx).y; }
     __device__ real dphi(int dy, int dx) const { return ddv(dy, dx).x; }
@@ -1033,7 +1067,7 @@ struct RingAcc {
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
     __device__ real divu() const { return w.dv[sl[1]][lane]; }
-    __device__ float2 lagu() const { return w.uv[sl[1]][lane + 1]; }  // own lagged (u_x, u_y), divu mode only
+    __device__ float2 lagu() const { return w.uv[sq[1]][lane + 1]; }  // own lagged (u_x, u_y), divu mode only
     // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
@@ -1044,8 +1078,8 @@ struct RingAcc {
     __device__ void gpops(const Consts &K, real v[9]) const
     {
         typedef SetT<PS, SET_G> T;
-        constexpr int E = win_elems<T>();
-        const T *p = reinterpret_cast<const T *>(&w.gp[sgp][0][0]) + lane + off;
+        constexpr int E = win_elems<PS, SET_G>();
+        const T *p = w.template win<SET_G>(sgp, 0) + lane + off;
 #pragma unroll
         for (int i = 0; i < 9; i++) v[i] = dec_val(p[i * E - cx(i)]);
     }
@@ -1059,7 +1093,7 @@ template <class PS, int S, bool W>
 __device__ __forceinline__ void stage9(const Consts &K, const float *__restrict__ pin, int x, int y, int cell,
                                        SetT<PS, S> *dst)
 {
-    constexpr int E = win_elems<SetT<PS, S>>();
+    constexpr int E = win_elems<PS, S>();
     if constexpr (PS::esize(S) == 4) {
         cp_async4(dst + 0 * E - cx(0), pull_src<PS, S, 0, W>(K, pin, x, y, cell));
         cp_async4(dst + 1 * E - cx(1), pull_src<PS, S, 1, W>(K, pin, x, y, cell));
@@ -1087,8 +1121,8 @@ __device__ __forceinline__ void stage9(const Consts &K, const float *__restrict_
 
 // Lagged phi and T of the cell that wrote the population pulled into direction
 // I at row y, lane column: from the lag ring (own cell at a wall).
-template <int I, bool W>
-__device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int lane, int y, real &ph, real &tt)
+template <int I, bool W, class RG>
+__device__ __forceinline__ void lag_src(const Consts &K, const RG &w, int lane, int y, real &ph, real &tt)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
@@ -1097,8 +1131,8 @@ __device__ __forceinline__ void lag_src(const Consts &K, const WarpRing &w, int 
     tt = v.y;
 }
 
-template <bool W, int QF>
-__device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w, int lane, int y, real phi_own,
+template <bool W, int QF, class RG>
+__device__ __forceinline__ void lag_dev_sums(const Consts &K, const RG &w, int lane, int y, real phi_own,
                                              real T_own, real &dph, real &dtt)
 {
     real ph[9], tt[9];
@@ -1124,8 +1158,8 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const WarpRing &w,
 // Isotropic divergence of the lagged velocity at row y, lane column, from the
 // uv ring (columns x0 - 2 .. x0 + 31 at index lane + 1 + dx); a row beyond a
 // wall is the ghost -u of row y.  Same stencil and order as lagged_divu.
-template <bool W>
-__device__ __forceinline__ real ring_divu(const Consts &K, const WarpRing &w, int lane, int y)
+template <bool W, class RG>
+__device__ __forceinline__ real ring_divu(const Consts &K, const RG &w, int lane, int y)
 {
     const int c = lane + 1;
     const bool gs = W && y - 1 < 0, gn = W && y + 1 >= K.ny;
@@ -1143,7 +1177,7 @@ __device__ __forceinline__ real ring_divu(const Consts &K, const WarpRing &w, in
 // Phase A / phase B sweep of one warp over rows [ys, ye) of its strip.  WALLS =
 // false: every row ys - 2 .. ye + 1 lies inside the lattice.
 template <int MODE, bool WALLS, class PS>
-__device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing &w, int lane, int x0, int ys, int ye,
+__device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing<PS> &w, int lane, int x0, int ys, int ye,
                                            double acc[NRED])
 {
     typedef SetT<PS, SET_F> TF;  // f and l
@@ -1152,9 +1186,8 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     constexpr bool PB = MODE != MODE_REDUCE;  // phase B follows phase A
     constexpr bool HALF = PS::kHalf;          // f, g and l in half precision
     constexpr bool HMIX = HALF && PS::esize(SET_H) == 4;  // ... and h in FP32
-    constexpr int EF = win_elems<TF>();       // window slot size in elements of f / l, g, h
-    constexpr int EG = win_elems<TG>();
-    constexpr int EH = win_elems<TH>();
+    constexpr int EF = win_elems<PS, SET_F>();  // window slot size in elements of f / l, g
+    constexpr int EG = win_elems<PS, SET_G>();
     constexpr int CH = HALF ? 8 : 4;          // elements of a 16-byte chunk of f, g and l
     constexpr int PLEN = HALF ? 48 : 40;      // staged columns of a population window
     const int ex = x0 - 1 + lane;
@@ -1222,7 +1255,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                     const float *src = (wg == 0 ? set_plane<PS, SET_F>(pin, 0, K)
                                                 : (wg == 1 ? set_plane<PS, SET_H>(pin, 0, K) : set_plane<PS, SET_L>(pin, 0, K))) +
                                        wcol;
-                    float *dst = &w.pop[s3][9 * wg][0] + 4 * wpart;
+                    float *dst = (wg == 0 ? w.template win<SET_F>(s3, 0)
+                                          : (wg == 1 ? w.template win<SET_H>(s3, 0) : w.template win<SET_L>(s3, 0))) +
+                                 4 * wpart;
                     const int nq = wg == 1 ? 9 : PS::QFL;  // D2Q5 f and l: directions 0 .. 4
 #pragma unroll
                     for (int i = 0; i < 9; i++)
@@ -1236,10 +1271,12 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                     for (int q = 0; q < (NHW + 4) / 5; q++) {
                         const int wi = 5 * q + hg;
                         if (wi < NHW) {
-                            // HMIX: f 0..8, l 9..17 (ring windows 0..8, 18..26); else f, h, l = ring windows
+                            // HMIX: f 0..8, l 9..17; else f 0..8, h 9..17, l 18..26
                             const int set = HMIX ? (wi < 9 ? SET_F : SET_L) : (wi < 9 ? SET_F : (wi < 18 ? SET_H : SET_L));
                             const int i = wi % 9;
-                            const int slot = HMIX ? (wi < 9 ? wi : wi + 9) : wi;
+                            __half *dst = set == SET_F ? w.template win<SET_F>(s3, i)
+                                                       : (set == SET_H ? reinterpret_cast<__half *>(w.template win<SET_H>(s3, i))
+                                                                       : w.template win<SET_L>(s3, i));
                             const int before = set == SET_F ? set_bytes_before<PS>(SET_F)
                                                              : (set == SET_H ? set_bytes_before<PS>(SET_H)
                                                                              : set_bytes_before<PS>(SET_L));
@@ -1247,7 +1284,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                                                     reinterpret_cast<const char *>(pin) +
                                                     (size_t)(unsigned)K.plane * (unsigned)(before + 2 * i)) +
                                                 ((y - cy(i)) * K.pitch + x_lo + CH * hpart);
-                            cp_async16(reinterpret_cast<__half *>(&w.pop[s3][slot][0]) + CH * hpart, src);
+                            cp_async16(dst + CH * hpart, src);
                         }
                     }
                 }
@@ -1258,7 +1295,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                         for (int q = 0; q < 3; q++) {
                             const int i = 3 * q + wg;
                             const int cyi = wg == 0 ? cy(3 * q) : (wg == 1 ? cy(3 * q + 1) : cy(3 * q + 2));
-                            cp_async16(&w.pop[s3][9 + i][0] + 4 * wpart,
+                            cp_async16(reinterpret_cast<float *>(w.template win<SET_H>(s3, i)) + 4 * wpart,
                                        set_plane<PS, SET_H>(pin, i, K) + ((y - cyi) * K.pitch + x_lo_h + 4 * wpart));
                         }
                     }
@@ -1266,9 +1303,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             }
             stage_ax_win(y, s3);
         } else {
-            stage9<PS, SET_F, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TF *>(&w.pop[s3][0][0]) + lane + off);
-            stage9<PS, SET_H, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TH *>(&w.pop[s3][9][0]) + lane + off_h);
-            stage9<PS, SET_L, WALLS>(K, pin, xg, y, cell, reinterpret_cast<TF *>(&w.pop[s3][18][0]) + lane + off);
+            stage9<PS, SET_F, WALLS>(K, pin, xg, y, cell, w.template win<SET_F>(s3, 0) + lane + off);
+            stage9<PS, SET_H, WALLS>(K, pin, xg, y, cell, w.template win<SET_H>(s3, 0) + lane + off_h);
+            stage9<PS, SET_L, WALLS>(K, pin, xg, y, cell, w.template win<SET_L>(s3, 0) + lane + off);
             float *pa = &w.ax[s3][0][lane + off];
             cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
             cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
@@ -1292,7 +1329,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             if constexpr (!HALF) {
                 if (wg < 3) {
                     const float *src = set_plane<PS, SET_G>(pin, 0, K) + wcol;
-                    float *gw = &w.gp[y & 1][0][0];
+                    float *gw = reinterpret_cast<float *>(w.template win<SET_G>(y & 1, 0));
 #pragma unroll
                     for (int q = 0; q < 3; q++) {
                         const int i = 3 * q + wg;  // direction of this group's window
@@ -1302,7 +1339,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                 }
             } else {
                 if (hg < 5) {
-                    __half *gw = reinterpret_cast<__half *>(&w.gp[y & 1][0][0]);
+                    __half *gw = reinterpret_cast<__half *>(w.template win<SET_G>(y & 1, 0));
 #pragma unroll
                     for (int q = 0; q < 2; q++) {
                         const int i = 5 * q + hg;
@@ -1315,7 +1352,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             }
         } else if (b_lane) {
             stage9<PS, SET_G, WALLS>(K, pin, ex, y, y * K.pitch + ex,
-                                     reinterpret_cast<TG *>(&w.gp[y & 1][0][0]) + lane + off);
+                                     w.template win<SET_G>(y & 1, 0) + lane + off);
         }
     };
 
@@ -1370,18 +1407,18 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                     if (ex == K.nx / 2) acc[5] += (double)L.fs;
                 }
             } else {
-                const int s4 = ya & 3;
-                w.dd[s4][lane] = make_float2(L.dphi, L.dT);
-                w.cf[s4][lane] = make_float2(L.C, L.fs);
-                w.md[s4][lane] = L.mdot;
-                w.dv[s4][lane] = L.divu;
+                w.dd[s3][lane] = make_float2(L.dphi, L.dT);
+                w.cf[s3][lane] = make_float2(L.C, L.fs);
+                w.md[s3][lane] = L.mdot;
+                w.dv[s3][lane] = L.divu;
             }
         }
         __syncwarp();
         // ---- phase B, row ya - 1 ----------------------------------------------------------
         const int yb = ya - 1;
         if (PB && yb >= ys && yb < ye && b_lane) {
-            const RingAcc<PS, WALLS> A{w, lane, off, off_h, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
+            // rows yb - 1 = ya - 2, yb = ya - 1 and yb + 1 = ya are s3n, s3p and s3 mod 3
+            const RingAcc<PS, WALLS> A{w, lane, off, off_h, {s3n, s3p, s3}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
                                        {(yb - 1) & 7, yb & 7, (yb + 1) & 7}, s3p, yb & 1};
             phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
@@ -1394,14 +1431,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
 #ifdef LB_MAXNREG
 #define LB_STRIP_BOUNDS __maxnreg__(LB_MAXNREG)
 #else
-#define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, LB_SMINB)
+#define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, strip_min_blocks<PS>())
 #endif
 
 template <int MODE, class PS>
 __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B, double *__restrict__ partials)
 {
     extern __shared__ __align__(16) unsigned char lb_smem[];
-    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
+    WarpRing<PS> &w = reinterpret_cast<WarpRing<PS> *>(lb_smem)[threadIdx.y];
     const int lane = threadIdx.x;
     const int ngroups = strip_groups(K.nx);
     const int nblocks = ngroups * strip_segments(K.ny, K.segh);
@@ -1450,7 +1487,6 @@ struct StepRec {
     long long item0;  // first work item of the instance
 };
 
-constexpr size_t STEP_SMEM = STRIP_SMEM;
 
 template <class PS>
 __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst, int ninst, long long nitems,
@@ -1458,7 +1494,7 @@ __global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst,
 {
     const unsigned long long nwarps = (unsigned long long)gridDim.x * blockDim.y;
     extern __shared__ __align__(16) unsigned char lb_smem[];
-    WarpRing &w = reinterpret_cast<WarpRing *>(lb_smem)[threadIdx.y];
+    WarpRing<PS> &w = reinterpret_cast<WarpRing<PS> *>(lb_smem)[threadIdx.y];
     const int lane = threadIdx.x;
     double acc[NRED];  // unused in MODE_STEP
     for (;;) {
