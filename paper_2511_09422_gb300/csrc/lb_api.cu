@@ -267,7 +267,8 @@ template <class PS>
 static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long nitems, int parity,
                                   unsigned long long *counter, cudaStream_t st)
 {
-    constexpr size_t smem = lbk::strip_smem<PS>();
+    constexpr size_t smem = lbk::step_smem<PS>();
+    constexpr int sw = lbk::step_warps<PS>();
     static bool opted = false;
     if (!opted) {
         cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -276,9 +277,9 @@ static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long 
         opted = true;
     }
     // one persistent wave: as many blocks per SM as the rings of PS allow
-    const long long wave = 152LL * lbk::strip_min_blocks<PS>(), need = (nitems + LB_SW - 1) / LB_SW;
+    const long long wave = 152LL * lbk::step_min_blocks<PS>(), need = (nitems + sw - 1) / sw;
     const unsigned grid = (unsigned)(need < wave ? (need < 1 ? 1 : need) : wave);
-    lbk::lb_step_kernel<PS><<<grid, dim3(32, LB_SW, 1), smem, st>>>(rec, ninst, nitems, parity, counter);
+    lbk::lb_step_kernel<PS><<<grid, dim3(32, sw, 1), smem, st>>>(rec, ninst, nitems, parity, counter);
     return cudaGetLastError();
 }
 

@@ -108,8 +108,18 @@ struct PopF32Q5 : PopF32 {
 template <class PS, int S>
 using SetT = typename std::conditional<PS::esize(S) == 2, __half, float>::type;
 
+// v 2^-8 + c in one mixed-precision FMA (sm_100+: half multiplicands, FP32
+// addend and result).  The product of two halves is exact in FP32, so this is
+// the FP32 sum of the decoded deviation and c, rounded once; c = -0 gives the
+// deviation itself with the sign of a zero kept.
+__device__ __forceinline__ float dec_fma(__half v, float c)
+{
+    float d;
+    asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(__half_as_ushort(v)), "h"((unsigned short)0x1C00), "f"(c));
+    return d;
+}
 __device__ __forceinline__ real dec_val(float v) { return v; }
-__device__ __forceinline__ real dec_val(__half v) { return __half2float(v) * R(1.0 / 256.0); }
+__device__ __forceinline__ real dec_val(__half v) { return dec_fma(v, -0.0f); }
 template <class T>
 __device__ __forceinline__ T enc_val(real d);
 template <>
@@ -370,7 +380,10 @@ __device__ __forceinline__ real abb_fix(const Consts &K, real v, int x, int y, r
 template <class PS, int S>
 __device__ __forceinline__ real dec_pop(const Consts &K, int i, SetT<PS, S> v)
 {
-    return (PS::esize(S) == 2 && S == SET_L) ? dec_val(v) + wgt(i) * K.c_ref : dec_val(v);
+    if constexpr (PS::esize(S) == 2 && S == SET_L)
+        return dec_fma(v, wgt(i) * K.c_ref);
+    else
+        return dec_val(v);
 }
 
 template <class PS, int S>
@@ -992,6 +1005,31 @@ __host__ __device__ constexpr int strip_min_blocks()
     return (int)((228 * 1024) / (strip_smem<PS>() + 1024)) < 6 ? (int)((228 * 1024) / (strip_smem<PS>() + 1024)) : 6;
 }
 
+// Warps per block of the step kernel under storage PS.  Its warps claim work
+// items independently, so the block shape only packs rings into shared memory.
+// FP32 rings (24.3 KB a warp) fit nine warps per SM in blocks of three, but at
+// the 168 registers the compiler then takes the step is 3 % slower than eight
+// warps of two-warp blocks at 250 (measured at 4096^2).
+#ifndef LB_STEP_SW32
+#define LB_STEP_SW32 2
+#endif
+template <class PS>
+__host__ __device__ constexpr int step_warps() { return PS::kHalf ? LB_SW : LB_STEP_SW32; }
+template <class PS>
+__host__ __device__ constexpr size_t step_smem() { return sizeof(WarpRing<PS>) * step_warps<PS>(); }
+// Resident step blocks per SM: as many as shared memory allows, at most
+// LB_STEP_MAXW warps.
+#ifndef LB_STEP_MAXW
+#define LB_STEP_MAXW 12
+#endif
+template <class PS>
+__host__ __device__ constexpr int step_min_blocks()
+{
+    return (int)((228 * 1024) / (step_smem<PS>() + 1024)) < LB_STEP_MAXW / step_warps<PS>()
+               ? (int)((228 * 1024) / (step_smem<PS>() + 1024))
+               : LB_STEP_MAXW / step_warps<PS>();
+}
+
 __host__ __device__ inline int strip_groups(int nx) { return ((nx + LB_TX - 1) / LB_TX + LB_SW - 1) / LB_SW; }
 __host__ __device__ inline int strip_segments(int ny, int segh) { return 2 + (ny >= 5 ? (ny - 4 + segh - 1) / segh : 0); }
 
@@ -1489,7 +1527,7 @@ struct StepRec {
 
 
 template <class PS>
-__global__ void LB_STRIP_BOUNDS lb_step_kernel(const StepRec *__restrict__ inst, int ninst, long long nitems,
+__global__ void __launch_bounds__(32 * step_warps<PS>(), step_min_blocks<PS>()) lb_step_kernel(const StepRec *__restrict__ inst, int ninst, long long nitems,
                                                 int parity, unsigned long long *__restrict__ counter)
 {
     const unsigned long long nwarps = (unsigned long long)gridDim.x * blockDim.y;
