@@ -543,7 +543,7 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
 }
 
 // Own-cell lagged values staged for phase B (the accessor's aux(k)).
-enum { AX_Q = 0, AX_FS = 1, AX_UX = 2, AX_UY = 3, AX_C = 4, NAX = 5 };
+enum { AX_Q = 0, AX_FS = 1, AX_C = 2, NAX = 3 };
 
 // MODE_STEP collides and streams; MODE_FIELDS stores the macroscopic fields of the
 // current state instead; MODE_REDUCE runs phase A only and sums the diagnostics.
@@ -776,7 +776,7 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 
     // phase-field set (Sec. 3.1): F_i = w c.[d_t(phi u) + cs2 n (1 - phi^2)/(sqrt2 eps)]/cs2 + w phi div u
     {
-        const float2 u_p = K.divu ? A.lagu() : make_float2(A.aux(AX_UX), A.aux(AX_UY));
+        const float2 u_p = A.lagu();
         const real ux_p = u_p.x, uy_p = u_p.y;
         const real kf = -(R(1.0) / R(3.0)) * phi2m1 * K.inv_s2eps;
         const real ax = (phi * ux - phi_p * ux_p) + kf * nxv;
@@ -969,14 +969,14 @@ struct WarpRing {
     static constexpr int OFF_H = 9 * win_bytes<PS>(SET_F);            // h windows in a pop row
     static constexpr int OFF_L = OFF_H + 9 * win_bytes<PS>(SET_H);    // l windows
     static constexpr int POPROW = OFF_L + 9 * win_bytes<PS>(SET_L);   // bytes of one pop row
-    float2 lag[8][34];    // (phi, T) lagged
+    float2 lag[5][34];    // (phi, T) lagged           rows y mod 5
     float2 dd[3][32];     // (dphi, dT)                 rows y mod 3
     float2 cf[3][32];     // (C, f_s)                   rows y mod 3
     float2 ps[4][32];     // (p, S) lagged, staged      rows y & 3
     float md[3][32];      // mdot                       rows y mod 3
     float dv[3][32];      // div u of the phi and h sources, rows y mod 3
-    float2 uv[4][34];     // lagged (u_x, u_y), staged when div u is the lagged velocity divergence
-    float ax[3][NAX][WW];  // staged own-cell Q, f_s, u_x, u_y, C
+    float2 uv[4][34];     // lagged (u_x, u_y), staged    rows y & 3
+    float ax[3][NAX][WW];  // staged own-cell Q, f_s, C   rows y mod 3
     alignas(16) unsigned char pop[3][POPROW];       // staged pulls of f, h, l (windows 0..8 of each)
     alignas(16) unsigned char gp[2][9 * win_bytes<PS>(SET_G)];  // staged pulls of g
     // first element of window i of set S (f, h or l) in pop row r, or of g in gp row r
@@ -1049,6 +1049,7 @@ __device__ __forceinline__ void segment_rows(int ny, int segh, int s, int &ys, i
 }
 
 __device__ __forceinline__ int mod3(int v) { return ((v % 3) + 3) % 3; }
+__device__ __forceinline__ int mod5(int v) { return ((v % 5) + 5) % 5; }
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -1105,7 +1106,7 @@ struct RingAcc {
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
     __device__ real divu() const { return w.dv[sl[1]][lane]; }
-    __device__ float2 lagu() const { return w.uv[sq[1]][lane + 1]; }  // own lagged (u_x, u_y), divu mode only
+    __device__ float2 lagu() const { return w.uv[sq[1]][lane + 1]; }  // own lagged (u_x, u_y)
     // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
@@ -1160,28 +1161,29 @@ __device__ __forceinline__ void stage9(const Consts &K, const float *__restrict_
 // Lagged phi and T of the cell that wrote the population pulled into direction
 // I at row y, lane column: from the lag ring (own cell at a wall).
 template <int I, bool W, class RG>
-__device__ __forceinline__ void lag_src(const Consts &K, const RG &w, int lane, int y, real &ph, real &tt)
+__device__ __forceinline__ void lag_src(const Consts &K, const RG &w, int lane, int y, const int lr[3], real &ph, real &tt)
 {
     constexpr int ys_off = -cy(I);
     const int ys = y + ys_off;
-    const float2 v = (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) ? w.lag[y & 7][lane + 1] : w.lag[ys & 7][lane + 1 - cx(I)];
+    const float2 v = (W && ys_off != 0 && (ys < 0 || ys >= K.ny)) ? w.lag[lr[1]][lane + 1] : w.lag[lr[ys_off + 1]][lane + 1 - cx(I)];
     ph = v.x;
     tt = v.y;
 }
 
+// lr: lag-ring rows of rows y - 1, y and y + 1.
 template <bool W, int QF, class RG>
-__device__ __forceinline__ void lag_dev_sums(const Consts &K, const RG &w, int lane, int y, real phi_own,
+__device__ __forceinline__ void lag_dev_sums(const Consts &K, const RG &w, int lane, int y, const int lr[3], real phi_own,
                                              real T_own, real &dph, real &dtt)
 {
     real ph[9], tt[9];
-    lag_src<1, W>(K, w, lane, y, ph[1], tt[1]);
-    lag_src<2, W>(K, w, lane, y, ph[2], tt[2]);
-    lag_src<3, W>(K, w, lane, y, ph[3], tt[3]);
-    lag_src<4, W>(K, w, lane, y, ph[4], tt[4]);
-    lag_src<5, W>(K, w, lane, y, ph[5], tt[5]);
-    lag_src<6, W>(K, w, lane, y, ph[6], tt[6]);
-    lag_src<7, W>(K, w, lane, y, ph[7], tt[7]);
-    lag_src<8, W>(K, w, lane, y, ph[8], tt[8]);
+    lag_src<1, W>(K, w, lane, y, lr, ph[1], tt[1]);
+    lag_src<2, W>(K, w, lane, y, lr, ph[2], tt[2]);
+    lag_src<3, W>(K, w, lane, y, lr, ph[3], tt[3]);
+    lag_src<4, W>(K, w, lane, y, lr, ph[4], tt[4]);
+    lag_src<5, W>(K, w, lane, y, lr, ph[5], tt[5]);
+    lag_src<6, W>(K, w, lane, y, lr, ph[6], tt[6]);
+    lag_src<7, W>(K, w, lane, y, lr, ph[7], tt[7]);
+    lag_src<8, W>(K, w, lane, y, lr, ph[8], tt[8]);
     if (QF == 9)
         dph = (wgt(1) * (ph[1] - phi_own) + wgt(2) * (ph[2] - phi_own) + wgt(3) * (ph[3] - phi_own) +
                wgt(4) * (ph[4] - phi_own)) +
@@ -1249,19 +1251,21 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     const int wcol = x_lo + 4 * wpart;
     const int hg = lane / 6, hpart = lane - 6 * hg;    // half windows: 6 chunks, 5 windows per copy
 
-    auto stage_lag = [&](int yl) {
+    // lagged (phi, T) of row yl into lag-ring row lr (= yl mod 5)
+    auto stage_lag = [&](int yl, int lr) {
         if (WALLS && (yl < 0 || yl >= K.ny)) return;
         const int ro = yl * K.pitch;
-        cp_async4(&w.lag[yl & 7][lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xa));
-        cp_async4(&w.lag[yl & 7][lane].y, plane_ptr(ain, AUX_T, K) + (ro + xa));
+        cp_async4(&w.lag[lr][lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xa));
+        cp_async4(&w.lag[lr][lane].y, plane_ptr(ain, AUX_T, K) + (ro + xa));
         if (lane < 2) {
-            cp_async4(&w.lag[yl & 7][32 + lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xb));
-            cp_async4(&w.lag[yl & 7][32 + lane].y, plane_ptr(ain, AUX_T, K) + (ro + xb));
+            cp_async4(&w.lag[lr][32 + lane].x, plane_ptr(ain, AUX_PHI, K) + (ro + xb));
+            cp_async4(&w.lag[lr][32 + lane].y, plane_ptr(ain, AUX_T, K) + (ro + xb));
         }
     };
-    // lagged (u_x, u_y) of row yl with the one-column halo, for the divergence of phase A
+    // lagged (u_x, u_y) of row yl with the one-column halo: the own-cell velocity of
+    // phase B, and the divergence of phase A (div u the lagged velocity divergence)
     auto stage_u = [&](int yl) {
-        if (!K.divu || (WALLS && (yl < 0 || yl >= K.ny))) return;
+        if ((!PB && !K.divu) || (WALLS && (yl < 0 || yl >= K.ny))) return;
         const int ro = yl * K.pitch;
         cp_async4(&w.uv[yl & 3][lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xa));
         cp_async4(&w.uv[yl & 3][lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xa));
@@ -1270,17 +1274,11 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             cp_async4(&w.uv[yl & 3][32 + lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xb));
         }
     };
-    // own-cell lagged values of row y as float windows: Q, f_s, u_x (first copy), u_y, C (second)
+    // own-cell lagged values of row y as float windows: Q, f_s and (phase B) C, one copy
     auto stage_ax_win = [&](int y, int s3) {
-        if (wg < 3) {
-            const int k0 = wg, k1 = wg + 3;
-            const int a0 = k0 == 0 ? AUX_Q : (k0 == 1 ? AUX_FS : AUX_UX);
-            // with the lagged velocity divergence the own-cell u comes from the uv ring
-            if ((PB && !(K.divu && k0 == 2)) || k0 < 2)
-                cp_async16(&w.ax[s3][k0][4 * wpart], plane_ptr(ain, a0, K) + (y * K.pitch + wcol));
-            if (PB && k1 < NAX && !(K.divu && k1 == 3))
-                cp_async16(&w.ax[s3][k1][4 * wpart], plane_ptr(ain, k1 == 3 ? AUX_UY : AUX_C, K) + (y * K.pitch + wcol));
-        }
+        if (wg < 3 && (PB || wg < 2))
+            cp_async16(&w.ax[s3][wg][4 * wpart],
+                       plane_ptr(ain, wg == 0 ? AUX_Q : (wg == 1 ? AUX_FS : AUX_C), K) + (y * K.pitch + wcol));
     };
     // phase-A inputs of row y, and the own-cell lagged values phase B needs
     auto stage_a = [&](int y, int s3) {  // s3 = y mod 3
@@ -1347,13 +1345,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             float *pa = &w.ax[s3][0][lane + off];
             cp_async4(pa + AX_Q * WW, plane_ptr(ain, AUX_Q, K) + cell);
             cp_async4(pa + AX_FS * WW, plane_ptr(ain, AUX_FS, K) + cell);
-            if (PB) {
-                if (!K.divu) {  // else from the uv ring
-                    cp_async4(pa + AX_UX * WW, plane_ptr(ain, AUX_UX, K) + cell);
-                    cp_async4(pa + AX_UY * WW, plane_ptr(ain, AUX_UY, K) + cell);
-                }
-                cp_async4(pa + AX_C * WW, plane_ptr(ain, AUX_C, K) + cell);
-            }
+            if (PB) cp_async4(pa + AX_C * WW, plane_ptr(ain, AUX_C, K) + cell);
         }
         if (PB) {
             cp_async4(&w.ps[y & 3][lane].x, plane_ptr(ain, AUX_P, K) + cell);
@@ -1396,19 +1388,23 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
 
     const int ya0 = PB ? ys - 1 : ys;
     const int ya1 = PB ? ye : ye - 1;
-    stage_lag(ya0 - 1);
-    stage_lag(ya0);
-    stage_lag(ya0 + 1);
+    int s3 = mod3(ya0), l5 = mod5(ya0);  // ya mod 3 and ya mod 5, advanced with the loop
+    auto lrow = [&](int k) {             // lag-ring row of row ya + k, k in -2 .. 2
+        const int v = l5 + k;
+        return v >= 5 ? v - 5 : (v < 0 ? v + 5 : v);
+    };
+    stage_lag(ya0 - 1, lrow(-1));
+    stage_lag(ya0, lrow(0));
+    stage_lag(ya0 + 1, lrow(1));
     stage_u(ya0 - 1);
     stage_u(ya0);
     stage_u(ya0 + 1);
-    int s3 = mod3(ya0);  // ya mod 3, advanced with the loop
     stage_a(ya0, s3);
     cp_async_commit();
-    for (int ya = ya0; ya <= ya1; ya++, s3 = s3 == 2 ? 0 : s3 + 1) {
+    for (int ya = ya0; ya <= ya1; ya++, s3 = s3 == 2 ? 0 : s3 + 1, l5 = l5 == 4 ? 0 : l5 + 1) {
         const int s3n = s3 == 2 ? 0 : s3 + 1, s3p = s3 == 0 ? 2 : s3 - 1;  // (ya + 1), (ya - 1) mod 3
         if (ya < ya1) {
-            stage_lag(ya + 2);
+            stage_lag(ya + 2, lrow(2));
             stage_u(ya + 2);
             stage_a(ya + 1, s3n);
         }
@@ -1418,10 +1414,11 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         __syncwarp();
         // ---- phase A, row ya ------------------------------------------------------------
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
-            const float2 lag0 = w.lag[ya & 7][lane + 1];
+            const int lr[3] = {lrow(-1), lrow(0), lrow(1)};
+            const float2 lag0 = w.lag[lr[1]][lane + 1];
             const real phi_p = lag0.x, T_p = lag0.y;
             real dph, dtt, v[9];
-            lag_dev_sums<WALLS, PS::QFL>(K, w, lane, ya, phi_p, T_p, dph, dtt);
+            lag_dev_sums<WALLS, PS::QFL>(K, w, lane, ya, lr, phi_p, T_p, dph, dtt);
             load9<PS, SET_F>(K, w, s3, lane + off, v);
             const real delta = sum9(v) + dph;
             load9<PS, SET_H>(K, w, s3, lane + off_h, v);
@@ -1457,7 +1454,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         if (PB && yb >= ys && yb < ye && b_lane) {
             // rows yb - 1 = ya - 2, yb = ya - 1 and yb + 1 = ya are s3n, s3p and s3 mod 3
             const RingAcc<PS, WALLS> A{w, lane, off, off_h, {s3n, s3p, s3}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
-                                       {(yb - 1) & 7, yb & 7, (yb + 1) & 7}, s3p, yb & 1};
+                                       {lrow(-2), lrow(-1), lrow(0)}, s3p, yb & 1};
             phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
         }
         __syncwarp();
