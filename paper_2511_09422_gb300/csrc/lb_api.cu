@@ -47,6 +47,13 @@ struct lb_handle {
     size_t halo_bytes = 0;          // bytes of one face's halo message (slabs only)
 };
 
+// Kernel kind of a run: 0 FP32 D2Q9, 1 FP16 D2Q9, 2 FP32 with D2Q5 f and l, 3 FP16 f, g, l with FP32 h.
+static int kind_of(const lb_params *p)
+{
+    return p->pop_storage == LB_STORAGE_F16 ? 1
+                                            : (p->pop_storage == LB_STORAGE_F16_H32 ? 3 : (p->lattice_fl == 1 ? 2 : 0));
+}
+
 // Calls f(PS{}) with the storage trait of kernel kind `kind`.
 template <class F>
 static auto with_storage(int kind, F f)
@@ -186,13 +193,21 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.expand = (real)(1.0 - p->rho_s / p->rho_l);
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
     K.segh = (p->pop_storage != LB_STORAGE_F32 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
-    // a small lattice needs shorter segments to give every resident warp work: go
-    // down (to 8 rows at least) until there are two waves of work items
+    // Shorter segments where the lattice gives the persistent wave of W warps too
+    // few work items: a step takes about ceil(items / W) rounds of (segh + 3) rows
+    // (a segment's rows plus its fill and copy prologue); the height of the
+    // default and the shorter candidates (8 rows at least) that minimises it.
     {
-        const long long wave = 152LL * LB_SMINB * LB_SW, nstrip = (g->nx + LB_TX - 1) / LB_TX;
-        const int steps[] = {24, 16, 12, 8};
-        for (int c : steps)
-            if (c < K.segh && nstrip * lbk::strip_segments(g->ny, K.segh) < 2 * wave) K.segh = c;
+        const long long W = with_storage(kind_of(p), [](auto ps) {
+            return 152LL * lbk::step_min_blocks<decltype(ps)>() * lbk::step_warps<decltype(ps)>();
+        });
+        const long long nstrip = (g->nx + LB_TX - 1) / LB_TX;
+        auto cost = [&](int h) { return (nstrip * lbk::strip_segments(g->ny, h) + W - 1) / W * (h + 3); };
+        const int cand[] = {24, 16, 12, 8};
+        int best = K.segh;
+        for (int c : cand)
+            if (c < K.segh && cost(c) < cost(best)) best = c;
+        K.segh = best;
     }
     K.qfl = p->lattice_fl == LB_LATTICE_D2Q5 ? 5 : 9;
     K.divu = p->divu_mode;
@@ -332,9 +347,7 @@ static lb_status create_handle(const lb_grid *grid, const lb_params *params, con
     h->grid = *grid;
     h->params = *params;
     h->half = params->pop_storage != LB_STORAGE_F32;
-    h->kind = params->pop_storage == LB_STORAGE_F16 ? 1
-                                                    : (params->pop_storage == LB_STORAGE_F16_H32 ? 3
-                                                                                                 : (params->lattice_fl == 1 ? 2 : 0));
+    h->kind = kind_of(params);
     h->K = make_consts(grid, params);
     h->K.ghost_lo = ghost_lo;
     h->K.ghost_hi = ghost_hi;

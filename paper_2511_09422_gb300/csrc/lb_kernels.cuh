@@ -929,12 +929,14 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #ifndef LB_SW
 #define LB_SW 2
 #endif
+// Blocks per SM of the capped diagnostics grid (one FP64 partial per warp).
 #ifndef LB_SMINB
 #define LB_SMINB 4
 #endif
 // Inner segment height of single-lattice handles, per kernel kind (measured on
 // the 4096^2 step): FP32 D2Q9 is fastest at 8-12 rows (32 rows: 5 % slower);
-// FP16 storage and D2Q5 f/l at 32 rows (12 rows: 5 % and 1.3 % slower).
+// the half forms and D2Q5 f/l at 32 rows (24 rows: 0.7-1.3 % slower).  The host
+// shortens them where a lattice gives the wave too few work items.
 #ifndef LB_SEGH
 #define LB_SEGH 12
 #endif
