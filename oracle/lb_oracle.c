@@ -84,6 +84,19 @@ double orc_zeta(double phi, double fs, double zl, double zs, double zg)
     return 0.5 * phi * (zl - zg) + fs * (zs - zl) + 0.5 * (zl + zg);
 }
 
+/* Volumetric heat capacity rho C_p of the advective terms of the enthalpy set
+ * (the h equilibrium and the source Q).  rhocp_rule 0 (the reading taken):
+ * the linear property rule applied to the product rho C_p of each phase.
+ * rhocp_rule 1 (the literal reading, for comparison only): the rule applied
+ * to rho and to C_p apart and the two multiplied, which peaks inside the
+ * interface when the phases have equal rho C_p but different densities. */
+static double rhocp_of(const orc_params *p, double phi, double fs)
+{
+    if (p->rhocp_rule == 1)
+        return orc_zeta(phi, fs, p->rho_l, p->rho_s, p->rho_g) * orc_zeta(phi, fs, p->cp_l, p->cp_s, p->cp_g);
+    return orc_zeta(phi, fs, p->rho_l * p->cp_l, p->rho_s * p->cp_s, p->rho_g * p->cp_g);
+}
+
 /* Fraction of phase-change material from the order parameter, clamped. */
 static double chi_of(double phi)
 {
@@ -412,7 +425,7 @@ orc_state *orc_create(const orc_grid *g, const orc_params *p, const double *phi0
         double Tc, fs;
         orc_enthalpy_invert(p, e, chi, &Tc, &fs);
         double rho = orc_zeta(ph, fs, p->rho_l, p->rho_s, p->rho_g);
-        double rhocp = orc_zeta(ph, fs, p->rho_l * p->cp_l, p->rho_s * p->cp_s, p->rho_g * p->cp_g);
+        double rhocp = rhocp_of(p, ph, fs);
         double feq[9], geq[9], heq[9], leq[9];
         equilibria_w(p, weights_fl(p), ph, C, e, Tc, 0.0, ux, uy, rho, rhocp, feq, geq, heq, leq);
         for (int i = 0; i < 9; i++) {
@@ -553,7 +566,7 @@ static void cell_dynamics(const orc_state *st, int x, int y, cell_out *o)
      * and multiplying would make rho C_p peak inside the interface when the
      * phases have equal rho C_p but very different densities.  This is the
      * same chi-weighted mixture that the enthalpy relation uses. */
-    double rhocp = orc_zeta(phi, fs, p->rho_l * p->cp_l, p->rho_s * p->cp_s, p->rho_g * p->cp_g);
+    double rhocp = rhocp_of(p, phi, fs);
 
     /* unit normal n = grad phi / |grad phi| (Eq. 1), undefined where
      * grad phi = 0.  Regularised as grad phi / sqrt(|grad phi|^2 + 1e-6): the

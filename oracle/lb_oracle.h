@@ -35,6 +35,7 @@ typedef struct {
     int fs_modulated_st, phase_change_on;
     int divu_mode; /* 0: div u = mdot (model value); 1: lagged velocity divergence */
     int lattice_fl; /* lattice of the phase-field and solute sets: 0 D2Q9, 1 D2Q5 */
+    int rhocp_rule; /* 0: the property rule on rho C_p; 1: on rho and C_p apart, multiplied */
 } orc_params;
 
 typedef struct orc_state orc_state;

@@ -21,7 +21,8 @@ PARAM_FIELDS = [(k, C.c_double) for k in (
     "rho_l", "rho_s", "rho_g", "mu_l", "mu_s", "mu_g", "lam_l", "lam_s", "lam_g",
     "cp_l", "cp_s", "cp_g", "latent", "T_sol", "T_liq", "k_p", "D_l", "D_s", "eps", "mobility",
     "sigma0", "sigma_T", "sigma_c", "T_ref", "c_ref", "gx", "gy")] + [
-    ("fs_modulated_st", C.c_int), ("phase_change_on", C.c_int), ("divu_mode", C.c_int), ("lattice_fl", C.c_int)]
+    ("fs_modulated_st", C.c_int), ("phase_change_on", C.c_int), ("divu_mode", C.c_int), ("lattice_fl", C.c_int),
+    ("rhocp_rule", C.c_int)]
 
 
 class _Grid(C.Structure):
@@ -86,7 +87,7 @@ def _grid(g: dict) -> _Grid:
 def _params(p: dict) -> _Params:
     s = _Params()
     for k, _ in PARAM_FIELDS:
-        setattr(s, k, p.get(k, 0) if k in ("divu_mode", "lattice_fl") else p[k])
+        setattr(s, k, p.get(k, 0) if k in ("divu_mode", "lattice_fl", "rhocp_rule") else p[k])
     return s
 
 

@@ -131,6 +131,47 @@ def test_source_moments(oracle_mod, seed):
 # Enthalpy relation (Eq. Hfl)
 # ------------------------------------------------------------------------------------------
 
+def _tf99(oracle_mod, w, params, chunk=50):
+    o = oracle_mod.Oracle(w["grid"], params, w["fields"])
+    prev = 0.0
+    for k in range(1, 400):
+        o.step(chunk)
+        r = o.reduce()
+        frac = r[3] / r[4]
+        if frac >= 0.99:
+            o.close()
+            return chunk * (k - 1) + chunk * (0.99 - prev) / (frac - prev), r
+        prev = frac
+    raise AssertionError("the droplet did not freeze")
+
+
+def test_heat_capacity_readings(oracle_mod):
+    """The property rule of Sec. 2 lists the heat capacity; the oracle applies
+    it to the volumetric rho C_p of each phase (reading R17), not to rho and
+    C_p apart.  (1) With C_p = 1 in every phase the two readings are the same
+    function, so the runs agree bit for bit: the option changes nothing else
+    (a gas density of 0.5 there; with C_p = 1 the gas's rho C_p is that
+    density).  (2) On the freezing droplet with (rho C_p)_g = (rho C_p)_l at a
+    gas density ratio of 0.1, where the literal product peaks threefold inside
+    the liquid-gas interface, the literal reading moves the freezing time by
+    5.0e-3 (1404.1 against 1397.1 steps) and the final V*_sl by 1e-6."""
+    wu = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.5, ste=0.15)
+    uniform = dict(wu["params"], divu_mode=1, cp_l=1.0, cp_s=1.0, cp_g=1.0)
+    runs = []
+    for rule in (0, 1):
+        o = oracle_mod.Oracle(wu["grid"], dict(uniform, rhocp_rule=rule), wu["fields"])
+        o.step(300)
+        runs.append(o.fields())
+        o.close()
+    for k in runs[0]:
+        assert np.all(np.isfinite(runs[0][k])), k
+        assert np.array_equal(runs[0][k], runs[1][k]), k
+    w = W.sessile_droplet(nx=48, ny=40, radius=12.0, rho_g=0.1, ste=0.15)
+    t0, _ = _tf99(oracle_mod, w, dict(w["params"], divu_mode=1, rhocp_rule=0))
+    t1, _ = _tf99(oracle_mod, w, dict(w["params"], divu_mode=1, rhocp_rule=1))
+    assert 2e-3 < (t1 - t0) / t0 < 1e-2, (t0, t1)
+
+
 def test_enthalpy_relation(oracle_mod):
     # a binary alloy with a mushy range, solid and liquid properties different
     p = W.base_params(rho_s=0.9, cp_s=0.7, cp_l=1.2, latent=4.0, T_sol=-0.3, T_liq=0.2)
