@@ -22,7 +22,11 @@ pytestmark = pytest.mark.gpu
 F16 = 1
 F16_H32 = 2
 HALF_FORMS = [F16, F16_H32]
-FIELD_TOL = 6e-3  # measured at most 2.1e-3 (pressure, heated channel) after 100 steps
+# Six roundings of a stored deviation to 11 bits (6 x 2^-11 = 2.9e-3).  Measured
+# after 100 steps over the seven cases below, both half forms: at most 2.3e-3
+# (C, ragged 97 x 71 droplet), 2.1e-3 (u_y and p, heated channel), 1.0e-3
+# (phi, impurity front), 5.2e-4 (f_s), 1.8e-4 (T).
+FIELD_TOL = 6 * 2.0 ** -11
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,7 +43,7 @@ def _half(w, form=F16):
 
 
 @pytest.mark.parametrize("form", HALF_FORMS)
-@pytest.mark.parametrize("name,make,steps", P.CASES[:1] + P.CASES[3:], ids=[c[0] for c in P.CASES[:1] + P.CASES[3:]])
+@pytest.mark.parametrize("name,make,steps", P.CASES, ids=[c[0] for c in P.CASES])
 def test_fp16_fields_against_oracle(oracle_mod, name, make, steps, form):
     w = make()
     got, red, want, wred = P._run_pair(oracle_mod, w, steps, params=_half(w, form)["params"])
