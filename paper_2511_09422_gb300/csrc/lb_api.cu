@@ -194,15 +194,17 @@ static Consts make_consts(const lb_grid *g, const lb_params *p)
     K.fs_mod = p->fs_modulated_st ? 1 : 0;
     K.segh = (p->pop_storage != LB_STORAGE_F32 || p->lattice_fl == LB_LATTICE_D2Q5) ? LB_SEGH_ALT : LB_SEGH;
     // Shorter segments where the lattice gives the persistent wave of W warps too
-    // few work items: a step takes about ceil(items / W) rounds of (segh + 3) rows
-    // (a segment's rows plus its fill and copy prologue); the height of the
-    // default and the shorter candidates (8 rows at least) that minimises it.
+    // few work items.  A work item costs about segh + 3 rows (its rows plus the
+    // fill and copy prologue); the warps share the items dynamically, so a step
+    // takes about items (segh + 3) / W plus one item, the last one started.  The
+    // height of the default and the shorter candidates (8 rows at least) that
+    // minimises it.
     {
         const long long W = with_storage(kind_of(p), [](auto ps) {
             return 152LL * lbk::step_min_blocks<decltype(ps)>() * lbk::step_warps<decltype(ps)>();
         });
         const long long nstrip = (g->nx + LB_TX - 1) / LB_TX;
-        auto cost = [&](int h) { return (nstrip * lbk::strip_segments(g->ny, h) + W - 1) / W * (h + 3); };
+        auto cost = [&](int h) { return (double)(nstrip * lbk::strip_segments(g->ny, h)) * (h + 3) / (double)W + (h + 3); };
         const int cand[] = {24, 16, 12, 8};
         int best = K.segh;
         for (int c : cand)
