@@ -31,7 +31,7 @@ struct lb_handle {
     lbk::StepRec *rec = nullptr;          // the step kernel's record of this lattice
     unsigned long long *counter = nullptr;  // the step kernel's work counters (2)
     long long nitems = 0;                   // work items of one step
-    int red_parts = 0;           // one per warp of the capped MODE_REDUCE grid
+    int red_parts = 0;           // partial slots: one per warp of the largest capped MODE_REDUCE grid
     bool half = false;           // some populations stored in half precision
     // kernel instantiation: 0 FP32 D2Q9, 1 FP16 D2Q9, 2 FP32 with D2Q5 f and l, 3 FP16 f, g, l with FP32 h
     int kind = 0;
@@ -226,16 +226,17 @@ static unsigned strip_blocks(const Consts &K)
     return (unsigned)(lbk::strip_groups(K.nx) * lbk::strip_segments(K.ny, K.segh));
 }
 
+template <class PS>
 static unsigned reduce_blocks(const Consts &K)
 {
-    const unsigned n = strip_blocks(K), cap = 152u * LB_SMINB;
+    const unsigned n = strip_blocks(K), cap = 152u * (unsigned)lbk::strip_min_blocks<PS, false>();
     return n < cap ? n : cap;
 }
 
 template <int MODE, class PS>
 static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials)
 {
-    constexpr size_t smem = lbk::strip_smem<PS>();
+    constexpr size_t smem = lbk::strip_smem<PS, MODE != lbk::MODE_REDUCE>();
     static bool opted = false;  // per instantiation: rings above 48 KB need the opt-in, and the
     if (!opted) {               // largest shared-memory carveout lets every resident block fit
         cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -243,7 +244,7 @@ static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t
                              cudaSharedmemCarveoutMaxShared);
         opted = true;
     }
-    const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks(K) : strip_blocks(K);
+    const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks<PS>(K) : strip_blocks(K);
     lbk::lb_strip_kernel<MODE, PS><<<grid, dim3(32, LB_SW, 1), smem, st>>>(K, B, partials);
 }
 
@@ -320,7 +321,9 @@ static lb_status launch_reduce(lb_handle *h, double out[lbk::NRED])
     B.status = h->status;
     launch_strip<lbk::MODE_REDUCE>(K, B, h->stream, h->kind, h->partials);
     CK(h, cudaGetLastError());
-    lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, h->red_parts, h->red_out);
+    // the warps of this launch's grid (the segment height, and so the grid, can change with lb_batch_tune)
+    const int nparts = (int)with_storage(h->kind, [&](auto ps) { return reduce_blocks<decltype(ps)>(K); }) * LB_SW;
+    lbk::lb_reduce_final_kernel<<<1, lbk::RED_THREADS, 0, h->stream>>>(h->partials, nparts, h->red_out);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(out, h->red_out, sizeof(double) * lbk::NRED, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -360,7 +363,8 @@ static lb_status create_handle(const lb_grid *grid, const lb_params *params, con
     const Consts &K = h->K;
     const long long n = (long long)grid->nx * grid->ny;
     const size_t plane_b = sizeof(float) * (size_t)K.plane;
-    h->red_parts = (int)reduce_blocks(K) * LB_SW;
+    // every grid reduce_blocks can give (a capped wave of at most 6 blocks per SM)
+    h->red_parts = 152 * 6 * LB_SW;
 
     auto alloc = [&](void **p, size_t b) -> cudaError_t {
         cudaError_t e = cudaMalloc(p, b);
@@ -760,13 +764,7 @@ __global__ void __launch_bounds__(lbk::RED_THREADS) noalloc_rows_kernel(const Co
         const int cell = y * K.pitch + x;
         const lbk::CellA c =
             lbk::cell_a<PS>(K, pin, ain, x, y, cell);
-        const double phid = (double)c.phi_p + (double)c.L.dphi;
-        acc[0] += phid;
-        acc[1] += (double)c.ed + (double)K.rr * (double)c.T_p + (double)K.lat_l * ((double)c.chi_p - (double)c.fs_p);
-        acc[2] += (double)c.L.C;
-        acc[3] += (double)c.L.fs;
-        acc[4] += (double)lbk::clamp01(R(0.5) * (R(1.0) + (real)phid));
-        if (x == xc) acc[5] += (double)c.L.fs;
+        lbk::add_diag(K, c.phi_p, c.L.dphi, c.ed, c.T_p, c.chi_p, c.fs_p, c.L.C, c.L.fs, x == xc, acc);
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll

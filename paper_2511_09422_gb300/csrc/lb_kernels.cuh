@@ -542,6 +542,43 @@ __device__ __forceinline__ CellA cell_a(const Consts &K, const float *__restrict
     return c;
 }
 
+// Error-free sum (Knuth's TwoSum, round to nearest): a + b = s + e exactly.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+
+// The diagnostics of one cell (sums of phi, rho H, C, f_s and chi over the
+// lattice, Sec. 4.2 and 4.4) added to FP64 sums with few FP64 operations, the
+// FP64 pipe being the scarce one on this GPU: phi as the exact FP64 sum of its
+// two FP32 parts; C, f_s and chi in FP32 (one conversion and one FP64 addition
+// each); rho H = (sum h + rr dT +
+// Q/2) + rr T_p + rho_l L (chi_p - f_s,p), whose cell terms cancel across the
+// lattice, as an FP32 pair hi + lo from error-free products and sums (its
+// error of order 2^-48 of the terms), so that the sum keeps the accuracy of an
+// FP64 evaluation.  Every kernel that sums the diagnostics calls this.
+__device__ __forceinline__ void add_diag(const Consts &K, real phi_p, real dphi, real ed, real T_p, real chi_p, real fs_p,
+                                         real C, real fs, bool centre, double acc[6])
+{
+    const real phid = __fadd_rn(phi_p, dphi);
+    float dlo, e1, e2;
+    const float d = two_sum(chi_p, -fs_p, dlo);
+    const float p = __fmul_rn(K.rr, T_p), plo = __fmaf_rn(K.rr, T_p, -p);
+    const float q = __fmul_rn(K.lat_l, d), qlo = __fmaf_rn(K.lat_l, d, -q);
+    const float s1 = two_sum(ed, p, e1);
+    const float hi = two_sum(s1, q, e2);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(plo, qlo)), __fmul_rn(K.lat_l, dlo));
+    acc[0] += (double)phi_p + (double)dphi;  // exact in FP64
+    acc[1] += (double)hi + (double)lo;
+    acc[2] += (double)C;
+    acc[3] += (double)fs;
+    acc[4] += (double)clamp01(R(0.5) * (R(1.0) + phid));
+    if (centre) acc[5] += (double)fs;
+}
+
 // Own-cell lagged values staged for phase B (the accessor's aux(k)).
 enum { AX_Q = 0, AX_FS = 1, AX_C = 2, NAX = 3 };
 
@@ -929,10 +966,6 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 #ifndef LB_SW
 #define LB_SW 2
 #endif
-// Blocks per SM of the capped diagnostics grid (one FP64 partial per warp).
-#ifndef LB_SMINB
-#define LB_SMINB 4
-#endif
 // Inner segment height of single-lattice handles, per kernel kind (measured on
 // the 4096^2 step): FP32 D2Q9 is fastest at 8-12 rows (32 rows: 5 % slower);
 // the half forms and D2Q5 f/l at 32 rows (24 rows: 0.7-1.3 % slower).  The host
@@ -965,22 +998,25 @@ __host__ __device__ constexpr int win_elems()
 }
 
 // The rings of one warp under storage PS (windows of half sets take 96 bytes,
-// so a warp's rings are smaller and more warps fit on an SM).
-template <class PS>
+// so a warp's rings are smaller and more warps fit on an SM).  PB = false:
+// the rings of a sweep that runs phase A alone (the diagnostics), without the
+// phase-A outputs, the staged (p, S) and the g pulls that only phase B reads
+// (one placeholder row each, never touched).
+template <class PS, bool PB = true>
 struct WarpRing {
     static constexpr int OFF_H = 9 * win_bytes<PS>(SET_F);            // h windows in a pop row
     static constexpr int OFF_L = OFF_H + 9 * win_bytes<PS>(SET_H);    // l windows
     static constexpr int POPROW = OFF_L + 9 * win_bytes<PS>(SET_L);   // bytes of one pop row
     float2 lag[5][34];    // (phi, T) lagged           rows y mod 5
-    float2 dd[3][32];     // (dphi, dT)                 rows y mod 3
-    float2 cf[3][32];     // (C, f_s)                   rows y mod 3
-    float2 ps[4][32];     // (p, S) lagged, staged      rows y & 3
-    float md[3][32];      // mdot                       rows y mod 3
-    float dv[3][32];      // div u of the phi and h sources, rows y mod 3
-    float2 uv[4][34];     // lagged (u_x, u_y), staged    rows y & 3
+    float2 dd[PB ? 3 : 1][32];     // (dphi, dT)                 rows y mod 3
+    float2 cf[PB ? 3 : 1][32];     // (C, f_s)                   rows y mod 3
+    float2 ps[PB ? 4 : 1][32];     // (p, S) lagged, staged      rows y & 3
+    float md[PB ? 3 : 1][32];      // mdot                       rows y mod 3
+    float dv[PB ? 3 : 1][32];      // div u of the phi and h sources, rows y mod 3
+    float2 uv[5][34];     // lagged (u_x, u_y), staged    rows y mod 5
     float ax[3][NAX][WW];  // staged own-cell Q, f_s, C   rows y mod 3
     alignas(16) unsigned char pop[3][POPROW];       // staged pulls of f, h, l (windows 0..8 of each)
-    alignas(16) unsigned char gp[2][9 * win_bytes<PS>(SET_G)];  // staged pulls of g
+    alignas(16) unsigned char gp[PB ? 2 : 1][PB ? 9 * win_bytes<PS>(SET_G) : 16];  // staged pulls of g
     // first element of window i of set S (f, h or l) in pop row r, or of g in gp row r
     template <int S>
     __device__ SetT<PS, S> *win(int r, int i)
@@ -996,15 +1032,16 @@ struct WarpRing {
     }
 };
 
-template <class PS>
-__host__ __device__ constexpr size_t strip_smem() { return sizeof(WarpRing<PS>) * LB_SW; }
+template <class PS, bool PB = true>
+__host__ __device__ constexpr size_t strip_smem() { return sizeof(WarpRing<PS, PB>) * LB_SW; }
 
 // Blocks (of LB_SW warps) resident per SM: as many as the rings of storage PS
 // allow in the 228 KB of shared memory (1 KB reserved per block), at most 6.
-template <class PS>
+template <class PS, bool PB = true>
 __host__ __device__ constexpr int strip_min_blocks()
 {
-    return (int)((228 * 1024) / (strip_smem<PS>() + 1024)) < 6 ? (int)((228 * 1024) / (strip_smem<PS>() + 1024)) : 6;
+    return (int)((228 * 1024) / (strip_smem<PS, PB>() + 1024)) < 6 ? (int)((228 * 1024) / (strip_smem<PS, PB>() + 1024))
+                                                                    : 6;
 }
 
 // Warps per block of the step kernel under storage PS.  Its warps claim work
@@ -1061,8 +1098,8 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 // Decoded staged pulls of set S for the lane whose window index is idx.
-template <class PS, int S>
-__device__ __forceinline__ void load9(const Consts &K, const WarpRing<PS> &w, int slot, int idx, real v[9])
+template <class PS, int S, class RG>
+__device__ __forceinline__ void load9(const Consts &K, const RG &w, int slot, int idx, real v[9])
 {
     typedef SetT<PS, S> T;
     constexpr int E = win_elems<PS, S>();
@@ -1108,7 +1145,7 @@ struct RingAcc {
     __device__ real S(int dy, int dx) const { return psv(dy, dx).y; }
     __device__ real mdot(int dy, int dx) const { return w.md[sl[dy + 1]][lane + dx]; }
     __device__ real divu() const { return w.dv[sl[1]][lane]; }
-    __device__ float2 lagu() const { return w.uv[sq[1]][lane + 1]; }  // own lagged (u_x, u_y)
+    __device__ float2 lagu() const { return w.uv[sg[1]][lane + 1]; }  // own lagged (u_x, u_y)
     // pulled f, h (wall rule applied), l of the cell at (x, y)
     template <int S>
     __device__ void pops(const Consts &K, const float *__restrict__, int x, int y, long long, real v[9], real T_own) const
@@ -1198,16 +1235,17 @@ __device__ __forceinline__ void lag_dev_sums(const Consts &K, const RG &w, int l
 }
 
 // Isotropic divergence of the lagged velocity at row y, lane column, from the
-// uv ring (columns x0 - 2 .. x0 + 31 at index lane + 1 + dx); a row beyond a
-// wall is the ghost -u of row y.  Same stencil and order as lagged_divu.
+// uv ring (columns x0 - 2 .. x0 + 31 at index lane + 1 + dx; lr the ring rows
+// of rows y - 1, y and y + 1, those of the lag ring); a row beyond a wall is
+// the ghost -u of row y.  Same stencil and order as lagged_divu.
 template <bool W, class RG>
-__device__ __forceinline__ real ring_divu(const Consts &K, const RG &w, int lane, int y)
+__device__ __forceinline__ real ring_divu(const Consts &K, const RG &w, int lane, int y, const int lr[3])
 {
     const int c = lane + 1;
     const bool gs = W && y - 1 < 0, gn = W && y + 1 >= K.ny;
-    const float2 *r0 = w.uv[y & 3];
-    const float2 *rs = gs ? r0 : w.uv[(y - 1) & 3];
-    const float2 *rn = gn ? r0 : w.uv[(y + 1) & 3];
+    const float2 *r0 = w.uv[lr[1]];
+    const float2 *rs = gs ? r0 : w.uv[lr[0]];
+    const float2 *rn = gn ? r0 : w.uv[lr[2]];
     const real ss = gs ? R(-1.0) : R(1.0), sn = gn ? R(-1.0) : R(1.0);
     const real dudx = wgt(1) * (r0[c + 1].x - r0[c - 1].x) +
                       wgt(5) * ((sn * rn[c + 1].x - sn * rn[c - 1].x) + (ss * rs[c + 1].x - ss * rs[c - 1].x));
@@ -1219,7 +1257,8 @@ __device__ __forceinline__ real ring_divu(const Consts &K, const RG &w, int lane
 // Phase A / phase B sweep of one warp over rows [ys, ye) of its strip.  WALLS =
 // false: every row ys - 2 .. ye + 1 lies inside the lattice.
 template <int MODE, bool WALLS, class PS>
-__device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing<PS> &w, int lane, int x0, int ys, int ye,
+__device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, WarpRing<PS, MODE != MODE_REDUCE> &w, int lane,
+                                           int x0, int ys, int ye,
                                            double acc[NRED])
 {
     typedef SetT<PS, SET_F> TF;  // f and l
@@ -1266,14 +1305,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     };
     // lagged (u_x, u_y) of row yl with the one-column halo: the own-cell velocity of
     // phase B, and the divergence of phase A (div u the lagged velocity divergence)
-    auto stage_u = [&](int yl) {
+    auto stage_u = [&](int yl, int lr) {  // into uv-ring row lr (= yl mod 5)
         if ((!PB && !K.divu) || (WALLS && (yl < 0 || yl >= K.ny))) return;
         const int ro = yl * K.pitch;
-        cp_async4(&w.uv[yl & 3][lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xa));
-        cp_async4(&w.uv[yl & 3][lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xa));
+        cp_async4(&w.uv[lr][lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xa));
+        cp_async4(&w.uv[lr][lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xa));
         if (lane < 2) {
-            cp_async4(&w.uv[yl & 3][32 + lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xb));
-            cp_async4(&w.uv[yl & 3][32 + lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xb));
+            cp_async4(&w.uv[lr][32 + lane].x, plane_ptr(ain, AUX_UX, K) + (ro + xb));
+            cp_async4(&w.uv[lr][32 + lane].y, plane_ptr(ain, AUX_UY, K) + (ro + xb));
         }
     };
     // own-cell lagged values of row y as float windows: Q, f_s and (phase B) C, one copy
@@ -1391,28 +1430,40 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     const int ya0 = PB ? ys - 1 : ys;
     const int ya1 = PB ? ye : ye - 1;
     int s3 = mod3(ya0), l5 = mod5(ya0);  // ya mod 3 and ya mod 5, advanced with the loop
-    auto lrow = [&](int k) {             // lag-ring row of row ya + k, k in -2 .. 2
+    auto lrow = [&](int k) {             // lag- and uv-ring row of row ya + k, k in -2 .. 3
         const int v = l5 + k;
         return v >= 5 ? v - 5 : (v < 0 ? v + 5 : v);
     };
+    // Rows of copies in flight: one with phase B, whose rings hold row ya - 1 for
+    // it; two for phase A alone (the diagnostics), in the ring rows phase B
+    // would hold.
+    constexpr int AHEAD = PB ? 1 : 2;
     stage_lag(ya0 - 1, lrow(-1));
     stage_lag(ya0, lrow(0));
     stage_lag(ya0 + 1, lrow(1));
-    stage_u(ya0 - 1);
-    stage_u(ya0);
-    stage_u(ya0 + 1);
+    stage_u(ya0 - 1, lrow(-1));
+    stage_u(ya0, lrow(0));
+    stage_u(ya0 + 1, lrow(1));
     stage_a(ya0, s3);
     cp_async_commit();
+    if constexpr (AHEAD == 2) {
+        if (ya0 < ya1) {
+            stage_lag(ya0 + 2, lrow(2));
+            stage_u(ya0 + 2, lrow(2));
+            stage_a(ya0 + 1, s3 == 2 ? 0 : s3 + 1);
+        }
+        cp_async_commit();
+    }
     for (int ya = ya0; ya <= ya1; ya++, s3 = s3 == 2 ? 0 : s3 + 1, l5 = l5 == 4 ? 0 : l5 + 1) {
         const int s3n = s3 == 2 ? 0 : s3 + 1, s3p = s3 == 0 ? 2 : s3 - 1;  // (ya + 1), (ya - 1) mod 3
-        if (ya < ya1) {
-            stage_lag(ya + 2, lrow(2));
-            stage_u(ya + 2);
-            stage_a(ya + 1, s3n);
+        if (ya + AHEAD <= ya1) {
+            stage_lag(ya + 1 + AHEAD, lrow(1 + AHEAD));
+            stage_u(ya + 1 + AHEAD, lrow(1 + AHEAD));
+            stage_a(ya + AHEAD, AHEAD == 1 ? s3n : s3p);  // (ya + 2) mod 3 = (ya - 1) mod 3
         }
         stage_g(ya);
         cp_async_commit();
-        cp_async_wait<1>();  // everything staged for row ya (and g of row ya - 1) has landed
+        cp_async_wait<AHEAD>();  // everything staged for row ya (and g of row ya - 1) has landed
         __syncwarp();
         // ---- phase A, row ya ------------------------------------------------------------
         if (!WALLS || (ya >= 0 && ya < K.ny)) {
@@ -1431,18 +1482,10 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             const real sl = sum9(v);
             const real fs_p = w.ax[s3][AX_FS][lane + off];
             const real chi_p = clamp01(R(0.5) * (R(1.0) + phi_p));
-            const real dv = K.divu ? ring_divu<WALLS>(K, w, lane, ya) : R(0.0);
+            const real dv = K.divu ? ring_divu<WALLS>(K, w, lane, ya, lr) : R(0.0);
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl, dv);
             if (MODE == MODE_REDUCE) {
-                if (b_lane) {
-                    const double phid = (double)phi_p + (double)L.dphi;
-                    acc[0] += phid;
-                    acc[1] += (double)ed + (double)K.rr * (double)T_p + (double)K.lat_l * ((double)chi_p - (double)fs_p);
-                    acc[2] += (double)L.C;
-                    acc[3] += (double)L.fs;
-                    acc[4] += (double)clamp01(R(0.5) * (R(1.0) + (real)phid));
-                    if (ex == K.nx / 2) acc[5] += (double)L.fs;
-                }
+                if (b_lane) add_diag(K, phi_p, L.dphi, ed, T_p, chi_p, fs_p, L.C, L.fs, ex == K.nx / 2, acc);
             } else {
                 w.dd[s3][lane] = make_float2(L.dphi, L.dT);
                 w.cf[s3][lane] = make_float2(L.C, L.fs);
@@ -1452,12 +1495,14 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         }
         __syncwarp();
         // ---- phase B, row ya - 1 ----------------------------------------------------------
-        const int yb = ya - 1;
-        if (PB && yb >= ys && yb < ye && b_lane) {
-            // rows yb - 1 = ya - 2, yb = ya - 1 and yb + 1 = ya are s3n, s3p and s3 mod 3
-            const RingAcc<PS, WALLS> A{w, lane, off, off_h, {s3n, s3p, s3}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
-                                       {lrow(-2), lrow(-1), lrow(0)}, s3p, yb & 1};
-            phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
+        if constexpr (PB) {
+            const int yb = ya - 1;
+            if (yb >= ys && yb < ye && b_lane) {
+                // rows yb - 1 = ya - 2, yb = ya - 1 and yb + 1 = ya are s3n, s3p and s3 mod 3
+                const RingAcc<PS, WALLS> A{w, lane, off, off_h, {s3n, s3p, s3}, {(yb - 1) & 3, yb & 3, (yb + 1) & 3},
+                                           {lrow(-2), lrow(-1), lrow(0)}, s3p, yb & 1};
+                phase_b<MODE, WALLS, PS>(K, B, A, ex, yb, yb * K.pitch + ex);
+            }
         }
         __syncwarp();
     }
@@ -1468,14 +1513,15 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
 #ifdef LB_MAXNREG
 #define LB_STRIP_BOUNDS __maxnreg__(LB_MAXNREG)
 #else
-#define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, strip_min_blocks<PS>())
+#define LB_STRIP_BOUNDS __launch_bounds__(32 * LB_SW, (strip_min_blocks<PS, MODE != MODE_REDUCE>()))
 #endif
 
 template <int MODE, class PS>
 __global__ void LB_STRIP_BOUNDS lb_strip_kernel(const Consts K, const Buffers B, double *__restrict__ partials)
 {
     extern __shared__ __align__(16) unsigned char lb_smem[];
-    WarpRing<PS> &w = reinterpret_cast<WarpRing<PS> *>(lb_smem)[threadIdx.y];
+    typedef WarpRing<PS, MODE != MODE_REDUCE> Ring;
+    Ring &w = reinterpret_cast<Ring *>(lb_smem)[threadIdx.y];
     const int lane = threadIdx.x;
     const int ngroups = strip_groups(K.nx);
     const int nblocks = ngroups * strip_segments(K.ny, K.segh);
