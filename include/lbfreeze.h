@@ -268,7 +268,7 @@ lb_status lb_batch_step(lb_batch *b, int n);
 lb_status lb_batch_use_graph(lb_batch *b, int on);
 
 /* Autotuner: for each size class (lattice rows < 192, < 320, >= 320) time
- * `trials` batched launches with inner row segments of 8, 16, 32 and 64 rows
+ * `trials` batched launches with inner row segments of 8, 12, 16, 24, 32 and 64 rows
  * and keep the fastest; seg_rows (3 ints, may be NULL) receives the choice per
  * class (0 for an empty class).  The trial launches do not advance the state.
  * Synchronises the stream. */

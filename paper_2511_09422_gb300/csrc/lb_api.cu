@@ -1007,7 +1007,7 @@ extern "C" lb_status lb_batch_tune(lb_batch *b, int trials, int seg_rows[3])
 {
     if (!b || trials < 1) return bfail(b, LB_ERR_INVALID_ARG, "null batch or trials < 1");
     if (b->sticky != LB_OK) return b->sticky;
-    const int cand[4] = {8, 16, 32, 64};
+    const int cand[6] = {8, 12, 16, 24, 32, 64};
     const int p = b->h[0]->cur;
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
@@ -1020,7 +1020,7 @@ extern "C" lb_status lb_batch_tune(lb_batch *b, int trials, int seg_rows[3])
         if (!any) continue;
         float best_ms = 0.0f;
         int best = 0;
-        for (int k = 0; k < 4 && st == LB_OK; k++) {
+        for (int k = 0; k < 6 && st == LB_OK; k++) {
             for (lb_handle *h : b->h)
                 if (size_class(h) == c) h->K.segh = cand[k];
             st = upload_instances(b);
