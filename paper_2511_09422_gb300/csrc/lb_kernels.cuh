@@ -552,32 +552,58 @@ __device__ __forceinline__ float two_sum(float a, float b, float &e)
 }
 
 // The diagnostics of one cell (sums of phi, rho H, C, f_s and chi over the
-// lattice, Sec. 4.2 and 4.4) added to FP64 sums with few FP64 operations, the
-// FP64 pipe being the scarce one on this GPU: phi as the exact FP64 sum of its
-// two FP32 parts; C, f_s and chi in FP32 (one conversion and one FP64 addition
-// each); rho H = (sum h + rr dT +
-// Q/2) + rr T_p + rho_l L (chi_p - f_s,p), whose cell terms cancel across the
-// lattice, as an FP32 pair hi + lo from error-free products and sums (its
-// error of order 2^-48 of the terms), so that the sum keeps the accuracy of an
-// FP64 evaluation.  Every kernel that sums the diagnostics calls this.
+// lattice, Sec. 4.2 and 4.4) as seven FP32 addends, chosen so that their sums
+// keep the accuracy of an FP64 evaluation: phi as its two FP32 parts phi_p and
+// dphi; rho H = (sum h + rr dT + Q/2) + rr T_p + rho_l L (chi_p - f_s,p), whose
+// cell terms cancel across the lattice, as an FP32 pair hi + lo from
+// error-free products and sums (error of order 2^-48 of the terms); C, f_s and
+// chi of the new phi.  FP64 is the scarce pipe on this GPU, so these are
+// added in FP32 with compensation where many cells are summed, and in FP64
+// elsewhere; both sums agree to about 1e-13.
+struct DiagTerms {
+    float t[7];
+};
+__device__ __forceinline__ DiagTerms diag_terms(const Consts &K, real phi_p, real dphi, real ed, real T_p, real chi_p,
+                                                real fs_p, real C, real fs)
+{
+    DiagTerms d;
+    float dlo, e1, e2;
+    const float dc = two_sum(chi_p, -fs_p, dlo);
+    const float p = __fmul_rn(K.rr, T_p), plo = __fmaf_rn(K.rr, T_p, -p);
+    const float q = __fmul_rn(K.lat_l, dc), qlo = __fmaf_rn(K.lat_l, dc, -q);
+    const float s1 = two_sum(ed, p, e1);
+    d.t[0] = phi_p;
+    d.t[1] = dphi;
+    d.t[2] = two_sum(s1, q, e2);
+    d.t[3] = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(plo, qlo)), __fmul_rn(K.lat_l, dlo));
+    d.t[4] = C;
+    d.t[5] = fs;
+    d.t[6] = clamp01(R(0.5) * (R(1.0) + __fadd_rn(phi_p, dphi)));
+    return d;
+}
+// FP64 sums of the diagnostics (acc[5]: f_s on the centre column).
 __device__ __forceinline__ void add_diag(const Consts &K, real phi_p, real dphi, real ed, real T_p, real chi_p, real fs_p,
                                          real C, real fs, bool centre, double acc[6])
 {
-    const real phid = __fadd_rn(phi_p, dphi);
-    float dlo, e1, e2;
-    const float d = two_sum(chi_p, -fs_p, dlo);
-    const float p = __fmul_rn(K.rr, T_p), plo = __fmaf_rn(K.rr, T_p, -p);
-    const float q = __fmul_rn(K.lat_l, d), qlo = __fmaf_rn(K.lat_l, d, -q);
-    const float s1 = two_sum(ed, p, e1);
-    const float hi = two_sum(s1, q, e2);
-    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(plo, qlo)), __fmul_rn(K.lat_l, dlo));
-    acc[0] += (double)phi_p + (double)dphi;  // exact in FP64
-    acc[1] += (double)hi + (double)lo;
-    acc[2] += (double)C;
-    acc[3] += (double)fs;
-    acc[4] += (double)clamp01(R(0.5) * (R(1.0) + phid));
+    const DiagTerms d = diag_terms(K, phi_p, dphi, ed, T_p, chi_p, fs_p, C, fs);
+    acc[0] += (double)d.t[0] + (double)d.t[1];
+    acc[1] += (double)d.t[2] + (double)d.t[3];
+    acc[2] += (double)d.t[4];
+    acc[3] += (double)d.t[5];
+    acc[4] += (double)d.t[6];
     if (centre) acc[5] += (double)fs;
 }
+// Compensated FP32 sum (TwoSum, the rounding errors gathered in c).
+struct CompSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float e;
+        s = two_sum(s, x, e);
+        c = __fadd_rn(c, e);
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 // Own-cell lagged values staged for phase B (the accessor's aux(k)).
 enum { AX_Q = 0, AX_FS = 1, AX_C = 2, NAX = 3 };
@@ -1427,6 +1453,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
         }
     };
 
+    CompSum csum[7];  // MODE_REDUCE: this segment's diagnostics addends (diag_terms)
     const int ya0 = PB ? ys - 1 : ys;
     const int ya1 = PB ? ye : ye - 1;
     int s3 = mod3(ya0), l5 = mod5(ya0);  // ya mod 3 and ya mod 5, advanced with the loop
@@ -1485,7 +1512,12 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
             const real dv = K.divu ? ring_divu<WALLS>(K, w, lane, ya, lr) : R(0.0);
             const Local L = local_fields(K, phi_p, delta, ed, T_p, chi_p, fs_p, sl, dv);
             if (MODE == MODE_REDUCE) {
-                if (b_lane) add_diag(K, phi_p, L.dphi, ed, T_p, chi_p, fs_p, L.C, L.fs, ex == K.nx / 2, acc);
+                if (b_lane) {
+                    const DiagTerms d = diag_terms(K, phi_p, L.dphi, ed, T_p, chi_p, fs_p, L.C, L.fs);
+#pragma unroll
+                    for (int q = 0; q < 7; q++) csum[q].add(d.t[q]);
+                    if (ex == K.nx / 2) acc[5] += (double)L.fs;
+                }
             } else {
                 w.dd[s3][lane] = make_float2(L.dphi, L.dT);
                 w.cf[s3][lane] = make_float2(L.C, L.fs);
@@ -1508,6 +1540,13 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
     }
     cp_async_wait<0>();
     __syncwarp();
+    if constexpr (MODE == MODE_REDUCE) {
+        acc[0] += csum[0].value() + csum[1].value();
+        acc[1] += csum[2].value() + csum[3].value();
+        acc[2] += csum[4].value();
+        acc[3] += csum[5].value();
+        acc[4] += csum[6].value();
+    }
 }
 
 #ifdef LB_MAXNREG
