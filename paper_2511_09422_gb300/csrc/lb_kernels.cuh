@@ -60,6 +60,8 @@ namespace lbk {
 // ---------------------------------------------------------------------------------------
 __host__ __device__ constexpr int cx(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
 __host__ __device__ constexpr int cy(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+// c_iy of a direction known only at run time: a 2-bit table (c_iy + 1 for i = 0 .. 8).
+__device__ __forceinline__ int cy_rt(int i) { return ((0x2865 >> (2 * i)) & 3) - 1; }
 __host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
 __host__ __device__ constexpr real wgt(int i) { return i == 0 ? (R(4.0) / R(9.0)) : (i <= 4 ? (R(1.0) / R(9.0)) : (R(1.0) / R(36.0))); }
 // Weights of the phase-field and solute sets on a lattice of Q = 9 or 5
@@ -1375,8 +1377,9 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                         const int wi = 5 * q + hg;
                         if (wi < NHW) {
                             // HMIX: f 0..8, l 9..17; else f 0..8, h 9..17, l 18..26
-                            const int set = HMIX ? (wi < 9 ? SET_F : SET_L) : (wi < 9 ? SET_F : (wi < 18 ? SET_H : SET_L));
-                            const int i = wi % 9;
+                            const int grp = wi >= 9 ? (wi >= 18 ? 2 : 1) : 0;
+                            const int set = HMIX ? (grp == 0 ? SET_F : SET_L) : (grp == 0 ? SET_F : (grp == 1 ? SET_H : SET_L));
+                            const int i = wi - 9 * grp;
                             __half *dst = set == SET_F ? w.template win<SET_F>(s3, i)
                                                        : (set == SET_H ? reinterpret_cast<__half *>(w.template win<SET_H>(s3, i))
                                                                        : w.template win<SET_L>(s3, i));
@@ -1386,7 +1389,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                             const __half *src = reinterpret_cast<const __half *>(
                                                     reinterpret_cast<const char *>(pin) +
                                                     (size_t)(unsigned)K.plane * (unsigned)(before + 2 * i)) +
-                                                ((y - cy(i)) * K.pitch + x_lo + CH * hpart);
+                                                ((y - cy_rt(i)) * K.pitch + x_lo + CH * hpart);
                             cp_async16(dst + CH * hpart, src);
                         }
                     }
@@ -1443,7 +1446,7 @@ __device__ __forceinline__ void strip_rows(const Consts &K, const Buffers &B, Wa
                         if (i < 9)
                             cp_async16(gw + i * EG + CH * hpart,
                                        reinterpret_cast<const __half *>(set_plane<PS, SET_G>(pin, i, K)) +
-                                           ((y - cy(i)) * K.pitch + x_lo + CH * hpart));
+                                           ((y - cy_rt(i)) * K.pitch + x_lo + CH * hpart));
                     }
                 }
             }
