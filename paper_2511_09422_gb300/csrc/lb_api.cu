@@ -233,15 +233,26 @@ static unsigned reduce_blocks(const Consts &K)
     return n < cap ? n : cap;
 }
 
+// Shared-memory carveout (percent of the 228 KB maximum) that holds `blocks`
+// resident blocks of `smem` bytes each (1 KB reserved per block) and no more:
+// the rest of the SM's 256 KB stays L1, which caches the per-lane staging
+// copies of the strip ends and wall bands.
+static int carveout_for(int blocks, size_t smem)
+{
+    const long long need = (long long)blocks * ((long long)smem + 1024), max = 228LL * 1024;
+    const int pct = (int)((100 * need + max - 1) / max);
+    return pct > 100 ? 100 : pct;
+}
+
 template <int MODE, class PS>
 static void launch_strip_as(const Consts &K, const lbk::Buffers &B, cudaStream_t st, double *partials)
 {
     constexpr size_t smem = lbk::strip_smem<PS, MODE != lbk::MODE_REDUCE>();
     static bool opted = false;  // per instantiation: rings above 48 KB need the opt-in, and the
-    if (!opted) {               // largest shared-memory carveout lets every resident block fit
+    if (!opted) {               // carveout holds every resident block
         cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(lbk::lb_strip_kernel<MODE, PS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+                             carveout_for(lbk::strip_min_blocks<PS, MODE != lbk::MODE_REDUCE>(), smem));
         opted = true;
     }
     const unsigned grid = MODE == lbk::MODE_REDUCE ? reduce_blocks<PS>(K) : strip_blocks(K);
@@ -291,7 +302,7 @@ static cudaError_t launch_step_as(const lbk::StepRec *rec, int ninst, long long 
     if (!opted) {
         cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(lbk::lb_step_kernel<PS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
+                             carveout_for(lbk::step_min_blocks<PS>(), smem));
         opted = true;
     }
     // one persistent wave: as many blocks per SM as the rings of PS allow
