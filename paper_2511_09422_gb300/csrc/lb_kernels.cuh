@@ -977,14 +977,15 @@ __device__ __forceinline__ void phase_b(const Consts &K, const Buffers &B, const
 // warp needs is staged into its rings by cp.async one row ahead of its use:
 // while the warp computes phase A of row y and phase B of row y - 1, the
 // copies for phase A of row y + 1 (and phase B of row y) are in flight.
-// Rings per warp (columns x0-2 .. x0+31 for lag, the warp's 32 lanes otherwise):
-//   lag  lagged (phi, T) pairs                             rows y & 7
-//   dd, cf, md, dv  (dphi, dT), (C, f_s), mdot, div u from phase A   rows y & 3
-//   uv   lagged (u_x, u_y) pairs (div u = lagged divergence only)      rows y & 3
+// Rings per warp (columns x0-2 .. x0+31 for lag and uv, the warp's 32 lanes otherwise;
+// WarpRing below, sized per storage form):
+//   lag  lagged (phi, T) pairs                             rows y mod 5
+//   uv   lagged (u_x, u_y) pairs                           rows y mod 5
+//   dd, cf, md, dv  (dphi, dT), (C, f_s), mdot, div u from phase A   rows y mod 3
 //   ps   staged lagged (p, S) pairs                        rows y & 3
 //   pop  staged pulls of f, h, l (stored form), windows    rows y mod 3
-//   ax   staged own-cell Q, f_s, u_x, u_y, C, windows       rows y mod 3
-//   gp   staged pulls of g, windows                         rows y & 1
+//   ax   staged own-cell Q, f_s, C, windows                rows y mod 3
+//   gp   staged pulls of g, windows                        rows y & 1
 // One launch covers the lattice.  Per group of LB_SW strips it has two bands with
 // the wall rules -- rows 0 .. 1 and rows ny-2 .. ny-1 -- and segments of K.segh
 // rows inside 2 .. ny-3, whose rows and pull sources (ys - 2 .. ye + 1) all lie
